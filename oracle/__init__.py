@@ -1,0 +1,25 @@
+"""FP64 CPU oracle of the two-population phase-field lattice Boltzmann step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, readable
+statement of what the GPU library computes, written from the paper
+(Otomo, Zhang & Chen, "Improved phase-field-based lattice Boltzmann models
+with a filtered collision operator", arXiv 1812.00118, Section 2 and Eq. 13).
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it.  The product path
+(``paper_1812_00118_gb300``) never imports, links or runs anything here,
+and nothing here imports the product path: the two share no code, no
+tables and no helpers.
+
+Modules
+-------
+lattice      D2Q9 / D3Q19 velocity sets and weights, lattice temperature T.
+pflbm        the per-time-step update (Eqs. 1-13) on whole fields, FP64.
+diagnostics  Laplace-law measurement and global sums used by validation.
+
+Every function cites the section / equation it follows.  Readings of
+places where the paper is silent or garbled are stated at the function
+that takes them.  Parity status: every function here is pinned by
+``tests/test_oracle_*.py`` except the optional diffusion correction
+``delta_theta`` (Eq. 14), whose function F the paper leaves open:
+parity unpinned.
+"""
