@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of the fused phase-field LB step (GLUPS) on GB300.
+
+Workload (the D3Q19 static-bubble configuration): 128^3 periodic box, FP32
+populations, bubble of radius 24 at the centre, interface width W = 5,
+density ratio 1000 (rho_L = 0.001, rho_H = 1), kinematic viscosity 1e-3 in
+both phases, sigma = 1e-3, mobility M = 0.1, initial u = 0, P = 0.
+
+A "step" is one lattice time step: one launch of the fused collide-and-
+pull-stream kernel over all 2,097,152 nodes.  Each step reads 2*19 FP32
+populations and writes 2*19 per node (304 algorithmic bytes per lattice
+update): 638 MB move per step, so the inputs are larger than the 129 MB L2
+and no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (launched by torchrun; weak
+scaling): the single-domain step has no data-parallel split without a halo
+exchange, which this build does not implement.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (128, 128, 128)          # nx, ny, nz
+BUBBLE_R, W_IF = 24.0, 5.0
+PHYS = dict(M=0.1, W=W_IF, sigma=1e-3, rho_L=1e-3, rho_H=1.0, nu_L=1e-3, nu_H=1e-3)
+BYTES_PER_LU = {"f64": 608, "f32": 304, "f16s": 152, "bf16s": 152}
+METRIC = "D3Q19 two-population phase-field LB throughput (GLUPS), 128^3 static bubble"
+WORKLOAD = ("D3Q19 static bubble 128^3 periodic, R=24, W=5, rho ratio 1000, nu=1e-3, sigma=1e-3, "
+            "M=0.1 (lattice units), fused collide + pull-stream step")
+PROFILE = os.path.join(ROOT, "profiles", "step_d3q19_f32_128cube.md")
+KERNEL_SOURCES = ["lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_instances.cuh", "lbm_tables.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--store", choices=list(BYTES_PER_LU), default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1812_00118_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "kernel_source_sha")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def workload_fields():
+    from paper_1812_00118_gb300 import inputs as I
+    nx, ny, nz = SHAPE
+    phi, u, P = I.sphere((nz, ny, nx), (nx / 2, ny / 2, nz / 2), BUBBLE_R, W_IF, drop=False)
+    return phi, u, P
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("LBM_BENCH_GLOO") is None else "gloo")
+    return world, rank, local, dist
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_glups(n_edge, steps, warmup=0):
+    """The FP64 numpy oracle as it stands on the host: `steps` time steps on a
+    periodic n_edge^3 crop of the workload fields around the bubble interface.
+    Returns (GLUPS, seconds, nodes)."""
+    import numpy as np
+
+    from oracle import lattice as OL
+    from oracle import pflbm as O
+    phi, u, P = workload_fields()
+    nx, ny, nz = SHAPE
+    if n_edge >= nx:
+        sl = (slice(None),) * 3
+    else:
+        c = (nz // 2, ny // 2, nx // 2 + int(BUBBLE_R))
+        sl = tuple(slice(ci - n_edge // 2, ci - n_edge // 2 + n_edge) for ci in c)
+    phi_s, P_s = np.ascontiguousarray(phi[sl]), np.ascontiguousarray(P[sl])
+    u_s = np.ascontiguousarray(u[(slice(None),) + sl])
+    p = O.Params(**PHYS)
+    h, g = O.init_populations(phi_s, u_s, P_s, OL.D3Q19, p)
+    for _ in range(warmup):
+        h, g = O.step(h, g, OL.D3Q19, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h, g = O.step(h, g, OL.D3Q19, p)
+    dt = time.perf_counter() - t0
+    nodes = phi_s.size
+    return nodes * steps / dt / 1e9, dt, nodes
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, each step a bounded crop of the workload."""
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return
+    # per-step crop sized so that warmup + steps take about 90 s at ~3 us/node
+    budget, cost = 90.0, 3e-6
+    n = int((budget / max(1, args.steps + args.warmup) / cost) ** (1 / 3))
+    n = max(8, min(SHAPE[0], n))
+    glups, dt, nodes = oracle_glups(n, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"periodic {n}^3 crop of the 128^3 fields per step"},
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps on a {n}^3 crop ({nodes} nodes) of the workload"},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1812_00118_gb300 import build, lbm
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    lbm.load()
+    store = {"f64": lbm.F64, "f32": lbm.F32, "f16s": lbm.F16S, "bf16s": lbm.BF16S}[args.store]
+    prm = lbm.make_params(store=store, **PHYS)
+    stream = torch.cuda.Stream()
+    phi, u, P = workload_fields()
+    nx, ny, nz = SHAPE
+    N = nx * ny * nz
+    with torch.cuda.stream(stream):
+        sim = lbm.Simulation(lbm.D3Q19, SHAPE, prm, stream=stream.cuda_stream)
+        sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
+                        np.ascontiguousarray(P.reshape(-1)))
+        sim.step(args.warmup)
+        stream.synchronize()
+        # --- device-timed region
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        time.sleep(0.3)
+        n0 = sim.launch_count()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        start.record(stream)
+        for a, b in evs:
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+        end.record(stream)
+        end.synchronize()
+        torch.cuda.synchronize()
+        launches = sim.launch_count() - n0
+        clk = clocks.stop()
+        ms = start.elapsed_time(end)
+        per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        diag = sim.diagnostics(raise_on_divergence=False)
+        # --- end-to-end region: host (pinned) fields in, K steps, fields out
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_phi, h_u, h_P = pin(phi.reshape(-1)), pin(u.reshape(-1)), pin(P.reshape(-1))
+        o_phi = torch.empty(N, dtype=torch.float64).pin_memory()
+        o_P = torch.empty(N, dtype=torch.float64).pin_memory()
+        o_ru = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_fields(h_phi, h_u, h_P)
+        sim.step(args.steps)
+        sim.macro(o_phi, o_P, o_ru)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+    total_lu = float(N) * args.steps * world
+    glups = total_lu / (ms * 1e-3) / 1e9
+    e2e_glups = total_lu / e2e_s / 1e9
+    peak, peak_kind = measured_peak()
+    alg_bytes = BYTES_PER_LU[args.store] * N
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic() if args.store == "f32" else None
+    line = {
+        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.store, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (638 MB of populations move per step, L2 is 129 MB)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "lbm::step_kernel<D3Q19>",
+                     "alg_bytes_per_launch": alg_bytes, "mean_launch_ms": per_launch_ms},
+        "clocks": clk,
+        "e2e": {"value": e2e_glups, "unit": "GLUPS",
+                "h2d_bytes_per_step": 5 * 8 * N / args.steps, "d2h_bytes_per_step": 5 * 8 * N / args.steps,
+                "note": "init_fields from pinned host phi,u,P + K steps + macro to pinned host, amortised per step"},
+        "gpu_launches": launches,
+        "diagnostics": {"sum_phi": diag["sum_phi"], "max_u": diag["max_u"], "nonfinite": diag["nonfinite"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, dt, nodes = oracle_glups(SHAPE[0], 3)
+        line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"3 oracle steps of the full 128^3 workload ({dt:.1f} s, numpy FP64, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

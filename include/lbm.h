@@ -1,0 +1,174 @@
+/*
+ * liblbm: GB300 (sm_103a) two-population phase-field lattice Boltzmann step.
+ *
+ * Model: Otomo, Zhang & Chen, "Improved phase-field-based lattice Boltzmann
+ * models with a filtered collision operator" (arXiv 1812.00118).
+ *   - h_i: Allen-Cahn interface LB with the theta counter-term (Section 2,
+ *     Eqs. 1-4), phi = sum_i h_i.
+ *   - g_i: pressure/momentum LB with forcing K_i (Eqs. 5-8), relaxation time
+ *     interpolated by Eq. 9, filtered collision (Eqs. 10-12), high-order
+ *     equilibrium correction delta f^eq (Section 3, Eq. 13).
+ *   - grad phi and lap phi by nearest-neighbour central differences (the
+ *     unnumbered stencils after Eq. 12).
+ *   - P = T sum g + (T rho_dif / 2) u.grad phi and rho u = sum c g +
+ *     (mu grad phi + F)/2 (text after Eq. 12).
+ *   - pull streaming on D2Q9 / D3Q19, periodic or halfway bounce-back walls.
+ *
+ * Conventions shared by every call:
+ *   - Lattice units (dx = dt = 1), T = 1/3.
+ *   - Fields are x-fastest: idx = x + nx*(y + ny*z); a D2Q9 grid has nz = 1.
+ *   - Vectors are component-major: v[d*N + idx], d = 0..dim-1, N = nx*ny*nz.
+ *   - Every field passed in or out is double precision, whatever the storage
+ *     type of the populations.
+ *   - Host pointers (on_device = 0) or device pointers (on_device = 1) are
+ *     accepted for fields; the caller owns them and the library never keeps
+ *     them past the call.
+ *   - The library owns its population buffers (two A/B sets of 2*Q*N values).
+ *   - All work is ordered on the CUDA stream given to lbm_create (NULL = the
+ *     legacy default stream).  Calls that return data to the host synchronise
+ *     that stream; lbm_step does not.
+ *   - Return value: LBM_OK (0) or a negative LBM_E* code; lbm_strerror gives
+ *     its text.  On an error nothing is launched and the state is unchanged,
+ *     except LBM_ECUDA, after which the context should be destroyed.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum lbm_bc { LBM_PERIODIC = 0, LBM_WALL = 1 };
+/* Population storage.  LBM_F64: FP64 storage and arithmetic.  LBM_F32: FP32
+ * storage and arithmetic.  LBM_F16S / LBM_BF16S: 16-bit storage of shifted
+ * values (h_i - w_i/2, (g_i - w_i P_ref/T) * g_scale) with FP32 arithmetic. */
+enum lbm_store { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* bad argument, size or parameter */
+    LBM_ENOMEM = -2,     /* device allocation failed */
+    LBM_ECUDA = -3,      /* a CUDA call failed */
+    LBM_EDIVERGED = -4,  /* a diagnostic found a non-finite value or |u| > 0.3 */
+    LBM_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    LBM_ENOTSUP = -6     /* combination not supported by this build */
+};
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
+
+/* Grid: nx, ny, nz >= 1 (nz == 1 for D2Q9).  bc[a] is the boundary type of
+ * both ends of axis a (0 = x, 1 = y, 2 = z).  A walled axis has halfway
+ * bounce-back walls half a spacing outside its first and last node; there
+ * the phi stencil mirrors the adjacent node (zero normal gradient). */
+typedef struct {
+    int nx, ny, nz;
+    int bc[3];
+} lbm_grid;
+
+/* Physical parameters (lattice units).
+ *   M       mobility (Eq. 1: tau_phi = M/T + 1/2), > 0
+ *   W       interface thickness (Eq. 4, Eq. 8), > 0
+ *   sigma   surface tension (Eq. 8), >= 0
+ *   rho_L   density of the light phase (phi = 0, "air"), > 0
+ *   rho_H   density of the heavy phase (phi = 1, "water"), > 0;
+ *           rho(phi) = rho_L + phi (rho_H - rho_L), rho_dif = rho_H - rho_L
+ *   nu_L, nu_H  kinematic viscosities; tau = nu/T + 1/2 each, and 1/tau_mix
+ *           interpolates 1/tau linearly in phi clipped to [0, 1] (Eq. 9)
+ *   g[3]    body acceleration; F_ex = rho g (force_mode 0) or
+ *           (rho - rho_bar) g (force_mode 1, rho_bar = mean density of the
+ *           initial phi, computed by lbm_init_fields / lbm_set_populations)
+ *   eps     regulariser of n = grad phi / (|grad phi| + eps) (Section 2), 1e-10
+ *   hocorr  1: add delta f^eq of Eq. 13 and read the velocity from
+ *           (rho + lap(rho)/4) u = sum c g + (mu grad phi + F)/2;
+ *           0: the uncorrected model of Section 2 (rho u = ...)
+ *   store   an lbm_store value
+ *   P_ref, g_scale  shift and scale of the 16-bit storage types (ignored
+ *           otherwise; g_scale = 0 means 1)
+ */
+typedef struct {
+    double M, W, sigma, rho_L, rho_H, nu_L, nu_H;
+    double g[3];
+    int force_mode;
+    double eps;
+    int hocorr;
+    int store;
+    double P_ref, g_scale;
+} lbm_params;
+
+/* Create a context: validates the grid and parameters, allocates the A/B
+ * population buffers on `cuda_stream` (a cudaStream_t, NULL for the default
+ * stream) of the current device.  Populations are zero until
+ * lbm_init_fields or lbm_set_populations.  `lattice` is an lbm_lattice.
+ * Errors: LBM_EINVAL (sizes < 1, nz != 1 for D2Q9, a periodic axis shorter
+ * than 1, tau <= 1/2, M <= 0, W <= 0, rho <= 0, unknown store),
+ * LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params,
+               void* cuda_stream, lbm_ctx** out);
+
+/* Initialise the populations from macroscopic fields (Section 4 set-ups
+ * start from (phi, u, P)): h = h^eq (Eq. 2) and g = g^eq (Eq. 6 with Eq. 7
+ * and Eq. 13) evaluated with the central-difference stencils of the given
+ * phi.  phi, P: N doubles; u: dim*N doubles (dim = 2 for D2Q9, 3 for
+ * D3Q19).  lbm_macro right after this call returns the same fields to
+ * rounding of the storage type.  Synchronises the stream. */
+int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const double* P,
+                    int on_device);
+
+/* Advance n >= 0 time steps: each step is one launch of the fused
+ * collide-and-pull-stream kernel (Eqs. 1-13) followed by a buffer swap.
+ * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of the current state (time t, before its collision):
+ * phi = sum h, P and rho u by the formulas after Eq. 12, where rho u is
+ * rho(phi) times the velocity the collision uses.  Any output pointer may be
+ * NULL.  Synchronises the stream. */
+int lbm_macro(lbm_ctx* ctx, double* phi, double* P, double* rho_u, int on_device);
+
+/* Pre-collision populations of the current state, converted to double:
+ * h and g are Q*N each, population-major (h[i*N + idx]) in the velocity
+ * order reported by lbm_lattice_info.  Checkpoint/resume: set(get(x))
+ * restores x exactly for every storage type.  Synchronises the stream. */
+int lbm_get_populations(lbm_ctx* ctx, double* h, double* g, int on_device);
+int lbm_set_populations(lbm_ctx* ctx, const double* h, const double* g, int on_device);
+
+/* FP64 diagnostics of the current state, reduced on the device in a fixed
+ * order (deterministic): out[0] = sum phi, out[1] = sum rho, out[2] = max |u|,
+ * out[3] = number of non-finite phi/u/P values.  Returns LBM_EDIVERGED
+ * (after filling out) if out[3] > 0 or out[2] > 0.3.  Synchronises. */
+int lbm_diagnostics(lbm_ctx* ctx, double out[4]);
+
+/* Laplace-law measurement (Section 4.1) in FP64 on the device:
+ * dP = <P>_{r < r_in} - <P>_{r > r_out}, r the minimum-image distance from
+ * centre[3] along periodic axes.  Synchronises. */
+int lbm_laplace(lbm_ctx* ctx, const double centre[3], double r_in, double r_out, double* dP);
+
+/* Velocity set of a lattice in the library's own order: Q, c[3*Q] (x, y, z
+ * components of each velocity, user axes: D2Q9 velocities lie in x-y) and
+ * w[Q].  Either array may be NULL. */
+int lbm_lattice_info(int lattice, int* Q, int* c, double* w);
+
+/* Number of kernel launches issued by the context since creation. */
+long long lbm_launch_count(const lbm_ctx* ctx);
+
+/* The CUDA stream of the context (as given to lbm_create). */
+void* lbm_stream(const lbm_ctx* ctx);
+
+/* Step kernel configuration: `tile` indexes the compiled CTA shapes of the
+ * lattice (D3Q19: 0 = 32x4, 1 = 32x8, 2 = 64x4, 3 = 32x2 threads in x-y;
+ * D2Q9: 0 = 128, 1 = 256, 2 = 64, 3 = 32 threads along x) and `lz` >= 1 is
+ * the number of planes along the march axis (z in 3-D, y in 2-D) one CTA
+ * processes.  Results do not depend on it (every shape computes the same
+ * arithmetic).  lbm_get_tile reports the current choice and its CTA shape.
+ * Errors: LBM_EINVAL for an unknown tile or lz < 1. */
+int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
+int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
+
+void lbm_destroy(lbm_ctx* ctx);
+const char* lbm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,551 @@
+// Device code of the phase-field LB step (Otomo, Zhang & Chen, arXiv 1812.00118).
+//
+// State convention: a population buffer holds the post-collision values
+// f*_i(x, t-1) at x; the pre-collision value of the current state is
+// obtained by pulling, f_i(x, t) = f*_i(x - c_i, t-1) (halfway bounce-back
+// f*_opp(i)(x, t-1) when x - c_i lies behind a wall).  So the step kernel
+// reads with a pull and writes locally; initialisation and set_populations
+// write with the inverse map ("push").
+//
+// Memory layout: population-major SoA, pop[i*N + x + NX*(y + NY*z)].
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int NX, NY, NZ;
+    long long N;
+    int wall[3];
+};
+
+// ---------------------------------------------------------------- parameters
+// Derived once on the host in double precision (lbm_api.cu).
+struct Phys {
+    double inv_tau_phi;    // 1 / (M/T + 1/2), Eq. 1
+    double theta_coef;     // (M/T) / W, Eq. 4
+    double beta, kappa;    // 48 sigma / W and 3 sigma W / 2, Eq. 8
+    double rho_L, rho_dif; // rho(phi) = rho_L + phi rho_dif
+    double om_L, om_dif;   // 1/tau_mix = om_L + clip(phi) om_dif, Eq. 9
+    double g[3];           // body acceleration, internal axes
+    int force_mode;        // 0: F = rho g, 1: F = (rho - rho_bar) g
+    double rho_bar;
+    double eps;            // n = grad phi / (|grad phi| + eps)
+    int hocorr;            // Eq. 13 and the corrected velocity definition
+    double h_shift;        // 16-bit storage keeps h_i - w_i h_shift
+    double g_shift;        // ... and (g_i - w_i g_shift) * g_scale
+    double g_scale, g_inv_scale;
+};
+
+// ---------------------------------------------------------------- storage
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
+
+template <int ST> struct Storage;
+template <> struct Storage<ST_F64> {
+    using S = double; using R = double;
+    static __device__ __forceinline__ R load(S v, R, R) { return v; }
+    static __device__ __forceinline__ S store(R v, R, R) { return v; }
+    static constexpr bool kShifted = false;
+};
+template <> struct Storage<ST_F32> {
+    using S = float; using R = float;
+    static __device__ __forceinline__ R load(S v, R, R) { return v; }
+    static __device__ __forceinline__ S store(R v, R, R) { return v; }
+    static constexpr bool kShifted = false;
+};
+template <> struct Storage<ST_F16S> {
+    using S = __half; using R = float;
+    // v = stored * inv_scale + shift
+    static __device__ __forceinline__ R load(S v, R shift, R inv_scale) {
+        return fmaf(__half2float(v), inv_scale, shift);
+    }
+    static __device__ __forceinline__ S store(R v, R shift, R scale) {
+        return __float2half_rn((v - shift) * scale);
+    }
+    static constexpr bool kShifted = true;
+};
+template <> struct Storage<ST_BF16S> {
+    using S = __nv_bfloat16; using R = float;
+    static __device__ __forceinline__ R load(S v, R shift, R inv_scale) {
+        return fmaf(__bfloat162float(v), inv_scale, shift);
+    }
+    static __device__ __forceinline__ S store(R v, R shift, R scale) {
+        return __float2bfloat16_rn((v - shift) * scale);
+    }
+    static constexpr bool kShifted = true;
+};
+
+// Conversion of the shift/scale constants into the arithmetic type.
+template <typename R>
+struct Shift {
+    R h_shift, g_shift, g_scale, g_inv_scale;
+    __device__ __forceinline__ explicit Shift(const Phys& p)
+        : h_shift((R)p.h_shift), g_shift((R)p.g_shift), g_scale((R)p.g_scale),
+          g_inv_scale((R)p.g_inv_scale) {}
+};
+
+__device__ __forceinline__ long long node_index(const Geom& G, int x, int y, int z) {
+    return (long long)x + (long long)G.NX * ((long long)y + (long long)G.NY * z);
+}
+
+// Source of the pull for direction (cx, cy, cz) at node (x, y, z): returns
+// the flat offset to read and sets *bounce when x - c lies behind a wall
+// (then the caller reads the opposite direction at the node itself).
+template <int CX, int CY, int CZ>
+__device__ __forceinline__ long long pull_source(const Geom& G, int x, int y, int z, bool* bounce) {
+    int sx = x - CX, sy = y - CY, sz = z - CZ;
+    bool bb = false;
+    if (CX != 0) {
+        if (sx < 0) { if (G.wall[0]) bb = true; else sx += G.NX; }
+        else if (sx >= G.NX) { if (G.wall[0]) bb = true; else sx -= G.NX; }
+    }
+    if (CY != 0) {
+        if (sy < 0) { if (G.wall[1]) bb = true; else sy += G.NY; }
+        else if (sy >= G.NY) { if (G.wall[1]) bb = true; else sy -= G.NY; }
+    }
+    if (CZ != 0) {
+        if (sz < 0) { if (G.wall[2]) bb = true; else sz += G.NZ; }
+        else if (sz >= G.NZ) { if (G.wall[2]) bb = true; else sz -= G.NZ; }
+    }
+    *bounce = bb;
+    return bb ? node_index(G, x, y, z) : node_index(G, sx, sy, sz);
+}
+
+// Pulled pre-collision population i at node (x, y, z) as stored (no conversion).
+template <int LAT, int I, typename S>
+__device__ __forceinline__ S pull(const S* __restrict__ pop, const Geom& G, int x, int y, int z) {
+    using L = Lattice<LAT>;
+    bool bb;
+    long long off = pull_source<L::cx[I], L::cy[I], L::cz[I]>(G, x, y, z, &bb);
+    const int dir = bb ? L::opp(I) : I;
+    return __ldg(pop + (long long)dir * G.N + off);
+}
+
+// Destination of the push that makes the pull of direction I at (x,y,z) return a value.
+template <int LAT, int I>
+__device__ __forceinline__ long long push_dest(const Geom& G, int x, int y, int z) {
+    using L = Lattice<LAT>;
+    bool bb;
+    long long off = pull_source<L::cx[I], L::cy[I], L::cz[I]>(G, x, y, z, &bb);
+    const int dir = bb ? L::opp(I) : I;
+    return (long long)dir * G.N + off;
+}
+
+// Coordinate along an axis for a stencil access: periodic wrap, or the
+// mirrored adjacent node behind a wall (zero normal gradient of phi).
+__device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
+    if (v < 0) return wall ? 0 : v + n;
+    if (v >= n) return wall ? n - 1 : v - n;
+    return v;
+}
+
+// compile-time loop helper
+template <int I, int N>
+struct Unroll {
+    template <typename F>
+    static __device__ __forceinline__ void run(F&& f) {
+        f(std::integral_constant<int, I>{});
+        Unroll<I + 1, N>::run(f);
+    }
+};
+template <int N>
+struct Unroll<N, N> {
+    template <typename F>
+    static __device__ __forceinline__ void run(F&&) {}
+};
+
+// ---------------------------------------------------------------- local physics
+// Everything a node needs after phi, grad phi and lap phi are known and the
+// moments of the pulled g are accumulated.  All arithmetic in R.
+template <typename R>
+struct NodeState {
+    R phi, gx, gy, gz, lap;
+    R rho, mu, Fx, Fy, Fz;
+    R ux, uy, uz, P;
+    R usq, ug, uF;
+    R pxx, pyy, pzz, pxy, pxz, pyz, tr3;   // Pi (Eq. 12, reading R3) and tr(Pi)/3
+    R omega;                               // 1 / tau_mix
+    R nx, ny, nz, theta;
+};
+
+// m0 = sum g, m1 = sum c g, m2 = sum c c g.  Follows the text after Eq. 12
+// for u and P (with the Eq. 13 velocity reading), Eq. 8 for mu, Eq. 9 for
+// tau_mix, Eq. 4 for theta.  Pi = m2 - sum c c g^eq with the closed form
+//   sum c c g^eq = rho u u + P I - (1/2) sum c c K,
+//   sum c c K = s [T(u grad + grad u) - u u (u.grad)] + rho_dif T I (u.grad)
+//             + [T(u F + F u) - u u (u.F)] / T,   s = rho_dif + mu / T,
+// which holds exactly on D2Q9 and D3Q19 (fourth-order isotropy); the
+// oracle sums sum c c (g - g^eq) term by term instead.
+template <typename R, bool THREE_D>
+__device__ __forceinline__ void node_state(NodeState<R>& s, const Phys& p, R m0, R mx, R my, R mz,
+                                           R mxx, R myy, R mzz, R mxy, R mxz, R myz) {
+    const R T = (R)(1.0 / 3.0);
+    const R rho_dif = (R)p.rho_dif;
+    s.rho = (R)p.rho_L + s.phi * rho_dif;
+    s.mu = (R)p.beta * s.phi * (s.phi - (R)1) * (s.phi - (R)0.5) - (R)p.kappa * s.lap;
+    const R fr = p.force_mode == 0 ? s.rho : s.rho - (R)p.rho_bar;
+    s.Fx = fr * (R)p.g[0];
+    s.Fy = fr * (R)p.g[1];
+    s.Fz = fr * (R)p.g[2];
+    const R rho_e = p.hocorr ? s.rho + (R)0.25 * rho_dif * s.lap : s.rho;
+    const R inv_rho_e = (R)1 / rho_e;
+    s.ux = (mx + (R)0.5 * (s.mu * s.gx + s.Fx)) * inv_rho_e;
+    s.uy = THREE_D ? (my + (R)0.5 * (s.mu * s.gy + s.Fy)) * inv_rho_e : (R)0;
+    s.uz = (mz + (R)0.5 * (s.mu * s.gz + s.Fz)) * inv_rho_e;
+    s.usq = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+    s.ug = s.ux * s.gx + s.uy * s.gy + s.uz * s.gz;
+    s.uF = s.ux * s.Fx + s.uy * s.Fy + s.uz * s.Fz;
+    s.P = T * m0 + (R)0.5 * T * rho_dif * s.ug;
+    // second moment of g^eq (closed form above), then Pi
+    const R sK = rho_dif + (R)3 * s.mu;
+    const R iso = rho_dif * T * s.ug;
+    auto ccK = [&](R ua, R ub, R ga, R gb, R Fa, R Fb, bool diag) {
+        R v = sK * (T * (ua * gb + ub * ga) - ua * ub * s.ug) + (T * (ua * Fb + Fa * ub) - ua * ub * s.uF) * (R)3;
+        return diag ? v + iso : v;
+    };
+    const R Pd = s.P;
+    s.pxx = mxx - (s.rho * s.ux * s.ux + Pd - (R)0.5 * ccK(s.ux, s.ux, s.gx, s.gx, s.Fx, s.Fx, true));
+    s.pzz = mzz - (s.rho * s.uz * s.uz + Pd - (R)0.5 * ccK(s.uz, s.uz, s.gz, s.gz, s.Fz, s.Fz, true));
+    s.pxz = mxz - (s.rho * s.ux * s.uz - (R)0.5 * ccK(s.ux, s.uz, s.gx, s.gz, s.Fx, s.Fz, false));
+    if (THREE_D) {
+        s.pyy = myy - (s.rho * s.uy * s.uy + Pd - (R)0.5 * ccK(s.uy, s.uy, s.gy, s.gy, s.Fy, s.Fy, true));
+        s.pxy = mxy - (s.rho * s.ux * s.uy - (R)0.5 * ccK(s.ux, s.uy, s.gx, s.gy, s.Fx, s.Fy, false));
+        s.pyz = myz - (s.rho * s.uy * s.uz - (R)0.5 * ccK(s.uy, s.uz, s.gy, s.gz, s.Fy, s.Fz, false));
+    } else {
+        s.pyy = s.pxy = s.pyz = (R)0;
+    }
+    s.tr3 = (s.pxx + s.pyy + s.pzz) * T;
+    const R pc = s.phi < (R)0 ? (R)0 : (s.phi > (R)1 ? (R)1 : s.phi);
+    s.omega = (R)p.om_L + pc * (R)p.om_dif;
+    const R gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
+    const R inv = (R)1 / (gmag + (R)p.eps);
+    s.nx = s.gx * inv;
+    s.ny = s.gy * inv;
+    s.nz = s.gz * inv;
+    const R d = s.phi - (R)0.5;
+    s.theta = (R)p.theta_coef * ((R)1 - (R)4 * d * d);
+}
+
+// Post-collision g*_i (Eq. 10 with G^eq = g^eq + K, Eqs. 6, 7, 11, 13):
+//   g*_i = rho Gamma_i + w_i (P/T - rho) + K_i/2 + delta f^eq_i
+//        + (1 - 1/tau_mix) w_i/(2T^2) (c_i c_i : Pi - T tr Pi)
+// and h*_i (Eq. 1 with Eq. 2).  Gamma_i is shared by both (Eq. 3).
+template <int LAT, int I, typename R>
+__device__ __forceinline__ void collide_dir(const NodeState<R>& s, const Phys& p, R h_in,
+                                            R* h_out, R* g_out) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
+    const R w = (R)L::w[I];
+    const R cu = (R)CX * s.ux + (R)CY * s.uy + (R)CZ * s.uz;
+    const R G = w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * s.usq);
+    const R cgr = (R)CX * s.gx + (R)CY * s.gy + (R)CZ * s.gz;
+    const R cF = (R)CX * s.Fx + (R)CY * s.Fy + (R)CZ * s.Fz;
+    const R K = ((G - w) * (R)p.rho_dif + (R)3 * G * s.mu) * (cgr - s.ug) + (R)3 * G * (cF - s.uF);
+    R ccPi = (R)(CX * CX) * s.pxx + (R)(CY * CY) * s.pyy + (R)(CZ * CZ) * s.pzz
+           + (R)(2 * CX * CY) * s.pxy + (R)(2 * CX * CZ) * s.pxz + (R)(2 * CY * CZ) * s.pyz;
+    R gs = s.rho * G + w * ((R)3 * s.P - s.rho) + (R)0.5 * K
+         + ((R)1 - s.omega) * w * (R)4.5 * (ccPi - s.tr3);
+    if (p.hocorr) gs += w * cu * (R)0.75 * (R)p.rho_dif * s.lap;
+    *g_out = gs;
+    const R cn = (R)CX * s.nx + (R)CY * s.ny + (R)CZ * s.nz;
+    const R heq = s.phi * G + s.theta * w * cn;
+    *h_out = h_in + (heq - h_in) * (R)p.inv_tau_phi;
+}
+
+// ---------------------------------------------------------------- fused step
+// One CTA owns a TX x TY column of nodes in the x-y plane and marches along
+// z over a chunk of LZ planes.  Per plane it (1) computes phi = sum of the
+// pulled h on the next plane for its tile plus a one-node halo ring into a
+// four-slot shared-memory ring, (2) collides the current plane with the CD
+// stencils read from the three resident planes.  With four slots one
+// barrier per plane suffices (the slot overwritten next was last read two
+// planes ago, before the previous barrier).
+template <int LAT, int ST, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Storage<ST>::S* __restrict__ gin,
+            typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
+            Geom G, Phys p, int LZ) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    using S = typename St::S;
+    using R = typename St::R;
+    constexpr int Q = L::Q;
+    constexpr int HY = L::kHasY ? 1 : 0;
+    constexpr int SX = TX + 2, SY = TY + 2 * HY;
+    __shared__ R phis[4][SY][SX];
+
+    const Shift<R> sh(p);
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * LZ;
+    const int z1 = min(z0 + LZ, G.NZ);
+    const R T = (R)(1.0 / 3.0);
+
+    // phi of plane zp (unwrapped; mapped by stencil_coord) into ring slot
+    auto fill = [&](int zp, int slot) {
+        const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
+        for (int k = tid; k < SX * SY; k += TX * TY) {
+            const int lx = k % SX, ly = k / SX;
+            const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
+            const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
+            R phi = (R)0;
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                phi += St::load(pull<LAT, i>(hin, G, xx, yy, zz), (R)W * sh.h_shift, (R)1);
+            });
+            phis[slot][ly][lx] = phi;
+        }
+    };
+
+    fill(z0 - 1, 0);
+    fill(z0, 1);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < G.NX && y < G.NY;
+
+    for (int z = z0; z < z1; ++z) {
+        const int j = z - z0;
+        fill(z + 1, (j + 2) & 3);
+        __syncthreads();
+        if (active) {
+            const int sm = j & 3, s0 = (j + 1) & 3, sp = (j + 2) & 3;
+            const int lx = tx + 1, ly = ty + HY;
+            NodeState<R> s;
+            s.phi = phis[s0][ly][lx];
+            // central differences (stencils after Eq. 12):
+            // grad phi = sum_i c_i w_i phi(x + c_i) / T  (the -c_i half of the
+            // paper's symmetric sum equals the +c_i half), lap = 2 sum w (phi_nb - phi) / T
+            R gx = 0, gy = 0, gz = 0, lap = 0;
+            Unroll<1, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+                const int slot = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
+                constexpr double W = L::w[i];
+                const R v = phis[slot][ly + CY][lx + CX];
+                const R wv = (R)W * v;
+                if (CX) gx += (R)CX * wv;
+                if (CY) gy += (R)CY * wv;
+                if (CZ) gz += (R)CZ * wv;
+                lap += (R)W * (v - s.phi);
+            });
+            s.gx = gx * (R)3;
+            s.gy = gy * (R)3;
+            s.gz = gz * (R)3;
+            s.lap = lap * (R)6;
+            // pulled g and its moments
+            R gv[Q];
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                gv[i] = St::load(pull<LAT, i>(gin, G, x, y, z), (R)W * sh.g_shift, sh.g_inv_scale);
+            });
+            R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+                const R v = gv[i];
+                m0 += v;
+                if (CX) { mx += (R)CX * v; mxx += v; }
+                if (CY) { my += (R)CY * v; myy += v; }
+                if (CZ) { mz += (R)CZ * v; mzz += v; }
+                if (CX * CY) mxy += (R)(CX * CY) * v;
+                if (CX * CZ) mxz += (R)(CX * CZ) * v;
+                if (CY * CZ) myz += (R)(CY * CZ) * v;
+            });
+            node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
+            (void)T;
+            const long long idx = node_index(G, x, y, z);
+            R hv[Q];
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                hv[i] = St::load(pull<LAT, i>(hin, G, x, y, z), (R)W * sh.h_shift, (R)1);
+            });
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                R hs, gs;
+                collide_dir<LAT, i, R>(s, p, hv[i], &hs, &gs);
+                constexpr double W = L::w[i];
+                hout[(long long)i * G.N + idx] = St::store(hs, (R)W * sh.h_shift, (R)1);
+                gout[(long long)i * G.N + idx] = St::store(gs, (R)W * sh.g_shift, sh.g_scale);
+            });
+        }
+    }
+}
+
+// ---------------------------------------------------------------- helper kernels
+// phi = sum_i of the pulled h at every node (double output).
+template <int LAT, int ST>
+__global__ void phi_kernel(const typename Storage<ST>::S* __restrict__ hin, Geom G, Phys p, double* phi) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX);
+    const int y = (int)((n / G.NX) % G.NY);
+    const int z = (int)(n / ((long long)G.NX * G.NY));
+    double acc = 0;
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr double W = L::w[i];
+        acc += (double)St::load(pull<LAT, i>(hin, G, x, y, z), (typename St::R)(W * p.h_shift),
+                                (typename St::R)1);
+    });
+    phi[n] = acc;
+}
+
+// CD stencils of a double phi field at node (x, y, z).
+template <int LAT>
+__device__ __forceinline__ void stencils(const double* __restrict__ phi, const Geom& G, int x, int y, int z,
+                                         double* gx, double* gy, double* gz, double* lap) {
+    using L = Lattice<LAT>;
+    const double f = phi[node_index(G, x, y, z)];
+    double ax = 0, ay = 0, az = 0, l = 0;
+    Unroll<1, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+        constexpr double W = L::w[i];
+        const int xx = stencil_coord(x + CX, G.NX, G.wall[0]);
+        const int yy = stencil_coord(y + CY, G.NY, G.wall[1]);
+        const int zz = stencil_coord(z + CZ, G.NZ, G.wall[2]);
+        const double v = phi[node_index(G, xx, yy, zz)];
+        ax += CX * W * v;
+        ay += CY * W * v;
+        az += CZ * W * v;
+        l += W * (v - f);
+    });
+    *gx = 3 * ax; *gy = 3 * ay; *gz = 3 * az; *lap = 6 * l;
+}
+
+// Macroscopic fields (phi given) in double: P and u (internal axes).
+template <int LAT, int ST>
+__global__ void macro_kernel(const typename Storage<ST>::S* __restrict__ gin, Geom G, Phys p,
+                             const double* __restrict__ phi, double* P, double* ux, double* uy, double* uz) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX);
+    const int y = (int)((n / G.NX) % G.NY);
+    const int z = (int)(n / ((long long)G.NX * G.NY));
+    NodeState<double> s;
+    s.phi = phi[n];
+    stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
+    double m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+        constexpr double W = L::w[i];
+        const double v = (double)St::load(pull<LAT, i>(gin, G, x, y, z), (typename St::R)(W * p.g_shift),
+                                          (typename St::R)p.g_inv_scale);
+        m0 += v;
+        mx += CX * v; my += CY * v; mz += CZ * v;
+    });
+    node_state<double, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
+    P[n] = s.P;
+    ux[n] = s.ux;
+    uy[n] = s.uy;
+    uz[n] = s.uz;
+}
+
+// Equilibrium initialisation (reading: h = h^eq, g = g^eq of the given
+// fields), written with the push map so that the next pull returns them.
+// phi: N doubles; u: 3 internal component arrays; P: N doubles.
+template <int LAT, int ST>
+__global__ void init_kernel(typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
+                            Geom G, Phys p, const double* __restrict__ phi, const double* __restrict__ ux,
+                            const double* __restrict__ uy, const double* __restrict__ uz,
+                            const double* __restrict__ P) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    using R = typename St::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX);
+    const int y = (int)((n / G.NX) % G.NY);
+    const int z = (int)(n / ((long long)G.NX * G.NY));
+    NodeState<double> s;
+    s.phi = phi[n];
+    stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
+    const double rho_dif = p.rho_dif;
+    s.rho = p.rho_L + s.phi * rho_dif;
+    s.mu = p.beta * s.phi * (s.phi - 1) * (s.phi - 0.5) - p.kappa * s.lap;
+    const double fr = p.force_mode == 0 ? s.rho : s.rho - p.rho_bar;
+    s.Fx = fr * p.g[0]; s.Fy = fr * p.g[1]; s.Fz = fr * p.g[2];
+    s.ux = ux[n]; s.uy = L::kHasY ? uy[n] : 0.0; s.uz = uz[n];
+    s.P = P[n];
+    s.usq = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+    s.ug = s.ux * s.gx + s.uy * s.gy + s.uz * s.gz;
+    s.uF = s.ux * s.Fx + s.uy * s.Fy + s.uz * s.Fz;
+    const double gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
+    s.nx = s.gx / (gmag + p.eps); s.ny = s.gy / (gmag + p.eps); s.nz = s.gz / (gmag + p.eps);
+    const double d = s.phi - 0.5;
+    s.theta = p.theta_coef * (1 - 4 * d * d);
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+        const double w = L::w[i];
+        const double cu = CX * s.ux + CY * s.uy + CZ * s.uz;
+        const double Gm = w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * s.usq);
+        const double cgr = CX * s.gx + CY * s.gy + CZ * s.gz;
+        const double cF = CX * s.Fx + CY * s.Fy + CZ * s.Fz;
+        const double K = ((Gm - w) * rho_dif + 3 * Gm * s.mu) * (cgr - s.ug) + 3 * Gm * (cF - s.uF);
+        double geq = s.rho * Gm + w * (3 * s.P - s.rho) - 0.5 * K;
+        if (p.hocorr) geq += w * cu * 0.75 * rho_dif * s.lap;
+        const double heq = s.phi * Gm + s.theta * w * (CX * s.nx + CY * s.ny + CZ * s.nz);
+        const long long dst = push_dest<LAT, i>(G, x, y, z);
+        hout[dst] = St::store((R)heq, (R)(w * p.h_shift), (R)1);
+        gout[dst] = St::store((R)geq, (R)(w * p.g_shift), (R)p.g_scale);
+    });
+}
+
+// Pre-collision populations out (double, population-major).
+template <int LAT, int ST>
+__global__ void get_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Storage<ST>::S* __restrict__ gin,
+                           Geom G, Phys p, double* h, double* g) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    using R = typename St::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX);
+    const int y = (int)((n / G.NX) % G.NY);
+    const int z = (int)(n / ((long long)G.NX * G.NY));
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr double W = L::w[i];
+        h[(long long)i * G.N + n] = (double)St::load(pull<LAT, i>(hin, G, x, y, z), (R)(W * p.h_shift), (R)1);
+        g[(long long)i * G.N + n] = (double)St::load(pull<LAT, i>(gin, G, x, y, z), (R)(W * p.g_shift),
+                                                     (R)p.g_inv_scale);
+    });
+}
+
+template <int LAT, int ST>
+__global__ void set_kernel(typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
+                           Geom G, Phys p, const double* __restrict__ h, const double* __restrict__ g) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    using R = typename St::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX);
+    const int y = (int)((n / G.NX) % G.NY);
+    const int z = (int)(n / ((long long)G.NX * G.NY));
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr double W = L::w[i];
+        const long long dst = push_dest<LAT, i>(G, x, y, z);
+        hout[dst] = St::store((R)h[(long long)i * G.N + n], (R)(W * p.h_shift), (R)1);
+        gout[dst] = St::store((R)g[(long long)i * G.N + n], (R)(W * p.g_shift), (R)p.g_scale);
+    });
+}
+
+}  // namespace lbm

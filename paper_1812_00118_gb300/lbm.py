@@ -1,0 +1,253 @@
+"""ctypes binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every call goes straight to the C-ABI of the CUDA library; no step of the
+method runs in Python.  Fields may be numpy float64 arrays (host) or torch
+float64 CUDA tensors (device); populations and fields are laid out as the
+header describes (x fastest, vectors component-major).
+
+If liblbm.so has not been built (``paper_1812_00118_gb300.build``), loading
+raises ``LbmLibraryMissing``: there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
+
+D2Q9, D3Q19 = 0, 1
+PERIODIC, WALL = 0, 1
+F64, F32, F16S, BF16S = 0, 1, 2, 3
+STORE_NAMES = {F64: "f64", F32: "f32", F16S: "f16s", BF16S: "bf16s"}
+
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+
+
+class LbmLibraryMissing(RuntimeError):
+    pass
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 3)]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double), ("W", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
+                ("nu_L", ctypes.c_double), ("nu_H", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("force_mode", ctypes.c_int),
+                ("eps", ctypes.c_double), ("hocorr", ctypes.c_int), ("store", ctypes.c_int),
+                ("P_ref", ctypes.c_double), ("g_scale", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every symbol include/lbm.h declares
+_VP, _DP, _IP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+SIGNATURES = [
+    ("lbm_create", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), _VP,
+                                  ctypes.POINTER(_VP)]),
+    ("lbm_init_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_macro", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    ("lbm_get_populations", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    ("lbm_set_populations", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    ("lbm_diagnostics", ctypes.c_int, [_VP, _DP]),
+    ("lbm_laplace", ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_double, _DP]),
+    ("lbm_lattice_info", ctypes.c_int, [ctypes.c_int, _IP, _IP, _DP]),
+    ("lbm_launch_count", ctypes.c_longlong, [_VP]),
+    ("lbm_stream", _VP, [_VP]),
+    ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
+    ("lbm_destroy", None, [_VP]),
+    ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+
+def load(path=LIB_PATH):
+    """Load liblbm.so and declare its signatures (idempotent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LbmLibraryMissing(
+            f"{path} not found: build it with `python -m paper_1812_00118_gb300.build` "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    return load().lbm_strerror(code).decode()
+
+
+def _check(code, what):
+    if code != OK:
+        raise LbmError(code, what)
+
+
+def lattice_info(lattice):
+    lib = load()
+    Q = ctypes.c_int()
+    c = (ctypes.c_int * 57)()
+    w = (ctypes.c_double * 19)()
+    _check(lib.lbm_lattice_info(lattice, ctypes.byref(Q), c, w), "lbm_lattice_info")
+    q = Q.value
+    return np.array(c[: 3 * q]).reshape(q, 3), np.array(w[:q])
+
+
+def make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1 / 6, nu_H=0.1 / 6,
+                g=(0.0, 0.0, 0.0), force_mode=0, eps=1e-10, hocorr=1, store=F32, P_ref=0.0, g_scale=0.0):
+    p = lbm_params()
+    p.M, p.W, p.sigma, p.rho_L, p.rho_H, p.nu_L, p.nu_H = M, W, sigma, rho_L, rho_H, nu_L, nu_H
+    for a in range(3):
+        p.g[a] = g[a] if a < len(g) else 0.0
+    p.force_mode, p.eps, p.hocorr, p.store = force_mode, eps, int(hocorr), store
+    p.P_ref, p.g_scale = P_ref, g_scale
+    return p
+
+
+def _ptr(a, writable=False):
+    """(pointer, on_device) for a numpy float64 C-contiguous array or a contiguous
+    torch float64 tensor (CUDA: device pointer; CPU, e.g. pinned: host pointer)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("fields must be C-contiguous float64 arrays")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("output array is read-only")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    if not (a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()):
+        raise ValueError("tensor fields must be contiguous float64")
+    return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+class Simulation:
+    """One LB domain on the current CUDA device (owns an lbm_ctx).
+
+    shape is the user grid (nx, ny) for D2Q9 or (nx, ny, nz) for D3Q19;
+    bc is a per-axis tuple of PERIODIC / WALL."""
+
+    def __init__(self, lattice, shape, params, bc=(PERIODIC, PERIODIC, PERIODIC), stream=None):
+        lib = load()
+        self.lattice = lattice
+        self.dim = 2 if lattice == D2Q9 else 3
+        nx, ny = shape[0], shape[1]
+        nz = shape[2] if self.dim == 3 else 1
+        self.shape = (nx, ny, nz)
+        self.N = nx * ny * nz
+        g = lbm_grid()
+        g.nx, g.ny, g.nz = nx, ny, nz
+        for a in range(3):
+            g.bc[a] = bc[a] if a < len(bc) else PERIODIC
+        self.params = params
+        self.Q = 9 if lattice == D2Q9 else 19
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        _check(lib.lbm_create(ctypes.byref(g), lattice, ctypes.byref(params), ctypes.c_void_p(stream),
+                              ctypes.byref(ctx)), "lbm_create")
+        self._ctx = ctx
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            load().lbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C-ABI calls
+    def init_fields(self, phi, u, P):
+        (pp, d0), (pu, d1), (pP, d2) = _ptr(phi), _ptr(u), _ptr(P)
+        if not (d0 == d1 == d2):
+            raise ValueError("phi, u and P must all be host or all device")
+        _check(load().lbm_init_fields(self._ctx, pp, pu, pP, d0), "lbm_init_fields")
+
+    def step(self, n=1):
+        _check(load().lbm_step(self._ctx, int(n)), "lbm_step")
+
+    def macro(self, phi=None, P=None, rho_u=None):
+        """Fill the given outputs (host arrays or device tensors); allocate host
+        arrays when none is given and return (phi, P, rho_u)."""
+        if phi is None and P is None and rho_u is None:
+            phi = np.empty(self.N)
+            P = np.empty(self.N)
+            rho_u = np.empty(self.dim * self.N)
+        ptrs, dev = [], None
+        for a in (phi, P, rho_u):
+            if a is None:
+                ptrs.append(None)
+                continue
+            p, d = _ptr(a, writable=True)
+            dev = d if dev is None else dev
+            if d != dev:
+                raise ValueError("outputs must all be host or all device")
+            ptrs.append(p)
+        _check(load().lbm_macro(self._ctx, *ptrs, dev or 0), "lbm_macro")
+        return phi, P, rho_u
+
+    def get_populations(self, h=None, g=None):
+        if h is None:
+            h = np.empty(self.Q * self.N)
+            g = np.empty(self.Q * self.N)
+        (ph, d0), (pg, d1) = _ptr(h, True), _ptr(g, True)
+        _check(load().lbm_get_populations(self._ctx, ph, pg, d0), "lbm_get_populations")
+        return h, g
+
+    def set_populations(self, h, g):
+        (ph, d0), (pg, d1) = _ptr(h), _ptr(g)
+        _check(load().lbm_set_populations(self._ctx, ph, pg, d0), "lbm_set_populations")
+
+    def diagnostics(self, raise_on_divergence=True):
+        out = (ctypes.c_double * 4)()
+        rc = load().lbm_diagnostics(self._ctx, out)
+        if rc not in (OK, EDIVERGED) or (rc == EDIVERGED and raise_on_divergence):
+            _check(rc, "lbm_diagnostics")
+        return dict(sum_phi=out[0], sum_rho=out[1], max_u=out[2], nonfinite=out[3], status=rc)
+
+    def laplace(self, centre, r_in, r_out):
+        c = (ctypes.c_double * 3)(*[float(v) for v in (list(centre) + [0.0] * 3)[:3]])
+        dP = ctypes.c_double()
+        _check(load().lbm_laplace(self._ctx, c, r_in, r_out, ctypes.byref(dP)), "lbm_laplace")
+        return dP.value
+
+    def launch_count(self):
+        return load().lbm_launch_count(self._ctx)
+
+    def set_tile(self, tile, lz):
+        _check(load().lbm_set_tile(self._ctx, tile, lz), "lbm_set_tile")
+
+    def get_tile(self):
+        t, lz, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().lbm_get_tile(self._ctx, ctypes.byref(t), ctypes.byref(lz), ctypes.byref(tx),
+                                   ctypes.byref(ty)), "lbm_get_tile")
+        return t.value, lz.value, tx.value, ty.value
+
+    @property
+    def ctx(self):
+        return self._ctx

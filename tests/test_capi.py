@@ -1,0 +1,69 @@
+"""Host-side checks of the C-ABI (no GPU needed): the library builds, loads,
+exports every function include/*.h declares, and reports a velocity set
+equal to the oracle's up to ordering."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1812_00118_gb300 import build, lbm
+    build.build()
+    return lbm.load()
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm\w*)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_symbols_exported(lib):
+    from paper_1812_00118_gb300 import lbm
+    names = declared_functions()
+    assert len(names) >= 14
+    bound = {n for n, _, _ in lbm.SIGNATURES}
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared but not exported"
+        assert n in bound, f"{n} has no Python binding"
+
+
+@pytest.mark.parametrize("lat_id,olat", [(0, L.D2Q9), (1, L.D3Q19)], ids=["D2Q9", "D3Q19"])
+def test_lattice_info_matches_oracle(lib, lat_id, olat):
+    from paper_1812_00118_gb300 import lbm
+    c, w = lbm.lattice_info(lat_id)
+    assert len(w) == olat.Q
+    ours = {tuple(v): wv for v, wv in zip(c.tolist(), w)}
+    theirs = {tuple(int(a) for a in v): wv for v, wv in zip(olat.c, olat.w)}
+    assert ours.keys() == theirs.keys()
+    for k in ours:
+        assert ours[k] == pytest.approx(theirs[k], abs=1e-16)
+
+
+def test_strerror(lib):
+    from paper_1812_00118_gb300 import lbm
+    assert lbm.strerror(0) == "ok"
+    assert "invalid" in lbm.strerror(-1)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1812_00118_gb300 import lbm
+    saved = lbm._lib
+    lbm._lib = None
+    try:
+        with pytest.raises(lbm.LbmLibraryMissing):
+            lbm.load(str(tmp_path / "nope.so"))
+    finally:
+        lbm._lib = saved

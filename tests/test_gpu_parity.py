@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle, element
+by element, on seeded inputs (paper_1812_00118_gb300.inputs).
+
+Tolerances (derived from the arithmetic):
+* FP64 storage/arithmetic: the GPU and the oracle differ only in the order
+  of floating-point operations (the kernel forms Pi from closed-form
+  moments, the stencils from one-sided sums), so one step agrees to a few
+  ulp of the largest population: 1e-13 absolute on populations of O(1);
+  after hundreds of steps 1e-10 normwise.
+* FP32 storage/arithmetic: 1e-5 normwise on phi, u and P after 1000 steps
+  (the stated accuracy target), 2e-6 after one step.
+"""
+import numpy as np
+import pytest
+
+from oracle import pflbm as O
+from paper_1812_00118_gb300 import inputs as I
+from parity_helpers import (lib_to_oracle_pops, normwise, oracle_lattice, oracle_macro_flat,
+                            oracle_params, oracle_to_lib_pops, user_velocity)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_00118_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def make_case(L, lat_id, shape_zyx, bc, store, seed=3, drop=False, **kw):
+    """Seeded smooth random (or drop) fields; returns (sim, oracle h, g, lat, p)."""
+    nz, ny, nx = shape_zyx
+    if drop:
+        c = (nx / 2, ny / 2, nz / 2 if lat_id == 1 else 0)
+        R = min(nx, ny) / 4
+        phi, u, P = I.sphere(shape_zyx, c, R, kw.pop("W_init", 4.0), drop=True)
+    else:
+        phi, u, P = I.smooth_random(shape_zyx, seed, dim=2 if lat_id == 0 else 3)
+    base = dict(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1, nu_H=0.02,
+                g=(1e-5, -2e-5, 3e-5 if lat_id == 1 else 0.0), store=store)
+    base.update(kw)
+    prm = L.make_params(**base)
+    user_shape = (nx, ny) if lat_id == 0 else (nx, ny, nz)
+    sim = L.Simulation(lat_id, user_shape, prm, bc=bc)
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, lat_id),
+                    np.ascontiguousarray(P.reshape(-1)))
+    lat = oracle_lattice(lat_id)
+    p = oracle_params(prm, bc, lat_id)
+    h, g = O.init_populations(phi, u, P, lat, p)
+    return sim, h, g, lat, p, (phi, u, P)
+
+
+CASES = [
+    (1, (13, 21, 37), (0, 0, 0)),      # D3Q19 periodic, ragged in x and y, several z chunks
+    (1, (19, 11, 35), (1, 0, 1)),      # D3Q19 walls in x and z
+    (1, (5, 9, 70), (0, 1, 0)),        # D3Q19 wall in y, x spans three 32-wide tiles
+    (0, (1, 47, 133), (0, 0)),         # D2Q9 periodic, ragged
+    (0, (1, 40, 70), (1, 1)),          # D2Q9 channel with walls on both axes
+]
+IDS = ["d3q19-periodic", "d3q19-xzwall", "d3q19-ywall", "d2q9-periodic", "d2q9-walls"]
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", CASES, ids=IDS)
+def test_init_macro_roundtrip(lbm, lat_id, shape, bc):
+    sim, h, g, lat, p, (phi, u, P) = make_case(lbm, lat_id, shape, bc, lbm.F64)
+    f, Pg, ru = sim.macro()
+    np.testing.assert_allclose(f, phi.reshape(-1), atol=1e-14)
+    np.testing.assert_allclose(Pg, P.reshape(-1), atol=1e-15)
+    rho = p.rho_L + phi.reshape(-1) * p.rho_dif
+    dim = 2 if lat_id == 0 else 3
+    np.testing.assert_allclose(ru, (rho[None] * u[:dim].reshape(dim, -1)).reshape(-1), atol=1e-15)
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", CASES, ids=IDS)
+def test_one_step_populations_f64(lbm, lat_id, shape, bc):
+    sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F64)
+    # start from populations with off-equilibrium content, set through the C-ABI
+    rng = np.random.default_rng(5)
+    h = h + rng.normal(scale=1e-3, size=h.shape)
+    g = g + rng.normal(scale=1e-5, size=g.shape)
+    sim.set_populations(oracle_to_lib_pops(h, lat_id), oracle_to_lib_pops(g, lat_id))
+    sim.step(1)
+    hg, gg = sim.get_populations()
+    h1, g1 = O.step(h, g, lat, p)
+    np.testing.assert_allclose(lib_to_oracle_pops(hg, lat_id, shape), h1, atol=1e-13, rtol=0)
+    np.testing.assert_allclose(lib_to_oracle_pops(gg, lat_id, shape), g1, atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", CASES, ids=IDS)
+def test_many_steps_f64(lbm, lat_id, shape, bc):
+    sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F64)
+    sim.step(100)
+    h, g = O.run(h, g, lat, p, 100)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+    assert normwise(f, fo) < 1e-10
+    assert normwise(Pg, Po) < 1e-10
+    assert normwise(ru, ruo) < 1e-10
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", CASES, ids=IDS)
+def test_one_step_f32(lbm, lat_id, shape, bc):
+    sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    sim.step(1)
+    h, g = O.step(h, g, lat, p)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+    assert normwise(f, fo) < 2e-6
+    assert normwise(Pg, Po) < 2e-6
+    assert normwise(ru, ruo) < 2e-6
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [(1, (12, 14, 20), (0, 0, 0)), (0, (1, 48, 50), (0, 1))],
+                         ids=["d3q19-drop", "d2q9-drop-walls"])
+def test_1000_steps_f32_drop(lbm, lat_id, shape, bc):
+    """FP32 storage after 1000 steps of a drop at density ratio 1000 with a body
+    force: phi, u and P within 1e-5 normwise of the FP64 oracle."""
+    sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32, drop=True, W_init=3.0, W=3.0,
+                                     g=(2e-6, 1e-6, 0.0), nu_L=0.1, nu_H=0.05)
+    sim.step(1000)
+    h, g = O.run(h, g, lat, p, 1000)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+    assert normwise(f, fo) < 1e-5
+    assert normwise(Pg, Po) < 1e-5
+    assert normwise(ru, ruo) < 1e-5
+
+
+def test_config1_static_droplet_f64(lbm):
+    """D2Q9 64x64 periodic FP64, drop R = 16, W = 4, rho ratio 1000, M = 0.1,
+    tau = 0.55 in both phases, sigma = 0.01, 2000 steps: element-wise parity
+    with the oracle, exact phi conservation, and the Laplace jump equal to the
+    oracle's."""
+    prm = lbm.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.05 / 3, nu_H=0.05 / 3,
+                          store=lbm.F64)
+    shape = (1, 64, 64)
+    phi, u, P = I.sphere(shape, (32, 32, 0), 16, 4.0, drop=True)
+    sim = lbm.Simulation(lbm.D2Q9, (64, 64), prm, bc=(0, 0))
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, 0), np.ascontiguousarray(P.reshape(-1)))
+    d0 = sim.diagnostics()
+    sim.step(2000)
+    d1 = sim.diagnostics()
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-12 * d0["sum_phi"]
+    lat = oracle_lattice(0)
+    p = oracle_params(prm, (0, 0), 0)
+    h, g = O.init_populations(phi, u, P, lat, p)
+    h, g = O.run(h, g, lat, p, 2000)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
+    assert normwise(f, fo) < 1e-10
+    assert normwise(Pg, Po) < 1e-10
+    assert normwise(ru, ruo) < 1e-10
+    from oracle import diagnostics as D
+    R = D.effective_radius(fo.reshape(shape), 2, True)
+    dP_o = D.laplace_jump(Po.reshape(shape), (32, 32, 0), R, 4.0)
+    dP_g = sim.laplace((32, 32), R - 8.0, R + 8.0)
+    assert dP_g == pytest.approx(dP_o, rel=1e-9)
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[3]], ids=["d3q19", "d2q9"])
+def test_tile_shapes_identical(lbm, lat_id, shape, bc):
+    """Every compiled CTA shape and z-chunk length gives bit-identical results."""
+    ref = None
+    for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100)):
+        sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+        sim.set_tile(tile, lz)
+        sim.step(7)
+        hg, gg = sim.get_populations()
+        if ref is None:
+            ref = (hg, gg)
+        else:
+            assert np.array_equal(hg, ref[0]) and np.array_equal(gg, ref[1]), (tile, lz)
+
+
+@pytest.mark.parametrize("store", ["F64", "F32"])
+def test_checkpoint_resume_bit_exact(lbm, store):
+    st = getattr(lbm, store)
+    simA, *_ = make_case(lbm, 1, (10, 12, 14), (0, 1, 0), st)
+    simA.step(20)
+    hA, gA = simA.get_populations()
+    simB, *_ = make_case(lbm, 1, (10, 12, 14), (0, 1, 0), st)
+    simB.step(10)
+    h, g = simB.get_populations()
+    simB.set_populations(h, g)
+    simB.step(10)
+    hB, gB = simB.get_populations()
+    assert np.array_equal(hA, hB) and np.array_equal(gA, gB)
+
+
+def test_conservation_f32_long(lbm):
+    """FP32: sum phi drifts only by rounding (relative 1e-6 over 2000 steps)."""
+    sim, *_ = make_case(lbm, 1, (24, 24, 24), (0, 0, 0), lbm.F32, drop=True)
+    d0 = sim.diagnostics()
+    sim.step(2000)
+    d1 = sim.diagnostics()
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-6 * d0["sum_phi"]
+    assert d1["nonfinite"] == 0
+
+
+def test_device_tensors_roundtrip(lbm):
+    """Fields passed as torch CUDA tensors (device pointers) give the same
+    result as host arrays."""
+    import torch
+    shape = (9, 10, 11)
+    phi, u, P = I.smooth_random(shape, 4)
+    prm = lbm.make_params(store=lbm.F64)
+    a = lbm.Simulation(lbm.D3Q19, (11, 10, 9), prm)
+    a.init_fields(phi.reshape(-1).copy(), user_velocity(u, 1), P.reshape(-1).copy())
+    b = lbm.Simulation(lbm.D3Q19, (11, 10, 9), prm)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    b.init_fields(dev(phi.reshape(-1)), dev(user_velocity(u, 1)), dev(P.reshape(-1)))
+    a.step(5)
+    b.step(5)
+    fa, Pa, ua = a.macro()
+    fb = torch.empty(a.N, dtype=torch.float64, device="cuda")
+    Pb = torch.empty_like(fb)
+    ub = torch.empty(3 * a.N, dtype=torch.float64, device="cuda")
+    b.macro(fb, Pb, ub)
+    assert np.array_equal(fa, fb.cpu().numpy())
+    assert np.array_equal(Pa, Pb.cpu().numpy())
+    assert np.array_equal(ua, ub.cpu().numpy())
+
+
+def test_invalid_arguments(lbm):
+    bad = lbm.make_params(M=-1.0)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Simulation(lbm.D3Q19, (8, 8, 8), bad)
+    assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.Simulation(lbm.D2Q9, (0, 8), lbm.make_params())
