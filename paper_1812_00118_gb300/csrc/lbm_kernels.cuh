@@ -139,11 +139,14 @@ __device__ __forceinline__ long long push_dest(const Geom& G, int x, int y, int 
 }
 
 // Coordinate along an axis for a stencil access: periodic wrap, or the
-// mirrored adjacent node behind a wall (zero normal gradient of phi).
+// mirrored adjacent node behind a wall (zero normal gradient of phi).  The
+// halo of a CTA tile wider than the grid can lie more than one period out,
+// so the wrap is a full modulo; the result is always in [0, n).
 __device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
-    if (v < 0) return wall ? 0 : v + n;
-    if (v >= n) return wall ? n - 1 : v - n;
-    return v;
+    if (v >= 0 && v < n) return v;
+    if (wall) return v < 0 ? 0 : n - 1;
+    const int r = v % n;
+    return r < 0 ? r + n : r;
 }
 
 // compile-time loop helper
