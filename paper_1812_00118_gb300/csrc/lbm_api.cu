@@ -326,8 +326,9 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
         c->K = table_for(1, params->store);
         c->lz = 16;
     }
+    c->G.NXY = c->G.NX * c->G.NY;
     c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
-    if (!c->K) { delete c; return LBM_EINVAL; }
+    if (!c->K || c->G.N >= (1LL << 31)) { delete c; return LBM_EINVAL; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
     const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.N;
     for (int b = 0; b < 2; ++b) {

@@ -6,14 +6,14 @@
 
 namespace lbm {
 
-template <int LAT, int ST, int TX, int TY>
+template <int LAT, int ST, int TX, int TY, int MINB>
 cudaError_t launch_step_tile(const void* hin, const void* gin, void* hout, void* gout, const Geom& G,
                              const Phys& p, int lz, cudaStream_t s) {
     using S = typename Storage<ST>::S;
     dim3 block(TX, TY);
     dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + lz - 1) / lz);
-    step_kernel<LAT, ST, TX, TY><<<grid, block, 0, s>>>((const S*)hin, (const S*)gin, (S*)hout, (S*)gout, G,
-                                                        p, lz);
+    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, s>>>((const S*)hin, (const S*)gin, (S*)hout, (S*)gout, G,
+                                                        phys_as<typename Storage<ST>::R>(p), lz);
     return cudaGetLastError();
 }
 
@@ -28,7 +28,8 @@ struct Launchers {
     }
     static cudaError_t macro(const void* gin, const Geom& G, const Phys& p, const double* phi, double* P,
                              double* ux, double* uy, double* uz, cudaStream_t s) {
-        macro_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>((const S*)gin, G, p, phi, P, ux, uy, uz);
+        macro_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>((const S*)gin, G, phys_as<double>(p), phi, P,
+                                                                    ux, uy, uz);
         return cudaGetLastError();
     }
     static cudaError_t init(void* hout, void* gout, const Geom& G, const Phys& p, const double* phi,

@@ -22,7 +22,8 @@ namespace lbm {
 // ---------------------------------------------------------------- geometry
 struct Geom {
     int NX, NY, NZ;
-    long long N;
+    int NXY;          // NX * NY
+    long long N;      // NX * NY * NZ (< 2^31, checked by lbm_create)
     int wall[3];
 };
 
@@ -43,6 +44,32 @@ struct Phys {
     double g_shift;        // ... and (g_i - w_i g_shift) * g_scale
     double g_scale, g_inv_scale;
 };
+
+// The same parameters in the arithmetic type of a kernel, converted once on
+// the host so that FP32 kernels execute no FP64 conversions.
+template <typename R>
+struct PhysT {
+    R inv_tau_phi, theta_coef, beta, kappa, rho_L, rho_dif, om_L, om_dif;
+    R g[3];
+    R rho_bar, eps;
+    R h_shift, g_shift, g_scale, g_inv_scale;
+    int force_mode, hocorr;
+};
+
+template <typename R>
+inline PhysT<R> phys_as(const Phys& p) {
+    PhysT<R> q;
+    q.inv_tau_phi = (R)p.inv_tau_phi; q.theta_coef = (R)p.theta_coef;
+    q.beta = (R)p.beta; q.kappa = (R)p.kappa;
+    q.rho_L = (R)p.rho_L; q.rho_dif = (R)p.rho_dif;
+    q.om_L = (R)p.om_L; q.om_dif = (R)p.om_dif;
+    for (int a = 0; a < 3; ++a) q.g[a] = (R)p.g[a];
+    q.rho_bar = (R)p.rho_bar; q.eps = (R)p.eps;
+    q.h_shift = (R)p.h_shift; q.g_shift = (R)p.g_shift;
+    q.g_scale = (R)p.g_scale; q.g_inv_scale = (R)p.g_inv_scale;
+    q.force_mode = p.force_mode; q.hocorr = p.hocorr;
+    return q;
+}
 
 // ---------------------------------------------------------------- storage
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
@@ -82,14 +109,24 @@ template <> struct Storage<ST_BF16S> {
     static constexpr bool kShifted = true;
 };
 
-// Conversion of the shift/scale constants into the arithmetic type.
-template <typename R>
-struct Shift {
-    R h_shift, g_shift, g_scale, g_inv_scale;
-    __device__ __forceinline__ explicit Shift(const Phys& p)
-        : h_shift((R)p.h_shift), g_shift((R)p.g_shift), g_scale((R)p.g_scale),
-          g_inv_scale((R)p.g_inv_scale) {}
-};
+// Read-only loads: default caching for h (re-read by neighbouring threads of
+// the same CTA), L1::no_allocate for g (read once) so g does not evict h.
+template <typename S> __device__ __forceinline__ S ld_keep(const S* p) { return __ldg(p); }
+template <typename S> __device__ __forceinline__ S ld_stream(const S* p);
+template <> __device__ __forceinline__ double ld_stream<double>(const double* p) {
+    double v; asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p)); return v;
+}
+template <> __device__ __forceinline__ float ld_stream<float>(const float* p) {
+    float v; asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p)); return v;
+}
+template <> __device__ __forceinline__ __half ld_stream<__half>(const __half* p) {
+    unsigned short v; asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_half(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(const __nv_bfloat16* p) {
+    unsigned short v; asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_bfloat16(v);
+}
 
 __device__ __forceinline__ long long node_index(const Geom& G, int x, int y, int z) {
     return (long long)x + (long long)G.NX * ((long long)y + (long long)G.NY * z);
@@ -126,6 +163,32 @@ __device__ __forceinline__ S pull(const S* __restrict__ pop, const Geom& G, int 
     long long off = pull_source<L::cx[I], L::cy[I], L::cz[I]>(G, x, y, z, &bb);
     const int dir = bb ? L::opp(I) : I;
     return __ldg(pop + (long long)dir * G.N + off);
+}
+
+// Pull with a fast path: for a node at least one spacing away from every
+// face (`interior`) the source is base - (c . strides) in the same
+// direction; otherwise the general wrap / bounce-back rule above.
+template <int LAT, int I, bool STREAM, typename S>
+__device__ __forceinline__ S pull_at(const S* __restrict__ pop, const Geom& G, int x, int y, int z, int base,
+                                     bool interior) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
+    int off, dir = I;
+    if (interior) {
+        off = base - CX - CY * G.NX - CZ * G.NXY;
+    } else {
+        bool bb;
+        off = (int)pull_source<CX, CY, CZ>(G, x, y, z, &bb);
+        if (bb) dir = L::opp(I);
+    }
+    const S* p = pop + (long long)dir * G.N + off;
+    return STREAM ? ld_stream(p) : ld_keep(p);
+}
+
+template <int LAT>
+__device__ __forceinline__ bool is_interior(const Geom& G, int x, int y, int z) {
+    return x >= 1 && x <= G.NX - 2 && z >= 1 && z <= G.NZ - 2 &&
+           (!Lattice<LAT>::kHasY || (y >= 1 && y <= G.NY - 2));
 }
 
 // Destination of the push that makes the pull of direction I at (x,y,z) return a value.
@@ -187,7 +250,7 @@ struct NodeState {
 // which holds exactly on D2Q9 and D3Q19 (fourth-order isotropy); the
 // oracle sums sum c c (g - g^eq) term by term instead.
 template <typename R, bool THREE_D>
-__device__ __forceinline__ void node_state(NodeState<R>& s, const Phys& p, R m0, R mx, R my, R mz,
+__device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R m0, R mx, R my, R mz,
                                            R mxx, R myy, R mzz, R mxy, R mxz, R myz) {
     const R T = (R)(1.0 / 3.0);
     const R rho_dif = (R)p.rho_dif;
@@ -241,7 +304,7 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const Phys& p, R m0,
 //        + (1 - 1/tau_mix) w_i/(2T^2) (c_i c_i : Pi - T tr Pi)
 // and h*_i (Eq. 1 with Eq. 2).  Gamma_i is shared by both (Eq. 3).
 template <int LAT, int I, typename R>
-__device__ __forceinline__ void collide_dir(const NodeState<R>& s, const Phys& p, R h_in,
+__device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R>& p, R h_in,
                                             R* h_out, R* g_out) {
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
@@ -264,17 +327,21 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const Phys& p
 
 // ---------------------------------------------------------------- fused step
 // One CTA owns a TX x TY column of nodes in the x-y plane and marches along
-// z over a chunk of LZ planes.  Per plane it (1) computes phi = sum of the
-// pulled h on the next plane for its tile plus a one-node halo ring into a
-// four-slot shared-memory ring, (2) collides the current plane with the CD
-// stencils read from the three resident planes.  With four slots one
-// barrier per plane suffices (the slot overwritten next was last read two
-// planes ago, before the previous barrier).
-template <int LAT, int ST, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+// z over a chunk of LZ planes.  Per plane it
+//   (1) issues the pulled g loads of its own node on the current plane and,
+//       in the same latency window, computes phi = sum of the pulled h on the
+//       NEXT plane for the tile plus a one-node halo ring into a four-slot
+//       shared-memory ring (phi at a neighbour needs that neighbour's pulled
+//       h, so the ring is recomputed; its h reads hit L2),
+//   (2) after one barrier, forms the CD stencils from the three resident
+//       planes, the moments of g, the local state, and writes h*, g*.
+// Four slots make one barrier per plane enough: the slot written in
+// iteration j+2 was last read in iteration j, before iteration j+1's barrier.
+template <int LAT, int ST, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
 step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Storage<ST>::S* __restrict__ gin,
             typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
-            Geom G, Phys p, int LZ) {
+            Geom G, PhysT<typename Storage<ST>::R> p, int LZ) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using S = typename St::S;
@@ -284,12 +351,10 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
     constexpr int SX = TX + 2, SY = TY + 2 * HY;
     __shared__ R phis[4][SY][SX];
 
-    const Shift<R> sh(p);
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * LZ;
     const int z1 = min(z0 + LZ, G.NZ);
-    const R T = (R)(1.0 / 3.0);
 
     // phi of plane zp (unwrapped; mapped by stencil_coord) into ring slot
     auto fill = [&](int zp, int slot) {
@@ -298,11 +363,13 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             const int lx = k % SX, ly = k / SX;
             const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
             const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
+            const int base = xx + G.NX * yy + G.NXY * zz;
+            const bool in = is_interior<LAT>(G, xx, yy, zz);
             R phi = (R)0;
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                phi += St::load(pull<LAT, i>(hin, G, xx, yy, zz), (R)W * sh.h_shift, (R)1);
+                phi += St::load(pull_at<LAT, i, false>(hin, G, xx, yy, zz, base, in), (R)W * p.h_shift, (R)1);
             });
             phis[slot][ly][lx] = phi;
         }
@@ -316,7 +383,34 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
 
     for (int z = z0; z < z1; ++z) {
         const int j = z - z0;
+        const int base = x + G.NX * y + G.NXY * z;
+        const bool in = is_interior<LAT>(G, x, y, z);
+        // (1) g of this node (streamed, overlapping the phi fill's h loads)
+        R gv[Q];
+        if (active) {
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                gv[i] = St::load(pull_at<LAT, i, true>(gin, G, x, y, z, base, in), (R)W * p.g_shift,
+                                 p.g_inv_scale);
+            });
+        }
         fill(z + 1, (j + 2) & 3);
+        R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+        if (active) {
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+                const R v = gv[i];
+                m0 += v;
+                if (CX) { mx += (R)CX * v; mxx += v; }
+                if (CY) { my += (R)CY * v; myy += v; }
+                if (CZ) { mz += (R)CZ * v; mzz += v; }
+                if (CX * CY) mxy += (R)(CX * CY) * v;
+                if (CX * CZ) mxz += (R)(CX * CZ) * v;
+                if (CY * CZ) myz += (R)(CY * CZ) * v;
+            });
+        }
         __syncthreads();
         if (active) {
             const int sm = j & 3, s0 = (j + 1) & 3, sp = (j + 2) & 3;
@@ -330,8 +424,8 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                const int slot = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
                 constexpr double W = L::w[i];
+                const int slot = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
                 const R v = phis[slot][ly + CY][lx + CX];
                 const R wv = (R)W * v;
                 if (CX) gx += (R)CX * wv;
@@ -343,42 +437,15 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             s.gy = gy * (R)3;
             s.gz = gz * (R)3;
             s.lap = lap * (R)6;
-            // pulled g and its moments
-            R gv[Q];
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr double W = L::w[i];
-                gv[i] = St::load(pull<LAT, i>(gin, G, x, y, z), (R)W * sh.g_shift, sh.g_inv_scale);
-            });
-            R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                const R v = gv[i];
-                m0 += v;
-                if (CX) { mx += (R)CX * v; mxx += v; }
-                if (CY) { my += (R)CY * v; myy += v; }
-                if (CZ) { mz += (R)CZ * v; mzz += v; }
-                if (CX * CY) mxy += (R)(CX * CY) * v;
-                if (CX * CZ) mxz += (R)(CX * CZ) * v;
-                if (CY * CZ) myz += (R)(CY * CZ) * v;
-            });
             node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
-            (void)T;
-            const long long idx = node_index(G, x, y, z);
-            R hv[Q];
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                hv[i] = St::load(pull<LAT, i>(hin, G, x, y, z), (R)W * sh.h_shift, (R)1);
-            });
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
+                const R hv = St::load(pull_at<LAT, i, false>(hin, G, x, y, z, base, in), (R)W * p.h_shift, (R)1);
                 R hs, gs;
-                collide_dir<LAT, i, R>(s, p, hv[i], &hs, &gs);
-                constexpr double W = L::w[i];
-                hout[(long long)i * G.N + idx] = St::store(hs, (R)W * sh.h_shift, (R)1);
-                gout[(long long)i * G.N + idx] = St::store(gs, (R)W * sh.g_shift, sh.g_scale);
+                collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
+                hout[(long long)i * G.N + base] = St::store(hs, (R)W * p.h_shift, (R)1);
+                gout[(long long)i * G.N + base] = St::store(gs, (R)W * p.g_shift, p.g_scale);
             });
         }
     }
@@ -430,7 +497,7 @@ __device__ __forceinline__ void stencils(const double* __restrict__ phi, const G
 
 // Macroscopic fields (phi given) in double: P and u (internal axes).
 template <int LAT, int ST>
-__global__ void macro_kernel(const typename Storage<ST>::S* __restrict__ gin, Geom G, Phys p,
+__global__ void macro_kernel(const typename Storage<ST>::S* __restrict__ gin, Geom G, PhysT<double> p,
                              const double* __restrict__ phi, double* P, double* ux, double* uy, double* uz) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;

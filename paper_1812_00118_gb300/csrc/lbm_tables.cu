@@ -18,25 +18,25 @@ namespace {
 cudaError_t step_dispatch(const void* hin, const void* gin, void* hout, void* gout, const Geom& G, const Phys& p,
                           int tile, int lz, cudaStream_t s) {
     switch (tile) {
-        case 0: return launch_step_tile<1, LBM_ST, 32, 4>(hin, gin, hout, gout, G, p, lz, s);
-        case 1: return launch_step_tile<1, LBM_ST, 32, 8>(hin, gin, hout, gout, G, p, lz, s);
-        case 2: return launch_step_tile<1, LBM_ST, 64, 4>(hin, gin, hout, gout, G, p, lz, s);
-        case 3: return launch_step_tile<1, LBM_ST, 32, 2>(hin, gin, hout, gout, G, p, lz, s);
+        case 0: return launch_step_tile<1, LBM_ST, 32, 4, 4>(hin, gin, hout, gout, G, p, lz, s);
+        case 1: return launch_step_tile<1, LBM_ST, 32, 8, 2>(hin, gin, hout, gout, G, p, lz, s);
+        case 2: return launch_step_tile<1, LBM_ST, 64, 4, 2>(hin, gin, hout, gout, G, p, lz, s);
+        case 3: return launch_step_tile<1, LBM_ST, 32, 4, 5>(hin, gin, hout, gout, G, p, lz, s);
         default: return cudaErrorInvalidValue;
     }
 }
 const KernelTable kTable = {step_dispatch, Launchers<1, LBM_ST>::phi, Launchers<1, LBM_ST>::macro,
                             Launchers<1, LBM_ST>::init, Launchers<1, LBM_ST>::get, Launchers<1, LBM_ST>::set,
-                            4, {32, 32, 64, 32}, {4, 8, 4, 2}};
+                            4, {32, 32, 64, 32}, {4, 8, 4, 4}};
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 cudaError_t step_dispatch(const void* hin, const void* gin, void* hout, void* gout, const Geom& G, const Phys& p,
                           int tile, int lz, cudaStream_t s) {
     switch (tile) {
-        case 0: return launch_step_tile<0, LBM_ST, 128, 1>(hin, gin, hout, gout, G, p, lz, s);
-        case 1: return launch_step_tile<0, LBM_ST, 256, 1>(hin, gin, hout, gout, G, p, lz, s);
-        case 2: return launch_step_tile<0, LBM_ST, 64, 1>(hin, gin, hout, gout, G, p, lz, s);
-        case 3: return launch_step_tile<0, LBM_ST, 32, 1>(hin, gin, hout, gout, G, p, lz, s);
+        case 0: return launch_step_tile<0, LBM_ST, 128, 1, 4>(hin, gin, hout, gout, G, p, lz, s);
+        case 1: return launch_step_tile<0, LBM_ST, 256, 1, 2>(hin, gin, hout, gout, G, p, lz, s);
+        case 2: return launch_step_tile<0, LBM_ST, 64, 1, 8>(hin, gin, hout, gout, G, p, lz, s);
+        case 3: return launch_step_tile<0, LBM_ST, 32, 1, 8>(hin, gin, hout, gout, G, p, lz, s);
         default: return cudaErrorInvalidValue;
     }
 }

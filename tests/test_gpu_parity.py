@@ -7,8 +7,10 @@ Tolerances (derived from the arithmetic):
   moments, the stencils from one-sided sums), so one step agrees to a few
   ulp of the largest population: 1e-13 absolute on populations of O(1);
   after hundreds of steps 1e-10 normwise.
-* FP32 storage/arithmetic: 1e-5 normwise on phi, u and P after 1000 steps
-  (the stated accuracy target), 2e-6 after one step.
+* FP32 storage/arithmetic: 1e-5 normwise on phi, u and P after one step and
+  after 1000 steps (the stated accuracy target).  One FP32 step already
+  costs ~5e-6 on P: P = T sum g is a sum of 19 stored values up to ~30x
+  larger than P, each rounded to 2^-24.
 """
 import numpy as np
 import pytest
@@ -110,9 +112,9 @@ def test_one_step_f32(lbm, lat_id, shape, bc):
     h, g = O.step(h, g, lat, p)
     f, Pg, ru = sim.macro()
     fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
-    assert normwise(f, fo) < 2e-6
-    assert normwise(Pg, Po) < 2e-6
-    assert normwise(ru, ruo) < 2e-6
+    assert normwise(f, fo) < 1e-5
+    assert normwise(Pg, Po) < 1e-5
+    assert normwise(ru, ruo) < 1e-5
 
 
 @pytest.mark.parametrize("lat_id,shape,bc", [(1, (12, 14, 20), (0, 0, 0)), (0, (1, 48, 50), (0, 1))],
