@@ -82,7 +82,8 @@ def profiled_traffic():
 def workload_fields():
     from paper_1812_00118_gb300 import inputs as I
     nx, ny, nz = SHAPE
-    phi, u, P = I.sphere((nz, ny, nx), (nx / 2, ny / 2, nz / 2), BUBBLE_R, W_IF, drop=False)
+    # centred in the box: the centre ((n-1)/2, ...) lies between nodes
+    phi, u, P = I.sphere((nz, ny, nx), ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2), BUBBLE_R, W_IF, drop=False)
     return phi, u, P
 
 

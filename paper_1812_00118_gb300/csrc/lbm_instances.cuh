@@ -12,8 +12,8 @@ cudaError_t launch_step_tile(const void* hin, const void* gin, void* hout, void*
     using S = typename Storage<ST>::S;
     dim3 block(TX, TY);
     dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + lz - 1) / lz);
-    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, s>>>((const S*)hin, (const S*)gin, (S*)hout, (S*)gout, G,
-                                                        phys_as<typename Storage<ST>::R>(p), lz);
+    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, s>>>(
+        dir_ptrs<S, Lattice<LAT>::Q>(hin, gin, hout, gout, G.N), G, phys_as<typename Storage<ST>::R>(p), lz);
     return cudaGetLastError();
 }
 

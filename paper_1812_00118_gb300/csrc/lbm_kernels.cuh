@@ -165,23 +165,49 @@ __device__ __forceinline__ S pull(const S* __restrict__ pop, const Geom& G, int 
     return __ldg(pop + (long long)dir * G.N + off);
 }
 
-// Pull with a fast path: for a node at least one spacing away from every
-// face (`interior`) the source is base - (c . strides) in the same
-// direction; otherwise the general wrap / bounce-back rule above.
+// Per-direction base pointers of the four population arrays (population i of
+// array a starts at a + i*N).  Passed by value as a kernel parameter so every
+// direction's base comes from the parameter bank and a pulled address is one
+// multiply-add of a per-plane row offset plus an immediate x offset.
+template <typename S, int Q>
+struct DirPtrs {
+    const S* hin[Q];
+    const S* gin[Q];
+    S* hout[Q];
+    S* gout[Q];
+};
+
+template <typename S, int Q>
+inline DirPtrs<S, Q> dir_ptrs(const void* hin, const void* gin, void* hout, void* gout, long long N) {
+    DirPtrs<S, Q> d;
+    for (int i = 0; i < Q; ++i) {
+        d.hin[i] = (const S*)hin + (long long)i * N;
+        d.gin[i] = (const S*)gin + (long long)i * N;
+        d.hout[i] = (S*)hout + (long long)i * N;
+        d.gout[i] = (S*)gout + (long long)i * N;
+    }
+    return d;
+}
+
+// Pull of direction I at node (x, y, z) with flat offset `base`.  For a node
+// at least one spacing away from every face (`interior`) the source is
+// base - cy NX - cz NXY - cx in the same direction; otherwise the general
+// wrap / bounce-back rule of pull_source.  `arr` is the array of per-direction
+// base pointers (hin or gin of a DirPtrs).
 template <int LAT, int I, bool STREAM, typename S>
-__device__ __forceinline__ S pull_at(const S* __restrict__ pop, const Geom& G, int x, int y, int z, int base,
+__device__ __forceinline__ S pull_at(const S* const* arr, const Geom& G, int x, int y, int z, int base,
                                      bool interior) {
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
-    int off, dir = I;
+    const S* p;
     if (interior) {
-        off = base - CX - CY * G.NX - CZ * G.NXY;
+        const int rb = base - CY * G.NX - CZ * G.NXY;
+        p = arr[I] + rb - CX;
     } else {
         bool bb;
-        off = (int)pull_source<CX, CY, CZ>(G, x, y, z, &bb);
-        if (bb) dir = L::opp(I);
+        const int off = (int)pull_source<CX, CY, CZ>(G, x, y, z, &bb);
+        p = (bb ? arr[L::opp(I)] : arr[I]) + off;
     }
-    const S* p = pop + (long long)dir * G.N + off;
     return STREAM ? ld_stream(p) : ld_keep(p);
 }
 
@@ -339,9 +365,8 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
 // iteration j+2 was last read in iteration j, before iteration j+1's barrier.
 template <int LAT, int ST, int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB)
-step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Storage<ST>::S* __restrict__ gin,
-            typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
-            Geom G, PhysT<typename Storage<ST>::R> p, int LZ) {
+step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<typename Storage<ST>::R> p,
+            int LZ) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using S = typename St::S;
@@ -369,7 +394,7 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                phi += St::load(pull_at<LAT, i, false>(hin, G, xx, yy, zz, base, in), (R)W * p.h_shift, (R)1);
+                phi += St::load(pull_at<LAT, i, false>(D.hin, G, xx, yy, zz, base, in), (R)W * p.h_shift, (R)1);
             });
             phis[slot][ly][lx] = phi;
         }
@@ -391,7 +416,7 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                gv[i] = St::load(pull_at<LAT, i, true>(gin, G, x, y, z, base, in), (R)W * p.g_shift,
+                gv[i] = St::load(pull_at<LAT, i, true>(D.gin, G, x, y, z, base, in), (R)W * p.g_shift,
                                  p.g_inv_scale);
             });
         }
@@ -441,11 +466,11 @@ step_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Stor
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                const R hv = St::load(pull_at<LAT, i, false>(hin, G, x, y, z, base, in), (R)W * p.h_shift, (R)1);
+                const R hv = St::load(pull_at<LAT, i, false>(D.hin, G, x, y, z, base, in), (R)W * p.h_shift, (R)1);
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
-                hout[(long long)i * G.N + base] = St::store(hs, (R)W * p.h_shift, (R)1);
-                gout[(long long)i * G.N + base] = St::store(gs, (R)W * p.g_shift, p.g_scale);
+                D.hout[i][base] = St::store(hs, (R)W * p.h_shift, (R)1);
+                D.gout[i][base] = St::store(gs, (R)W * p.g_shift, p.g_scale);
             });
         }
     }
