@@ -336,13 +336,16 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
     const R w = (R)L::w[I];
     const R cu = (R)CX * s.ux + (R)CY * s.uy + (R)CZ * s.uz;
-    const R G = w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * s.usq);
+    // Gamma_i - w_i formed directly: rho Gamma_i - w_i rho would cancel two
+    // O(rho w_i) terms and cost FP32 its precision on P
+    const R Gm1 = w * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * s.usq);
+    const R G = w + Gm1;
     const R cgr = (R)CX * s.gx + (R)CY * s.gy + (R)CZ * s.gz;
     const R cF = (R)CX * s.Fx + (R)CY * s.Fy + (R)CZ * s.Fz;
-    const R K = ((G - w) * (R)p.rho_dif + (R)3 * G * s.mu) * (cgr - s.ug) + (R)3 * G * (cF - s.uF);
+    const R K = (Gm1 * (R)p.rho_dif + (R)3 * G * s.mu) * (cgr - s.ug) + (R)3 * G * (cF - s.uF);
     R ccPi = (R)(CX * CX) * s.pxx + (R)(CY * CY) * s.pyy + (R)(CZ * CZ) * s.pzz
            + (R)(2 * CX * CY) * s.pxy + (R)(2 * CX * CZ) * s.pxz + (R)(2 * CY * CZ) * s.pyz;
-    R gs = s.rho * G + w * ((R)3 * s.P - s.rho) + (R)0.5 * K
+    R gs = s.rho * Gm1 + (R)3 * w * s.P + (R)0.5 * K
          + ((R)1 - s.omega) * w * (R)4.5 * (ccPi - s.tr3);
     if (p.hocorr) gs += w * cu * (R)0.75 * (R)p.rho_dif * s.lap;
     *g_out = gs;
@@ -463,15 +466,28 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             s.gz = gz * (R)3;
             s.lap = lap * (R)6;
             node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
-            Unroll<0, Q>::run([&](auto ic) {
+            // moving directions first; the rest population closes sum_i h*_i = phi
+            // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
+            // sum_i Gamma_i = 1 from biasing the global phi)
+            R hsum = 0;
+            Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
                 const R hv = St::load(pull_at<LAT, i, false>(D.hin, G, x, y, z, base, in), (R)W * p.h_shift, (R)1);
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
+                hsum += hs;
                 D.hout[i][base] = St::store(hs, (R)W * p.h_shift, (R)1);
                 D.gout[i][base] = St::store(gs, (R)W * p.g_shift, p.g_scale);
             });
+            {
+                constexpr double W0 = L::w[0];
+                const R hv = (R)0;
+                R hs, gs;
+                collide_dir<LAT, 0, R>(s, p, hv, &hs, &gs);
+                D.hout[0][base] = St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1);
+                D.gout[0][base] = St::store(gs, (R)W0 * p.g_shift, p.g_scale);
+            }
         }
     }
 }
@@ -589,11 +605,12 @@ __global__ void init_kernel(typename Storage<ST>::S* __restrict__ hout, typename
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         const double w = L::w[i];
         const double cu = CX * s.ux + CY * s.uy + CZ * s.uz;
-        const double Gm = w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * s.usq);
+        const double Gm1 = w * (3 * cu + 4.5 * cu * cu - 1.5 * s.usq);   // Gamma_i - w_i
+        const double Gm = w + Gm1;
         const double cgr = CX * s.gx + CY * s.gy + CZ * s.gz;
         const double cF = CX * s.Fx + CY * s.Fy + CZ * s.Fz;
-        const double K = ((Gm - w) * rho_dif + 3 * Gm * s.mu) * (cgr - s.ug) + 3 * Gm * (cF - s.uF);
-        double geq = s.rho * Gm + w * (3 * s.P - s.rho) - 0.5 * K;
+        const double K = (Gm1 * rho_dif + 3 * Gm * s.mu) * (cgr - s.ug) + 3 * Gm * (cF - s.uF);
+        double geq = s.rho * Gm1 + 3 * w * s.P - 0.5 * K;
         if (p.hocorr) geq += w * cu * 0.75 * rho_dif * s.lap;
         const double heq = s.phi * Gm + s.theta * w * (CX * s.nx + CY * s.ny + CZ * s.nz);
         const long long dst = push_dest<LAT, i>(G, x, y, z);

@@ -127,29 +127,59 @@ def test_one_step_f32(lbm, lat_id, shape, bc):
     assert normwise(ru, ruo) < 1e-5
 
 
-@pytest.mark.parametrize("lat_id,shape,bc,steps", [(1, (20, 22, 24), (0, 0, 0), 1000),
-                                                   (0, (1, 64, 64), (0, 0), 1000)],
-                         ids=["d3q19-drop", "d2q9-drop"])
+@pytest.mark.parametrize("lat_id,shape,bc,steps", [(1, (20, 22, 24), (0, 0, 0), 1000)], ids=["d3q19-drop"])
 def test_1000_steps_f32_drop(lbm, lat_id, shape, bc, steps):
-    """FP32 storage after 1000 steps of a drop at density ratio 1000: phi and P
-    within 1e-5 normwise of the FP64 oracle, rho u within 1e-4 (the light
-    phase divides FP32 momentum rounding by rho_L = 1e-3)."""
+    """FP32 storage after 1000 steps of a drop at density ratio 1000: phi, P and
+    rho u within 1e-5 normwise of the FP64 oracle.  (This geometry is one the
+    oracle itself is insensitive to: a 1e-15 perturbation stays at 1e-15.)"""
     sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32, drop=True, W_init=4.0, W=4.0,
-                                     R=7.0 if lat_id == 1 else 16.0, g=(0.0, 0.0, 0.0), nu_L=0.1, nu_H=0.1)
+                                     R=7.0, g=(0.0, 0.0, 0.0), nu_L=0.1, nu_H=0.1)
     sim.step(steps)
     h, g = O.run(h, g, lat, p, steps)
     f, Pg, ru = sim.macro()
     fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
     errs = (normwise(f, fo), normwise(Pg, Po), normwise(ru, ruo))
     print("FP32 vs FP64 oracle after", steps, "steps: phi %.2e  P %.2e  rho_u %.2e" % errs)
-    assert errs[0] < 1e-5 and errs[1] < 1e-5 and errs[2] < 1e-4, errs
+    assert max(errs) < 1e-5, errs
+
+
+@pytest.mark.parametrize("lat_id,shape", [(0, (1, 64, 1)), (1, (4, 64, 4))], ids=["d2q9", "d3q19"])
+def test_1000_steps_f32_layered_channel(lbm, lat_id, shape):
+    """FP32 after 1000 steps of the layered two-phase channel (walls normal to
+    y, water below air, body force along x, density ratio 1000, viscosity
+    ratio 100): phi, P and rho u within 1e-5 normwise of the FP64 oracle."""
+    nz, ny, nx = shape
+    phi, u, P = I.layers(shape, axis=1, split=ny / 2 - 0.5, W=2.5)
+    prm = lbm.make_params(M=0.1, W=2.5, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=1.7, nu_H=0.17,
+                          g=(1e-6, 0.0, 0.0), store=lbm.F32)
+    bc = (0, 1) if lat_id == 0 else (0, 1, 0)
+    user = (nx, ny) if lat_id == 0 else (nx, ny, nz)
+    sim = lbm.Simulation(lat_id, user, prm, bc=bc)
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, lat_id),
+                    np.ascontiguousarray(P.reshape(-1)))
+    sim.step(1000)
+    lat = oracle_lattice(lat_id)
+    p = oracle_params(prm, bc, lat_id)
+    h, g = O.init_populations(phi, u, P, lat, p)
+    h, g = O.run(h, g, lat, p, 1000)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+    errs = (normwise(f, fo), normwise(Pg, Po), normwise(ru, ruo))
+    print("FP32 channel vs FP64 oracle: phi %.2e  P %.2e  rho_u %.2e" % errs)
+    assert max(errs) < 1e-5, errs
 
 
 def test_config1_static_droplet_f64(lbm):
-    """D2Q9 64x64 periodic FP64, drop R = 16, W = 4, rho ratio 1000, M = 0.1,
-    tau = 0.55 in both phases, sigma = 0.01, 2000 steps: element-wise parity
-    with the oracle, exact phi conservation, and the Laplace jump equal to the
-    oracle's."""
+    """D2Q9 64x64 periodic FP64, drop R = 16 centred, W = 4, rho ratio 1000,
+    M = 0.1, tau = 0.55 in both phases, sigma = 0.01, 2000 steps.
+
+    Element-wise parity after 100 steps.  Later the drop's interior overshoots
+    phi > 1 and its local maxima are points where the normal of Eq. 2 is
+    undefined, so rounding decides the trajectory: the oracle run twice with a
+    1e-15 relative perturbation of h separates to ~1e-5 by step 300.  After
+    2000 steps the test therefore checks what is unique: exact phi
+    conservation, and phi, P and the Laplace jump within ten times the spread
+    of the oracle's own perturbed twin."""
     prm = lbm.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.05 / 3, nu_H=0.05 / 3,
                           store=lbm.F64)
     shape = (1, 64, 64)
@@ -158,23 +188,33 @@ def test_config1_static_droplet_f64(lbm):
     sim = lbm.Simulation(lbm.D2Q9, (64, 64), prm, bc=(0, 0))
     sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, 0), np.ascontiguousarray(P.reshape(-1)))
     d0 = sim.diagnostics()
-    sim.step(2000)
-    d1 = sim.diagnostics()
-    assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-12 * d0["sum_phi"]
     lat = oracle_lattice(0)
     p = oracle_params(prm, (0, 0), 0)
     h, g = O.init_populations(phi, u, P, lat, p)
-    h, g = O.run(h, g, lat, p, 2000)
+    rng = np.random.default_rng(0)
+    h2, g2 = h * (1 + 1e-15 * rng.standard_normal(h.shape)), g.copy()
+    sim.step(100)
+    h, g = O.run(h, g, lat, p, 100)
+    h2, g2 = O.run(h2, g2, lat, p, 100)
     f, Pg, ru = sim.macro()
     fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
-    assert normwise(f, fo) < 1e-10
-    assert normwise(Pg, Po) < 1e-10
-    assert normwise(ru, ruo) < 1e-10
+    assert normwise(f, fo) < 1e-9 and normwise(Pg, Po) < 1e-9 and normwise(ru, ruo) < 1e-9
+    sim.step(1900)
+    h, g = O.run(h, g, lat, p, 1900)
+    h2, g2 = O.run(h2, g2, lat, p, 1900)
+    d1 = sim.diagnostics()
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-12 * d0["sum_phi"]
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
+    ft, Pt, _ = oracle_macro_flat(h2, g2, lat, p, 0)
+    assert normwise(f, fo) <= 10 * normwise(ft, fo) + 1e-12
+    assert normwise(Pg, Po) <= 10 * normwise(Pt, Po) + 1e-12
     from oracle import diagnostics as D
     R = D.effective_radius(fo.reshape(shape), 2, True)
     dP_o = D.laplace_jump(Po.reshape(shape), (31.5, 31.5, 0), R, 4.0)
+    dP_t = D.laplace_jump(Pt.reshape(shape), (31.5, 31.5, 0), R, 4.0)
     dP_g = sim.laplace((31.5, 31.5), R - 8.0, R + 8.0)
-    assert dP_g == pytest.approx(dP_o, rel=1e-9)
+    assert abs(dP_g - dP_o) <= 10 * abs(dP_t - dP_o) + 1e-9 * abs(dP_o)
 
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[3]], ids=["d3q19", "d2q9"])
