@@ -326,11 +326,24 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
         c->K = table_for(1, params->store);
         c->lz = 16;
     }
-    c->G.NXY = c->G.NX * c->G.NY;
+    // ghost padding (see lbm_kernels.cuh): x ghosts of at least 2 cells and a
+    // multiple of 16 bytes, rows padded to 16 bytes; y ghosts 2 cells (D3Q19);
+    // one ghost plane at each z end
+    {
+        const int A = (int)(16 / c->elem);              // elements per 16 bytes
+        c->G.GX = ((A > 2 ? A : 2) + A - 1) / A * A;
+        c->G.GY = lattice == LBM_D2Q9 ? 0 : 2;
+        c->G.GZ = 1;
+        c->G.PX = ((c->G.NX + A - 1) / A) * A + 2 * c->G.GX;
+        c->G.PY = c->G.NY + 2 * c->G.GY;
+        c->G.PZ = c->G.NZ + 2 * c->G.GZ;
+        c->G.PXY = c->G.PX * c->G.PY;
+        c->G.NP = (long long)c->G.PXY * c->G.PZ;
+    }
     c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
-    if (!c->K || c->G.N >= (1LL << 31)) { delete c; return LBM_EINVAL; }
+    if (!c->K || c->G.NP >= (1LL << 31)) { delete c; return LBM_EINVAL; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
-    const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.N;
+    const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
     for (int b = 0; b < 2; ++b) {
         if (cudaMallocAsync(&c->h[b], bytes, c->stream) != cudaSuccess ||
             cudaMallocAsync(&c->g[b], bytes, c->stream) != cudaSuccess) {

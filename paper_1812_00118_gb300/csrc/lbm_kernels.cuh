@@ -1,13 +1,24 @@
 // Device code of the phase-field LB step (Otomo, Zhang & Chen, arXiv 1812.00118).
 //
-// State convention: a population buffer holds the post-collision values
-// f*_i(x, t-1) at x; the pre-collision value of the current state is
-// obtained by pulling, f_i(x, t) = f*_i(x - c_i, t-1) (halfway bounce-back
-// f*_opp(i)(x, t-1) when x - c_i lies behind a wall).  So the step kernel
-// reads with a pull and writes locally; initialisation and set_populations
-// write with the inverse map ("push").
+// State convention: a population buffer holds, at node x, the values that
+// the next step pulls: the pre-collision population of the current state is
+// f_i(x, t) = buf_i(x - c_i).  The step kernel therefore reads with a pull
+// and writes its post-collision f*_i(x) at x.
 //
-// Memory layout: population-major SoA, pop[i*N + x + NX*(y + NY*z)].
+// Memory layout (ghost-padded SoA): every population array covers a padded
+// grid PX x PY x PZ around the NX x NY x NZ nodes, x fastest; node (x, y, z)
+// sits at ((z + GZ) PY + (y + GY)) PX + (x + GX), population i at offset
+// i * NP.  The ghost cells make every pull a fixed offset with no wrap or
+// wall test in x and y:
+//   * periodic axis: a value written within R = 2 nodes of a face is also
+//     written at its periodic image in the ghost layer;
+//   * wall axis (halfway bounce-back): the node next to the wall writes its
+//     outgoing f*_j into array opp(j) at x + c_j, the ghost cell its own pull
+//     of opp(j) reads, so the pull returns f*_j(x) reflected.
+// Along z (the axis every kernel marches over) a periodic pull wraps the
+// plane index and a wall pull reads the ghost plane (GZ = 1).
+// GX >= 2 is also a multiple of 16 bytes of storage so that rows are
+// aligned for bulk tensor copies.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -20,10 +31,15 @@
 namespace lbm {
 
 // ---------------------------------------------------------------- geometry
+constexpr int kRep = 2;   // periodic replication depth in x and y
+
 struct Geom {
-    int NX, NY, NZ;
-    int NXY;          // NX * NY
-    long long N;      // NX * NY * NZ (< 2^31, checked by lbm_create)
+    int NX, NY, NZ;   // nodes (internal axes)
+    int GX, GY, GZ;   // ghost widths
+    int PX, PY, PZ;   // padded extents
+    int PXY;          // PX * PY
+    long long NP;     // PX * PY * PZ (< 2^31, checked on the host)
+    long long N;      // NX * NY * NZ
     int wall[3];
 };
 
@@ -128,47 +144,52 @@ template <> __device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(co
     return __ushort_as_bfloat16(v);
 }
 
-__device__ __forceinline__ long long node_index(const Geom& G, int x, int y, int z) {
-    return (long long)x + (long long)G.NX * ((long long)y + (long long)G.NY * z);
+// Padded flat offset of (possibly ghost) coordinates.
+__device__ __forceinline__ int pidx(const Geom& G, int x, int y, int z) {
+    return ((z + G.GZ) * G.PY + (y + G.GY)) * G.PX + (x + G.GX);
 }
 
-// Source of the pull for direction (cx, cy, cz) at node (x, y, z): returns
-// the flat offset to read and sets *bounce when x - c lies behind a wall
-// (then the caller reads the opposite direction at the node itself).
-template <int CX, int CY, int CZ>
-__device__ __forceinline__ long long pull_source(const Geom& G, int x, int y, int z, bool* bounce) {
-    int sx = x - CX, sy = y - CY, sz = z - CZ;
-    bool bb = false;
-    if (CX != 0) {
-        if (sx < 0) { if (G.wall[0]) bb = true; else sx += G.NX; }
-        else if (sx >= G.NX) { if (G.wall[0]) bb = true; else sx -= G.NX; }
-    }
-    if (CY != 0) {
-        if (sy < 0) { if (G.wall[1]) bb = true; else sy += G.NY; }
-        else if (sy >= G.NY) { if (G.wall[1]) bb = true; else sy -= G.NY; }
-    }
-    if (CZ != 0) {
-        if (sz < 0) { if (G.wall[2]) bb = true; else sz += G.NZ; }
-        else if (sz >= G.NZ) { if (G.wall[2]) bb = true; else sz -= G.NZ; }
-    }
-    *bounce = bb;
-    return bb ? node_index(G, x, y, z) : node_index(G, sx, sy, sz);
+// Plane a pull from z - cz reads: wrapped when z is periodic, the ghost plane
+// when it is walled.
+__device__ __forceinline__ int pull_plane(const Geom& G, int zs) {
+    if (G.wall[2]) return zs;
+    return zs < 0 ? zs + G.NZ : (zs >= G.NZ ? zs - G.NZ : zs);
 }
 
-// Pulled pre-collision population i at node (x, y, z) as stored (no conversion).
-template <int LAT, int I, typename S>
-__device__ __forceinline__ S pull(const S* __restrict__ pop, const Geom& G, int x, int y, int z) {
-    using L = Lattice<LAT>;
-    bool bb;
-    long long off = pull_source<L::cx[I], L::cy[I], L::cz[I]>(G, x, y, z, &bb);
-    const int dir = bb ? L::opp(I) : I;
-    return __ldg(pop + (long long)dir * G.N + off);
+// Coordinate along an axis for a phi stencil access: periodic wrap, or the
+// mirrored adjacent node behind a wall (zero normal gradient of phi).  The
+// halo of a CTA tile wider than the grid can lie more than one period out,
+// so the wrap is a full modulo; the result is always in [0, n).
+__device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
+    if (v >= 0 && v < n) return v;
+    if (wall) return v < 0 ? 0 : n - 1;
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// Store v at ghost-padded coordinates (x, y, z) of one population array and
+// at its periodic images (shifts by +-NX, +-NY along periodic axes) that lie
+// in the ghost band (within kRep of the nodes in x, GY in y) and are not a
+// node's own cell.  The z axis is never replicated.
+template <typename S>
+__device__ __forceinline__ void store_rep(S* __restrict__ arr, const Geom& G, int x, int y, int z, S v) {
+    arr[pidx(G, x, y, z)] = v;
+    const int rx = G.wall[0] ? 0 : 1;
+    const int ry = (G.wall[1] || G.GY == 0) ? 0 : 1;
+    const int Ry = G.GY < kRep ? G.GY : kRep;
+    for (int kx = -rx; kx <= rx; ++kx) {
+        for (int ky = -ry; ky <= ry; ++ky) {
+            if (kx == 0 && ky == 0) continue;
+            const int xs = x + kx * G.NX, ys = y + ky * G.NY;
+            if (xs < -kRep || xs >= G.NX + kRep || ys < -Ry || ys >= G.NY + Ry) continue;
+            if (xs >= 0 && xs < G.NX && ys >= 0 && ys < G.NY) continue;
+            arr[pidx(G, xs, ys, z)] = v;
+        }
+    }
 }
 
 // Per-direction base pointers of the four population arrays (population i of
-// array a starts at a + i*N).  Passed by value as a kernel parameter so every
-// direction's base comes from the parameter bank and a pulled address is one
-// multiply-add of a per-plane row offset plus an immediate x offset.
+// array a starts at a + i*NP).  Passed by value as a kernel parameter.
 template <typename S, int Q>
 struct DirPtrs {
     const S* hin[Q];
@@ -178,64 +199,53 @@ struct DirPtrs {
 };
 
 template <typename S, int Q>
-inline DirPtrs<S, Q> dir_ptrs(const void* hin, const void* gin, void* hout, void* gout, long long N) {
+inline DirPtrs<S, Q> dir_ptrs(const void* hin, const void* gin, void* hout, void* gout, long long NP) {
     DirPtrs<S, Q> d;
     for (int i = 0; i < Q; ++i) {
-        d.hin[i] = (const S*)hin + (long long)i * N;
-        d.gin[i] = (const S*)gin + (long long)i * N;
-        d.hout[i] = (S*)hout + (long long)i * N;
-        d.gout[i] = (S*)gout + (long long)i * N;
+        d.hin[i] = (const S*)hin + (long long)i * NP;
+        d.gin[i] = (const S*)gin + (long long)i * NP;
+        d.hout[i] = (S*)hout + (long long)i * NP;
+        d.gout[i] = (S*)gout + (long long)i * NP;
     }
     return d;
 }
 
-// Pull of direction I at node (x, y, z) with flat offset `base`.  For a node
-// at least one spacing away from every face (`interior`) the source is
-// base - cy NX - cz NXY - cx in the same direction; otherwise the general
-// wrap / bounce-back rule of pull_source.  `arr` is the array of per-direction
-// base pointers (hin or gin of a DirPtrs).
+// Pull of direction I at node (x, y, z): zoff[0..2] are the padded offsets of
+// the planes z+1, z, z-1 as pulls read them (index 1 - cz), rbase the padded
+// offset of (x, y) within a plane.
 template <int LAT, int I, bool STREAM, typename S>
-__device__ __forceinline__ S pull_at(const S* const* arr, const Geom& G, int x, int y, int z, int base,
-                                     bool interior) {
+__device__ __forceinline__ S pull_pad(const S* const* arr, const Geom& G, const int* zoff, int rbase) {
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
-    const S* p;
-    if (interior) {
-        const int rb = base - CY * G.NX - CZ * G.NXY;
-        p = arr[I] + rb - CX;
-    } else {
-        bool bb;
-        const int off = (int)pull_source<CX, CY, CZ>(G, x, y, z, &bb);
-        p = (bb ? arr[L::opp(I)] : arr[I]) + off;
-    }
+    const S* p = arr[I] + zoff[1 + CZ] + rbase - CY * G.PX - CX;
     return STREAM ? ld_stream(p) : ld_keep(p);
 }
 
-template <int LAT>
-__device__ __forceinline__ bool is_interior(const Geom& G, int x, int y, int z) {
-    return x >= 1 && x <= G.NX - 2 && z >= 1 && z <= G.NZ - 2 &&
-           (!Lattice<LAT>::kHasY || (y >= 1 && y <= G.NY - 2));
-}
-
-// Destination of the push that makes the pull of direction I at (x,y,z) return a value.
-template <int LAT, int I>
-__device__ __forceinline__ long long push_dest(const Geom& G, int x, int y, int z) {
+// Write the post-collision value v of direction J at node (x, y, z): its own
+// cell (with periodic images) and, if x + c_J crosses a wall, the bounce-back
+// ghost cell of array opp(J).  `edge` is false for nodes further than kRep
+// from every x/y face and not next to a z wall: they need only the one store.
+template <int LAT, int J, typename S>
+__device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, int y, int z, int own, bool edge, S v) {
     using L = Lattice<LAT>;
-    bool bb;
-    long long off = pull_source<L::cx[I], L::cy[I], L::cz[I]>(G, x, y, z, &bb);
-    const int dir = bb ? L::opp(I) : I;
-    return (long long)dir * G.N + off;
+    constexpr int CX = L::cx[J], CY = L::cy[J], CZ = L::cz[J];
+    if (!edge) {
+        arr[J][own] = v;
+        return;
+    }
+    store_rep(arr[J], G, x, y, z, v);
+    const int tx = x + CX, ty = y + CY, tz = z + CZ;
+    const bool wall_cross = (CX != 0 && G.wall[0] && (tx < 0 || tx >= G.NX)) ||
+                            (CY != 0 && G.wall[1] && (ty < 0 || ty >= G.NY)) ||
+                            (CZ != 0 && G.wall[2] && (tz < 0 || tz >= G.NZ));
+    if (wall_cross) store_rep(arr[L::opp(J)], G, tx, ty, tz, v);
 }
 
-// Coordinate along an axis for a stencil access: periodic wrap, or the
-// mirrored adjacent node behind a wall (zero normal gradient of phi).  The
-// halo of a CTA tile wider than the grid can lie more than one period out,
-// so the wrap is a full modulo; the result is always in [0, n).
-__device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
-    if (v >= 0 && v < n) return v;
-    if (wall) return v < 0 ? 0 : n - 1;
-    const int r = v % n;
-    return r < 0 ? r + n : r;
+template <int LAT>
+__device__ __forceinline__ bool is_edge(const Geom& G, int x, int y, int z) {
+    return x < kRep || x >= G.NX - kRep ||
+           (Lattice<LAT>::kHasY && (y < kRep || y >= G.NY - kRep)) ||
+           (G.wall[2] && (z == 0 || z == G.NZ - 1));
 }
 
 // compile-time loop helper
@@ -384,20 +394,23 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
     const int z0 = blockIdx.z * LZ;
     const int z1 = min(z0 + LZ, G.NZ);
 
-    // phi of plane zp (unwrapped; mapped by stencil_coord) into ring slot
+    // phi of plane zp (unwrapped) into ring slot: every halo position is
+    // mapped to the node whose phi it holds (periodic image or wall mirror)
     auto fill = [&](int zp, int slot) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
+        int zoff[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, zz + 1 - k) + G.GZ) * G.PXY;
         for (int k = tid; k < SX * SY; k += TX * TY) {
             const int lx = k % SX, ly = k / SX;
             const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
             const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
-            const int base = xx + G.NX * yy + G.NXY * zz;
-            const bool in = is_interior<LAT>(G, xx, yy, zz);
+            const int rb = (yy + G.GY) * G.PX + xx + G.GX;
             R phi = (R)0;
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                phi += St::load(pull_at<LAT, i, false>(D.hin, G, xx, yy, zz, base, in), (R)W * p.h_shift, (R)1);
+                phi += St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)W * p.h_shift, (R)1);
             });
             phis[slot][ly][lx] = phi;
         }
@@ -408,19 +421,20 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < G.NX && y < G.NY;
+    const int rb = (y + G.GY) * G.PX + x + G.GX;
 
     for (int z = z0; z < z1; ++z) {
         const int j = z - z0;
-        const int base = x + G.NX * y + G.NXY * z;
-        const bool in = is_interior<LAT>(G, x, y, z);
+        int zoff[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, z + 1 - k) + G.GZ) * G.PXY;
         // (1) g of this node (streamed, overlapping the phi fill's h loads)
         R gv[Q];
         if (active) {
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                gv[i] = St::load(pull_at<LAT, i, true>(D.gin, G, x, y, z, base, in), (R)W * p.g_shift,
-                                 p.g_inv_scale);
+                gv[i] = St::load(pull_pad<LAT, i, true>(D.gin, G, zoff, rb), (R)W * p.g_shift, p.g_inv_scale);
             });
         }
         fill(z + 1, (j + 2) & 3);
@@ -466,6 +480,8 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             s.gz = gz * (R)3;
             s.lap = lap * (R)6;
             node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
+            const bool edge = is_edge<LAT>(G, x, y, z);
+            const int own = (z + G.GZ) * G.PXY + rb;
             // moving directions first; the rest population closes sum_i h*_i = phi
             // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
             // sum_i Gamma_i = 1 from biasing the global phi)
@@ -473,61 +489,72 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                const R hv = St::load(pull_at<LAT, i, false>(D.hin, G, x, y, z, base, in), (R)W * p.h_shift, (R)1);
+                const R hv = St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)W * p.h_shift, (R)1);
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
                 hsum += hs;
-                D.hout[i][base] = St::store(hs, (R)W * p.h_shift, (R)1);
-                D.gout[i][base] = St::store(gs, (R)W * p.g_shift, p.g_scale);
+                write_dir<LAT, i>(D.hout, G, x, y, z, own, edge, St::store(hs, (R)W * p.h_shift, (R)1));
+                write_dir<LAT, i>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W * p.g_shift, p.g_scale));
             });
             {
                 constexpr double W0 = L::w[0];
-                const R hv = (R)0;
                 R hs, gs;
-                collide_dir<LAT, 0, R>(s, p, hv, &hs, &gs);
-                D.hout[0][base] = St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1);
-                D.gout[0][base] = St::store(gs, (R)W0 * p.g_shift, p.g_scale);
+                collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
+                write_dir<LAT, 0>(D.hout, G, x, y, z, own, edge, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
+                write_dir<LAT, 0>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
             }
         }
     }
 }
 
 // ---------------------------------------------------------------- helper kernels
-// phi = sum_i of the pulled h at every node (double output).
+__device__ __forceinline__ void node_coords(const Geom& G, long long n, int* x, int* y, int* z) {
+    *x = (int)(n % G.NX);
+    *y = (int)((n / G.NX) % G.NY);
+    *z = (int)(n / ((long long)G.NX * G.NY));
+}
+
+__device__ __forceinline__ void pull_planes(const Geom& G, int z, int* zoff) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, z + 1 - k) + G.GZ) * G.PXY;
+}
+
+// phi = sum_i of the pulled h at every node (double output, node order).
 template <int LAT, int ST>
-__global__ void phi_kernel(const typename Storage<ST>::S* __restrict__ hin, Geom G, Phys p, double* phi) {
+__global__ void phi_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p, double* phi) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
+    using R = typename St::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const int x = (int)(n % G.NX);
-    const int y = (int)((n / G.NX) % G.NY);
-    const int z = (int)(n / ((long long)G.NX * G.NY));
+    int x, y, z;
+    node_coords(G, n, &x, &y, &z);
+    int zoff[3];
+    pull_planes(G, z, zoff);
+    const int rb = (y + G.GY) * G.PX + x + G.GX;
     double acc = 0;
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr double W = L::w[i];
-        acc += (double)St::load(pull<LAT, i>(hin, G, x, y, z), (typename St::R)(W * p.h_shift),
-                                (typename St::R)1);
+        acc += (double)St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)(W * p.h_shift), (R)1);
     });
     phi[n] = acc;
 }
 
-// CD stencils of a double phi field at node (x, y, z).
+// CD stencils of a double phi field (node order) at node (x, y, z).
 template <int LAT>
 __device__ __forceinline__ void stencils(const double* __restrict__ phi, const Geom& G, int x, int y, int z,
                                          double* gx, double* gy, double* gz, double* lap) {
     using L = Lattice<LAT>;
-    const double f = phi[node_index(G, x, y, z)];
+    auto at = [&](int a, int b, int c) { return phi[(long long)a + (long long)G.NX * ((long long)b + (long long)G.NY * c)]; };
+    const double f = at(x, y, z);
     double ax = 0, ay = 0, az = 0, l = 0;
     Unroll<1, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         constexpr double W = L::w[i];
-        const int xx = stencil_coord(x + CX, G.NX, G.wall[0]);
-        const int yy = stencil_coord(y + CY, G.NY, G.wall[1]);
-        const int zz = stencil_coord(z + CZ, G.NZ, G.wall[2]);
-        const double v = phi[node_index(G, xx, yy, zz)];
+        const double v = at(stencil_coord(x + CX, G.NX, G.wall[0]), stencil_coord(y + CY, G.NY, G.wall[1]),
+                            stencil_coord(z + CZ, G.NZ, G.wall[2]));
         ax += CX * W * v;
         ay += CY * W * v;
         az += CZ * W * v;
@@ -538,41 +565,56 @@ __device__ __forceinline__ void stencils(const double* __restrict__ phi, const G
 
 // Macroscopic fields (phi given) in double: P and u (internal axes).
 template <int LAT, int ST>
-__global__ void macro_kernel(const typename Storage<ST>::S* __restrict__ gin, Geom G, PhysT<double> p,
+__global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<double> p,
                              const double* __restrict__ phi, double* P, double* ux, double* uy, double* uz) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
+    using R = typename St::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const int x = (int)(n % G.NX);
-    const int y = (int)((n / G.NX) % G.NY);
-    const int z = (int)(n / ((long long)G.NX * G.NY));
+    int x, y, z;
+    node_coords(G, n, &x, &y, &z);
+    int zoff[3];
+    pull_planes(G, z, zoff);
+    const int rb = (y + G.GY) * G.PX + x + G.GX;
     NodeState<double> s;
     s.phi = phi[n];
     stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
-    double m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+    double m0 = 0, mx = 0, my = 0, mz = 0;
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         constexpr double W = L::w[i];
-        const double v = (double)St::load(pull<LAT, i>(gin, G, x, y, z), (typename St::R)(W * p.g_shift),
-                                          (typename St::R)p.g_inv_scale);
+        const double v = (double)St::load(pull_pad<LAT, i, false>(D.gin, G, zoff, rb), (R)(W * p.g_shift),
+                                          (R)p.g_inv_scale);
         m0 += v;
         mx += CX * v; my += CY * v; mz += CZ * v;
     });
-    node_state<double, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
+    node_state<double, L::kHasY>(s, p, m0, mx, my, mz, 0, 0, 0, 0, 0, 0);
     P[n] = s.P;
     ux[n] = s.ux;
     uy[n] = s.uy;
     uz[n] = s.uz;
 }
 
-// Equilibrium initialisation (reading: h = h^eq, g = g^eq of the given
-// fields), written with the push map so that the next pull returns them.
-// phi: N doubles; u: 3 internal component arrays; P: N doubles.
+// Where the value pulled by node (x, y, z) for direction I lives: x - c_I
+// wrapped along periodic axes (the real cell; its ghost images are written
+// by store_rep), the ghost cell across a wall otherwise.
+template <int LAT, int I>
+__device__ __forceinline__ void pull_cell(const Geom& G, int x, int y, int z, int* tx, int* ty, int* tz) {
+    using L = Lattice<LAT>;
+    int a = x - L::cx[I], b = y - L::cy[I], c = z - L::cz[I];
+    if (!G.wall[0]) a = a < 0 ? a + G.NX : (a >= G.NX ? a - G.NX : a);
+    if (!G.wall[1]) b = b < 0 ? b + G.NY : (b >= G.NY ? b - G.NY : b);
+    if (!G.wall[2]) c = c < 0 ? c + G.NZ : (c >= G.NZ ? c - G.NZ : c);
+    *tx = a; *ty = b; *tz = c;
+}
+
+// Equilibrium initialisation (h = h^eq, g = g^eq of the given fields),
+// written where the next pull reads it.
 template <int LAT, int ST>
-__global__ void init_kernel(typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
-                            Geom G, Phys p, const double* __restrict__ phi, const double* __restrict__ ux,
+__global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p,
+                            const double* __restrict__ phi, const double* __restrict__ ux,
                             const double* __restrict__ uy, const double* __restrict__ uz,
                             const double* __restrict__ P) {
     using L = Lattice<LAT>;
@@ -580,9 +622,8 @@ __global__ void init_kernel(typename Storage<ST>::S* __restrict__ hout, typename
     using R = typename St::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const int x = (int)(n % G.NX);
-    const int y = (int)((n / G.NX) % G.NY);
-    const int z = (int)(n / ((long long)G.NX * G.NY));
+    int x, y, z;
+    node_coords(G, n, &x, &y, &z);
     NodeState<double> s;
     s.phi = phi[n];
     stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
@@ -613,50 +654,53 @@ __global__ void init_kernel(typename Storage<ST>::S* __restrict__ hout, typename
         double geq = s.rho * Gm1 + 3 * w * s.P - 0.5 * K;
         if (p.hocorr) geq += w * cu * 0.75 * rho_dif * s.lap;
         const double heq = s.phi * Gm + s.theta * w * (CX * s.nx + CY * s.ny + CZ * s.nz);
-        const long long dst = push_dest<LAT, i>(G, x, y, z);
-        hout[dst] = St::store((R)heq, (R)(w * p.h_shift), (R)1);
-        gout[dst] = St::store((R)geq, (R)(w * p.g_shift), (R)p.g_scale);
+        int tx, ty, tz;
+        pull_cell<LAT, i>(G, x, y, z, &tx, &ty, &tz);
+        store_rep(D.hout[i], G, tx, ty, tz, St::store((R)heq, (R)(w * p.h_shift), (R)1));
+        store_rep(D.gout[i], G, tx, ty, tz, St::store((R)geq, (R)(w * p.g_shift), (R)p.g_scale));
     });
 }
 
-// Pre-collision populations out (double, population-major).
+// Pre-collision populations out (double, population-major, node order).
 template <int LAT, int ST>
-__global__ void get_kernel(const typename Storage<ST>::S* __restrict__ hin, const typename Storage<ST>::S* __restrict__ gin,
-                           Geom G, Phys p, double* h, double* g) {
+__global__ void get_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p, double* h,
+                           double* g) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using R = typename St::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const int x = (int)(n % G.NX);
-    const int y = (int)((n / G.NX) % G.NY);
-    const int z = (int)(n / ((long long)G.NX * G.NY));
+    int x, y, z;
+    node_coords(G, n, &x, &y, &z);
+    int zoff[3];
+    pull_planes(G, z, zoff);
+    const int rb = (y + G.GY) * G.PX + x + G.GX;
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr double W = L::w[i];
-        h[(long long)i * G.N + n] = (double)St::load(pull<LAT, i>(hin, G, x, y, z), (R)(W * p.h_shift), (R)1);
-        g[(long long)i * G.N + n] = (double)St::load(pull<LAT, i>(gin, G, x, y, z), (R)(W * p.g_shift),
+        h[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)(W * p.h_shift), (R)1);
+        g[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.gin, G, zoff, rb), (R)(W * p.g_shift),
                                                      (R)p.g_inv_scale);
     });
 }
 
 template <int LAT, int ST>
-__global__ void set_kernel(typename Storage<ST>::S* __restrict__ hout, typename Storage<ST>::S* __restrict__ gout,
-                           Geom G, Phys p, const double* __restrict__ h, const double* __restrict__ g) {
+__global__ void set_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p,
+                           const double* __restrict__ h, const double* __restrict__ g) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using R = typename St::R;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const int x = (int)(n % G.NX);
-    const int y = (int)((n / G.NX) % G.NY);
-    const int z = (int)(n / ((long long)G.NX * G.NY));
+    int x, y, z;
+    node_coords(G, n, &x, &y, &z);
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr double W = L::w[i];
-        const long long dst = push_dest<LAT, i>(G, x, y, z);
-        hout[dst] = St::store((R)h[(long long)i * G.N + n], (R)(W * p.h_shift), (R)1);
-        gout[dst] = St::store((R)g[(long long)i * G.N + n], (R)(W * p.g_shift), (R)p.g_scale);
+        int tx, ty, tz;
+        pull_cell<LAT, i>(G, x, y, z, &tx, &ty, &tz);
+        store_rep(D.hout[i], G, tx, ty, tz, St::store((R)h[(long long)i * G.N + n], (R)(W * p.h_shift), (R)1));
+        store_rep(D.gout[i], G, tx, ty, tz, St::store((R)g[(long long)i * G.N + n], (R)(W * p.g_shift), (R)p.g_scale));
     });
 }
 
