@@ -135,8 +135,10 @@ int lbm_set_populations(lbm_ctx* ctx, const double* h, const double* g, int on_d
 
 /* FP64 diagnostics of the current state, reduced on the device in a fixed
  * order (deterministic): out[0] = sum phi, out[1] = sum rho, out[2] = max |u|,
- * out[3] = number of non-finite phi/u/P values.  Returns LBM_EDIVERGED
- * (after filling out) if out[3] > 0 or out[2] > 0.3.  Synchronises. */
+ * out[3] = number of non-finite phi/u/P values.  Returns LBM_ETIMEOUT if a
+ * bounded wait of a bulk-copy step gave up since creation, else
+ * LBM_EDIVERGED (after filling out) if out[3] > 0 or out[2] > 0.3.
+ * Synchronises. */
 int lbm_diagnostics(lbm_ctx* ctx, double out[4]);
 
 /* Laplace-law measurement (Section 4.1) in FP64 on the device:
@@ -155,13 +157,18 @@ long long lbm_launch_count(const lbm_ctx* ctx);
 /* The CUDA stream of the context (as given to lbm_create). */
 void* lbm_stream(const lbm_ctx* ctx);
 
-/* Step kernel configuration: `tile` indexes the compiled CTA shapes of the
- * lattice (D3Q19: 0 = 32x4, 1 = 32x8, 2 = 64x4, 3 = 32x2 threads in x-y;
- * D2Q9: 0 = 128, 1 = 256, 2 = 64, 3 = 32 threads along x) and `lz` >= 1 is
- * the number of planes along the march axis (z in 3-D, y in 2-D) one CTA
- * processes.  Results do not depend on it (every shape computes the same
- * arithmetic).  lbm_get_tile reports the current choice and its CTA shape.
- * Errors: LBM_EINVAL for an unknown tile or lz < 1. */
+/* Step kernel configuration.  `tile` indexes the compiled CTA shapes of the
+ * lattice: 0-3 load the pulled populations per thread (D3Q19: 32x4, 32x8,
+ * 64x4, 32x4 threads in x-y; D2Q9: 128, 256, 64, 32 threads along x), 4-7
+ * stage them with bulk tensor copies into a shared-memory pipeline (D3Q19:
+ * 32x4, 32x8, 64x4, 32x2; D2Q9: 128, 64, 192, 32).  `lz` >= 1 is the number
+ * of planes along the march axis (z in 3-D, y in 2-D) one CTA of tiles 0-3
+ * processes (tiles 4-7 balance planes over persistent CTAs and ignore it).
+ * Every shape computes the same arithmetic.  lbm_create picks tile 4 when
+ * the grid allows it (at least 4 nodes along x and y, shared memory fits),
+ * else tile 0.  lbm_get_tile reports the current choice and its CTA shape.
+ * Errors: LBM_EINVAL for an unknown tile or lz < 1, LBM_ENOTSUP for a
+ * bulk-copy tile this grid or storage type cannot use. */
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
 int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
 

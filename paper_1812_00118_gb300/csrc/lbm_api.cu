@@ -12,6 +12,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_tma.cuh"
 
 using namespace lbm;
 
@@ -31,6 +32,9 @@ struct lbm_ctx {
     int cur = 0;           // buffer holding the current state
     int tile = 0;          // step tile shape index
     int lz = 16;           // planes per CTA chunk
+    TmaMaps maps[2];       // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
+    int maps_tile = -1;    // tile the maps were made for
+    int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
     double* fields = nullptr;    // scratch: phi, P, ux, uy, uz (5 N doubles)
     double* partial = nullptr;   // scratch: reduction partials
     int n_partial_blocks = 0;
@@ -354,7 +358,15 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
         cudaMemsetAsync(c->h[b], 0, bytes, c->stream);
         cudaMemsetAsync(c->g[b], 0, bytes, c->stream);
     }
+    if (cudaMallocAsync((void**)&c->d_err, sizeof(int), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        lbm_destroy(c);
+        return LBM_ENOMEM;
+    }
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) { lbm_destroy(c); return LBM_ECUDA; }
+    // default: the bulk-copy pipeline when it can run this grid
+    c->tile = c->K->tma_ok(4, c->G) ? 4 : 0;
     *out = c;
     return LBM_OK;
 }
@@ -366,6 +378,7 @@ void lbm_destroy(lbm_ctx* c) {
         if (c->g[b]) cudaFreeAsync(c->g[b], c->stream);
     }
     if (c->fields) cudaFreeAsync(c->fields, c->stream);
+    if (c->d_err) cudaFreeAsync(c->d_err, c->stream);
     if (c->partial) cudaFreeAsync(c->partial, c->stream);
     cudaStreamSynchronize(c->stream);
     delete c;
@@ -400,11 +413,25 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
 
 int lbm_step(lbm_ctx* c, int n) {
     if (!c || n < 0) return LBM_EINVAL;
+    const bool tma = c->K->tile_tma[c->tile] != 0;
+    if (tma && c->maps_tile != c->tile) {
+        for (int b = 0; b < 2; ++b)
+            if (check_cuda(c->K->make_maps(c->tile, &c->maps[b], c->h[b], c->g[b], c->G))) return LBM_ECUDA;
+        c->maps_tile = c->tile;
+    }
+    StepArgs a;
+    a.G = c->G;
+    a.p = c->P;
+    a.tile = c->tile;
+    a.lz = c->lz;
+    a.stream = c->stream;
+    a.error_flag = c->d_err;
     for (int s = 0; s < n; ++s) {
-        const int a = c->cur, b = 1 - c->cur;
-        if (check_cuda(c->K->step(c->h[a], c->g[a], c->h[b], c->g[b], c->G, c->P, c->tile, c->lz, c->stream)))
-            return LBM_ECUDA;
-        c->cur = b;
+        const int i = c->cur, o = 1 - c->cur;
+        a.hin = c->h[i]; a.gin = c->g[i]; a.hout = c->h[o]; a.gout = c->g[o];
+        a.maps = &c->maps[i];
+        if (check_cuda(c->K->step(a))) return LBM_ECUDA;
+        c->cur = o;
         c->launches += 1;
     }
     return LBM_OK;
@@ -494,6 +521,9 @@ int lbm_diagnostics(lbm_ctx* c, double out[4]) {
     if (rc) return rc;
     rc = reduce_diag(c, out);
     if (rc) return rc;
+    int err = 0;
+    if (check_cuda(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost))) return LBM_ECUDA;
+    if (err) return LBM_ETIMEOUT;
     if (out[3] > 0 || out[2] > 0.3) return LBM_EDIVERGED;
     return LBM_OK;
 }
@@ -526,6 +556,7 @@ void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }
 // Step tile shape and z-chunk length (used by the tuner and the tests).
 int lbm_set_tile(lbm_ctx* c, int tile, int lz) {
     if (!c || tile < 0 || tile >= c->K->n_tiles || lz < 1) return LBM_EINVAL;
+    if (c->K->tile_tma[tile] && !c->K->tma_ok(tile, c->G)) return LBM_ENOTSUP;
     c->tile = tile;
     c->lz = lz;
     return LBM_OK;

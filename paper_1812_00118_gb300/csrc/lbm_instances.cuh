@@ -2,18 +2,103 @@
 // one translation unit per lattice (lbm_d2q9.cu, lbm_d3q19.cu) so that the
 // two lattices compile in parallel.
 #pragma once
+#include <cudaTypedefs.h>
+
 #include "lbm_internal.h"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
 template <int LAT, int ST, int TX, int TY, int MINB>
-cudaError_t launch_step_tile(const void* hin, const void* gin, void* hout, void* gout, const Geom& G,
-                             const Phys& p, int lz, cudaStream_t s) {
+cudaError_t launch_step_tile(const StepArgs& a) {
     using S = typename Storage<ST>::S;
+    const Geom& G = a.G;
     dim3 block(TX, TY);
-    dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + lz - 1) / lz);
-    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, s>>>(
-        dir_ptrs<S, Lattice<LAT>::Q>(hin, gin, hout, gout, G.NP), G, phys_as<typename Storage<ST>::R>(p), lz);
+    dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
+    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, a.stream>>>(
+        dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP), G, phys_as<typename Storage<ST>::R>(a.p),
+        a.lz);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bulk-copy tiles
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+template <int ST> struct TmaType;
+template <> struct TmaType<ST_F64> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; };
+template <> struct TmaType<ST_F32> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
+template <> struct TmaType<ST_F16S> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; };
+template <> struct TmaType<ST_BF16S> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; };
+
+// 4-D view (x, y, z, population) of one ghost-padded population array set.
+template <int LAT, int ST, int TX, int TY>
+cudaError_t make_maps_tile(TmaMaps* m, const void* h, const void* g, const Geom& G) {
+    using C = TmaCfg<LAT, ST, TX, TY>;
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t es = C::ES;
+    cuuint64_t dims[4] = {(cuuint64_t)G.PX, (cuuint64_t)G.PY, (cuuint64_t)G.PZ, (cuuint64_t)Lattice<LAT>::Q};
+    cuuint64_t strides[3] = {(cuuint64_t)G.PX * es, (cuuint64_t)G.PXY * es, (cuuint64_t)G.NP * es};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    struct { CUtensorMap* map; const void* base; cuuint32_t rows, k; } jobs[4] = {
+        {&m->h3, h, (cuuint32_t)C::RH, 3}, {&m->h1, h, (cuuint32_t)C::RH, 1},
+        {&m->g3, g, (cuuint32_t)C::RG, 3}, {&m->g1, g, (cuuint32_t)C::RG, 1}};
+    for (auto& jb : jobs) {
+        cuuint32_t box[4] = {(cuuint32_t)C::BX, jb.rows, 1, jb.k};
+        CUresult r = enc(jb.map, TmaType<ST>::v, 4, const_cast<void*>(jb.base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+template <int LAT, int ST, int TX, int TY>
+bool tma_tile_ok(const Geom& G) {
+    using C = TmaCfg<LAT, ST, TX, TY>;
+    // shared memory of one CTA, box limits, and the periodic images the
+    // halo of a tile reads (two cells deep) must exist
+    if (C::smem_bytes > 227 * 1024 || C::BX > 256 || C::RH > 256) return false;
+    if (G.NX < 2 * kRep || (Lattice<LAT>::kHasY && G.NY < 2 * kRep)) return false;
+    return tensor_map_encoder() != nullptr;
+}
+
+template <int LAT, int ST, int TX, int TY, int MINB>
+cudaError_t launch_tma_tile(const StepArgs& a) {
+    using S = typename Storage<ST>::S;
+    using C = TmaCfg<LAT, ST, TX, TY>;
+    auto kern = step_tma_kernel<LAT, ST, TX, TY, MINB>;
+    static int grid_per_sm = -1;
+    static int num_sms = 0;
+    if (grid_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX * TY, C::smem_bytes);
+        if (e != cudaSuccess || occ < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+        grid_per_sm = occ;
+    }
+    const Geom& G = a.G;
+    const long long work = (long long)((G.NX + TX - 1) / TX) * ((G.NY + TY - 1) / TY) * G.NZ;
+    long long grid = (long long)num_sms * grid_per_sm;
+    if (grid > work) grid = work;
+    kern<<<(unsigned)grid, dim3(TX, TY), C::smem_bytes, a.stream>>>(
+        *a.maps, dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP), G,
+        phys_as<typename Storage<ST>::R>(a.p), a.error_flag);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,28 @@
 
 namespace lbm {
 
+struct TmaMaps;
+
+// Everything one step launch needs.
+struct StepArgs {
+    const void* hin;
+    const void* gin;
+    void* hout;
+    void* gout;
+    Geom G;
+    Phys p;
+    int tile, lz;
+    cudaStream_t stream;
+    const TmaMaps* maps;   // tensor maps of (hin, gin) for a bulk-copy tile
+    int* error_flag;       // raised by a bounded wait that gave up
+};
+
 struct KernelTable {
-    cudaError_t (*step)(const void* hin, const void* gin, void* hout, void* gout, const Geom& G,
-                        const Phys& p, int tile, int lz, cudaStream_t s);
+    cudaError_t (*step)(const StepArgs& a);
+    // tensor maps of one input buffer pair for bulk-copy tile `tile`
+    cudaError_t (*make_maps)(int tile, TmaMaps* out, const void* h, const void* g, const Geom& G);
+    // true if bulk-copy tile `tile` can run this grid (shared memory, sizes)
+    bool (*tma_ok)(int tile, const Geom& G);
     cudaError_t (*phi)(const void* hin, const Geom& G, const Phys& p, double* phi, cudaStream_t s);
     cudaError_t (*macro)(const void* gin, const Geom& G, const Phys& p, const double* phi, double* P,
                          double* ux, double* uy, double* uz, cudaStream_t s);
@@ -21,7 +40,8 @@ struct KernelTable {
     cudaError_t (*set)(void* hout, void* gout, const Geom& G, const Phys& p, const double* h,
                        const double* g, cudaStream_t s);
     int n_tiles;            // number of compiled step tile shapes
-    int tile_tx[4], tile_ty[4];
+    int tile_tx[8], tile_ty[8];
+    int tile_tma[8];        // 1: bulk tensor copy pipeline, 0: per-thread loads
 };
 
 // One table per (lattice, storage), each defined in its own compilation of

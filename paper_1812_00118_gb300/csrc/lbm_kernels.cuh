@@ -238,7 +238,9 @@ __device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, i
     const bool wall_cross = (CX != 0 && G.wall[0] && (tx < 0 || tx >= G.NX)) ||
                             (CY != 0 && G.wall[1] && (ty < 0 || ty >= G.NY)) ||
                             (CZ != 0 && G.wall[2] && (tz < 0 || tz >= G.NZ));
-    if (wall_cross) store_rep(arr[L::opp(J)], G, tx, ty, tz, v);
+    // the ghost cell lies across a wall; along a periodic z the pull wraps the
+    // plane, so the cell does too (x and y ghosts are real ghost cells)
+    if (wall_cross) store_rep(arr[L::opp(J)], G, tx, ty, G.wall[2] ? tz : pull_plane(G, tz), v);
 }
 
 template <int LAT>

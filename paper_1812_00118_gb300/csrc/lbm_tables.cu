@@ -14,36 +14,77 @@ namespace lbm {
 namespace {
 
 #if LBM_LAT == 1
-// D3Q19: CTA shapes in the x-y plane
-cudaError_t step_dispatch(const void* hin, const void* gin, void* hout, void* gout, const Geom& G, const Phys& p,
-                          int tile, int lz, cudaStream_t s) {
-    switch (tile) {
-        case 0: return launch_step_tile<1, LBM_ST, 32, 4, 4>(hin, gin, hout, gout, G, p, lz, s);
-        case 1: return launch_step_tile<1, LBM_ST, 32, 8, 2>(hin, gin, hout, gout, G, p, lz, s);
-        case 2: return launch_step_tile<1, LBM_ST, 64, 4, 2>(hin, gin, hout, gout, G, p, lz, s);
-        case 3: return launch_step_tile<1, LBM_ST, 32, 4, 5>(hin, gin, hout, gout, G, p, lz, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-const KernelTable kTable = {step_dispatch, Launchers<1, LBM_ST>::phi, Launchers<1, LBM_ST>::macro,
-                            Launchers<1, LBM_ST>::init, Launchers<1, LBM_ST>::get, Launchers<1, LBM_ST>::set,
-                            4, {32, 32, 64, 32}, {4, 8, 4, 4}};
+// D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
+// the bulk tensor copy pipeline.
+#define LBM_TILES(X)        \
+    X(0, step, 32, 4, 4)    \
+    X(1, step, 32, 8, 2)    \
+    X(2, step, 64, 4, 2)    \
+    X(3, step, 32, 4, 5)    \
+    X(4, tma, 32, 4, 2)     \
+    X(5, tma, 32, 8, 1)     \
+    X(6, tma, 64, 4, 1)     \
+    X(7, tma, 32, 2, 3)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
-cudaError_t step_dispatch(const void* hin, const void* gin, void* hout, void* gout, const Geom& G, const Phys& p,
-                          int tile, int lz, cudaStream_t s) {
-    switch (tile) {
-        case 0: return launch_step_tile<0, LBM_ST, 128, 1, 4>(hin, gin, hout, gout, G, p, lz, s);
-        case 1: return launch_step_tile<0, LBM_ST, 256, 1, 2>(hin, gin, hout, gout, G, p, lz, s);
-        case 2: return launch_step_tile<0, LBM_ST, 64, 1, 8>(hin, gin, hout, gout, G, p, lz, s);
-        case 3: return launch_step_tile<0, LBM_ST, 32, 1, 8>(hin, gin, hout, gout, G, p, lz, s);
+#define LBM_TILES(X)        \
+    X(0, step, 128, 1, 4)   \
+    X(1, step, 256, 1, 2)   \
+    X(2, step, 64, 1, 8)    \
+    X(3, step, 32, 1, 8)    \
+    X(4, tma, 128, 1, 2)    \
+    X(5, tma, 64, 1, 4)     \
+    X(6, tma, 192, 1, 1)    \
+    X(7, tma, 32, 1, 6)
+#endif
+
+#define LBM_LAUNCH_step(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
+#define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
+#define LBM_CASE(ID, KIND, TX, TY, MB) \
+    case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
+
+cudaError_t step_dispatch(const StepArgs& a) {
+    switch (a.tile) {
+        LBM_TILES(LBM_CASE)
         default: return cudaErrorInvalidValue;
     }
 }
-const KernelTable kTable = {step_dispatch, Launchers<0, LBM_ST>::phi, Launchers<0, LBM_ST>::macro,
-                            Launchers<0, LBM_ST>::init, Launchers<0, LBM_ST>::get, Launchers<0, LBM_ST>::set,
-                            4, {128, 256, 64, 32}, {1, 1, 1, 1}};
-#endif
+
+#define LBM_MAPS_step(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
+#define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
+    case ID: return LBM_MAPS_##KIND(TX, TY);
+
+cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, const Geom& G) {
+    switch (tile) {
+        LBM_TILES(LBM_MAPS_CASE)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define LBM_OK_step(TX, TY) false
+#define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
+    case ID: return LBM_OK_##KIND(TX, TY);
+
+bool ok_dispatch(int tile, const Geom& G) {
+    switch (tile) {
+        LBM_TILES(LBM_OK_CASE)
+        default: return false;
+    }
+}
+
+#define LBM_TX(ID, KIND, TX, TY, MB) TX,
+#define LBM_TY(ID, KIND, TX, TY, MB) TY,
+#define LBM_ISTMA_step 0
+#define LBM_ISTMA_tma 1
+#define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
+
+const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
+                            Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
+                            Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
+                            Launchers<LBM_LAT, LBM_ST>::set, 8, {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
+                            {LBM_TILES(LBM_TMA)}};
 
 }  // namespace
 
