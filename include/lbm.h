@@ -163,7 +163,8 @@ void* lbm_stream(const lbm_ctx* ctx);
  * stage them with bulk tensor copies into a shared-memory pipeline (D3Q19:
  * 32x4, 32x8, 64x4, 32x2; D2Q9: 128, 64, 192, 32).  `lz` >= 1 is the number
  * of planes along the march axis (z in 3-D, y in 2-D) one CTA of tiles 0-3
- * processes (tiles 4-7 balance planes over persistent CTAs and ignore it).
+ * processes, and the planes of one work item of the persistent CTAs of
+ * tiles 4-7.
  * Every shape computes the same arithmetic.  lbm_create picks tile 4 when
  * the grid allows it (at least 4 nodes along x and y, shared memory fits),
  * else tile 0.  lbm_get_tile reports the current choice and its CTA shape.

@@ -334,11 +334,13 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
     // multiple of 16 bytes, rows padded to 16 bytes; y ghosts 2 cells (D3Q19);
     // one ghost plane at each z end
     {
-        const int A = (int)(16 / c->elem);              // elements per 16 bytes
-        c->G.GX = ((A > 2 ? A : 2) + A - 1) / A * A;
+        // x ghosts: 32 bytes of storage (at least 2 cells), so every row of
+        // nodes starts on a 32-byte sector and warps write whole sectors
+        const int A32 = (int)(32 / c->elem);            // elements per 32 bytes
+        c->G.GX = A32 > 2 ? A32 : 2;
         c->G.GY = lattice == LBM_D2Q9 ? 0 : 2;
         c->G.GZ = 1;
-        c->G.PX = ((c->G.NX + A - 1) / A) * A + 2 * c->G.GX;
+        c->G.PX = ((c->G.NX + A32 - 1) / A32) * A32 + 2 * c->G.GX;
         c->G.PY = c->G.NY + 2 * c->G.GY;
         c->G.PZ = c->G.NZ + 2 * c->G.GZ;
         c->G.PXY = c->G.PX * c->G.PY;
@@ -431,8 +433,9 @@ int lbm_step(lbm_ctx* c, int n) {
         a.hin = c->h[i]; a.gin = c->g[i]; a.hout = c->h[o]; a.gout = c->g[o];
         a.maps = &c->maps[i];
         if (check_cuda(c->K->step(a))) return LBM_ECUDA;
+        if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
         c->cur = o;
-        c->launches += 1;
+        c->launches += 2;
     }
     return LBM_OK;
 }

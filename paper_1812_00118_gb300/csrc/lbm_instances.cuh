@@ -9,15 +9,18 @@
 
 namespace lbm {
 
-template <int LAT, int ST, int TX, int TY, int MINB>
+template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST>
 cudaError_t launch_step_tile(const StepArgs& a) {
     using S = typename Storage<ST>::S;
     const Geom& G = a.G;
     dim3 block(TX, TY);
     dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
-    step_kernel<LAT, ST, TX, TY, MINB><<<grid, block, 0, a.stream>>>(
-        dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP), G, phys_as<typename Storage<ST>::R>(a.p),
-        a.lz);
+    const auto d = dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP);
+    const auto ph = phys_as<typename Storage<ST>::R>(a.p);
+    if (G.wall[0] || G.wall[1] || G.wall[2])
+        step_kernel<LAT, ST, TX, TY, MINB, HOIST, true><<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
+    else
+        step_kernel<LAT, ST, TX, TY, MINB, HOIST, false><<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
     return cudaGetLastError();
 }
 
@@ -78,9 +81,11 @@ template <int LAT, int ST, int TX, int TY, int MINB>
 cudaError_t launch_tma_tile(const StepArgs& a) {
     using S = typename Storage<ST>::S;
     using C = TmaCfg<LAT, ST, TX, TY>;
-    auto kern = step_tma_kernel<LAT, ST, TX, TY, MINB>;
-    static int grid_per_sm = -1;
+    const bool walls = a.G.wall[0] || a.G.wall[1] || a.G.wall[2];
+    auto kern = walls ? step_tma_kernel<LAT, ST, TX, TY, MINB, true> : step_tma_kernel<LAT, ST, TX, TY, MINB, false>;
+    static int grid_per_sm_v[2] = {-1, -1};
     static int num_sms = 0;
+    int& grid_per_sm = grid_per_sm_v[walls ? 1 : 0];
     if (grid_per_sm < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
         if (e != cudaSuccess) return e;
@@ -93,12 +98,13 @@ cudaError_t launch_tma_tile(const StepArgs& a) {
         grid_per_sm = occ;
     }
     const Geom& G = a.G;
-    const long long work = (long long)((G.NX + TX - 1) / TX) * ((G.NY + TY - 1) / TY) * G.NZ;
+    const int chunk = a.lz > 0 ? a.lz : 8;
+    const long long work = (long long)((G.NX + TX - 1) / TX) * ((G.NY + TY - 1) / TY) * ((G.NZ + chunk - 1) / chunk);
     long long grid = (long long)num_sms * grid_per_sm;
     if (grid > work) grid = work;
     kern<<<(unsigned)grid, dim3(TX, TY), C::smem_bytes, a.stream>>>(
         *a.maps, dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP), G,
-        phys_as<typename Storage<ST>::R>(a.p), a.error_flag);
+        phys_as<typename Storage<ST>::R>(a.p), chunk, a.error_flag);
     return cudaGetLastError();
 }
 
@@ -130,6 +136,14 @@ struct Launchers {
                            cudaStream_t s) {
         get_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>(
             dir_ptrs<S, Q>(hin, gin, nullptr, nullptr, G.NP), G, p, h, g);
+        return cudaGetLastError();
+    }
+    static cudaError_t halo(void* hout, void* gout, const Geom& G, cudaStream_t s) {
+        const int Ry = G.GY < kRep ? G.GY : kRep;
+        const long long ring = (long long)(G.NX + 2 * kRep) * (G.NY + 2 * Ry) - (long long)G.NX * G.NY;
+        const long long n = ring * (G.NZ + (G.wall[2] ? 2 : 0));
+        if (G.wall[0] && (G.wall[1] || G.GY == 0)) return cudaSuccess;   // no periodic x/y axis
+        halo_kernel<LAT, ST><<<blocks_for(n, 256), 256, 0, s>>>(dir_ptrs<S, Q>(hout, gout, hout, gout, G.NP), G);
         return cudaGetLastError();
     }
     static cudaError_t set(void* hout, void* gout, const Geom& G, const Phys& p, const double* h,

@@ -39,6 +39,8 @@ struct KernelTable {
                        double* g, cudaStream_t s);
     cudaError_t (*set)(void* hout, void* gout, const Geom& G, const Phys& p, const double* h,
                        const double* g, cudaStream_t s);
+    // periodic images of the ghost band of a freshly written buffer pair
+    cudaError_t (*halo)(void* hout, void* gout, const Geom& G, cudaStream_t s);
     int n_tiles;            // number of compiled step tile shapes
     int tile_tx[8], tile_ty[8];
     int tile_tma[8];        // 1: bulk tensor copy pipeline, 0: per-thread loads

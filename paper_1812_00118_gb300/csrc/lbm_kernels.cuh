@@ -17,8 +17,9 @@
 //     of opp(j) reads, so the pull returns f*_j(x) reflected.
 // Along z (the axis every kernel marches over) a periodic pull wraps the
 // plane index and a wall pull reads the ghost plane (GZ = 1).
-// GX >= 2 is also a multiple of 16 bytes of storage so that rows are
-// aligned for bulk tensor copies.
+// GX >= 2 is also 32 bytes of storage (rows padded to 32 bytes) so that every
+// row of nodes starts on a 32-byte sector: a warp's 32 consecutive stores
+// then fill whole sectors, and bulk tensor copies start 16-byte aligned.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -170,7 +171,8 @@ __device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
 // Store v at ghost-padded coordinates (x, y, z) of one population array and
 // at its periodic images (shifts by +-NX, +-NY along periodic axes) that lie
 // in the ghost band (within kRep of the nodes in x, GY in y) and are not a
-// node's own cell.  The z axis is never replicated.
+// node's own cell (a cell in a ghost plane behind a z wall never is).  The z
+// axis is never replicated.
 template <typename S>
 __device__ __forceinline__ void store_rep(S* __restrict__ arr, const Geom& G, int x, int y, int z, S v) {
     arr[pidx(G, x, y, z)] = v;
@@ -182,7 +184,7 @@ __device__ __forceinline__ void store_rep(S* __restrict__ arr, const Geom& G, in
             if (kx == 0 && ky == 0) continue;
             const int xs = x + kx * G.NX, ys = y + ky * G.NY;
             if (xs < -kRep || xs >= G.NX + kRep || ys < -Ry || ys >= G.NY + Ry) continue;
-            if (xs >= 0 && xs < G.NX && ys >= 0 && ys < G.NY) continue;
+            if (xs >= 0 && xs < G.NX && ys >= 0 && ys < G.NY && z >= 0 && z < G.NZ) continue;   // a node's cell
             arr[pidx(G, xs, ys, z)] = v;
         }
     }
@@ -221,34 +223,47 @@ __device__ __forceinline__ S pull_pad(const S* const* arr, const Geom& G, const 
     return STREAM ? ld_stream(p) : ld_keep(p);
 }
 
-// Write the post-collision value v of direction J at node (x, y, z): its own
-// cell (with periodic images) and, if x + c_J crosses a wall, the bounce-back
-// ghost cell of array opp(J).  `edge` is false for nodes further than kRep
-// from every x/y face and not next to a z wall: they need only the one store.
-template <int LAT, int J, typename S>
-__device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, int y, int z, int own, bool edge, S v) {
-    using L = Lattice<LAT>;
-    constexpr int CX = L::cx[J], CY = L::cy[J], CZ = L::cz[J];
-    if (!edge) {
-        arr[J][own] = v;
-        return;
-    }
-    store_rep(arr[J], G, x, y, z, v);
-    const int tx = x + CX, ty = y + CY, tz = z + CZ;
-    const bool wall_cross = (CX != 0 && G.wall[0] && (tx < 0 || tx >= G.NX)) ||
-                            (CY != 0 && G.wall[1] && (ty < 0 || ty >= G.NY)) ||
-                            (CZ != 0 && G.wall[2] && (tz < 0 || tz >= G.NZ));
-    // the ghost cell lies across a wall; along a periodic z the pull wraps the
-    // plane, so the cell does too (x and y ghosts are real ghost cells)
-    if (wall_cross) store_rep(arr[L::opp(J)], G, tx, ty, G.wall[2] ? tz : pull_plane(G, tz), v);
-}
+// Whether a node sits next to a wall (then some of its outgoing values also
+// go to bounce-back ghost cells).  The periodic images of the ghost band are
+// written after each step by halo_kernel, not by the step kernels.
+struct NodeWrites {
+    bool wall_adj;
+};
 
 template <int LAT>
-__device__ __forceinline__ bool is_edge(const Geom& G, int x, int y, int z) {
-    return x < kRep || x >= G.NX - kRep ||
-           (Lattice<LAT>::kHasY && (y < kRep || y >= G.NY - kRep)) ||
-           (G.wall[2] && (z == 0 || z == G.NZ - 1));
+__device__ __forceinline__ NodeWrites node_writes(const Geom& G, int x, int y, int z) {
+    NodeWrites w;
+    w.wall_adj = (G.wall[0] && (x == 0 || x == G.NX - 1)) ||
+                 (Lattice<LAT>::kHasY && G.wall[1] && (y == 0 || y == G.NY - 1)) ||
+                 (G.wall[2] && (z == 0 || z == G.NZ - 1));
+    return w;
 }
+
+// Write the post-collision value v of direction J at node (x, y, z): its own
+// cell `own` and, if the grid has walls (WALLS) and x + c_J crosses one, the
+// bounce-back ghost cell of array opp(J).
+template <int LAT, int J, bool WALLS, typename S>
+__device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, int y, int z, int own,
+                                          const NodeWrites& nw, S v) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[J], CY = L::cy[J], CZ = L::cz[J];
+    arr[J][own] = v;
+    if constexpr (WALLS) {
+        if (nw.wall_adj) {
+            const int tx = x + CX, ty = y + CY, tz = z + CZ;
+            const bool wall_cross = (CX != 0 && G.wall[0] && (tx < 0 || tx >= G.NX)) ||
+                                    (CY != 0 && G.wall[1] && (ty < 0 || ty >= G.NY)) ||
+                                    (CZ != 0 && G.wall[2] && (tz < 0 || tz >= G.NZ));
+            // the ghost cell lies across a wall; along a periodic z the pull wraps
+            // the plane, so the cell does too (x and y ghosts are ghost cells)
+            if (wall_cross) arr[L::opp(J)][pidx(G, tx, ty, G.wall[2] ? tz : pull_plane(G, tz))] = v;
+        }
+    }
+}
+
+// Reciprocal: correctly rounded, through the hardware reciprocal for FP32.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // compile-time loop helper
 template <int I, int N>
@@ -264,6 +279,29 @@ struct Unroll<N, N> {
     template <typename F>
     static __device__ __forceinline__ void run(F&&) {}
 };
+
+// Dot products with a compile-time integer vector: only the nonzero terms are
+// formed (IEEE arithmetic cannot drop 0 * x or x + 0 by itself), +-1
+// coefficients become additions and subtractions.
+template <int C, typename R>
+__device__ __forceinline__ R cmul(R v) {
+    if constexpr (C == 1) return v;
+    else if constexpr (C == -1) return -v;
+    else return (R)C * v;
+}
+template <int A, int B, typename R>
+__device__ __forceinline__ R cdot2(R a, R b) {
+    if constexpr (A != 0 && B != 0) return cmul<A>(a) + cmul<B>(b);
+    else if constexpr (A != 0) return cmul<A>(a);
+    else if constexpr (B != 0) return cmul<B>(b);
+    else return (R)0;
+}
+template <int A, int B, int C, typename R>
+__device__ __forceinline__ R cdot3(R a, R b, R c) {
+    if constexpr (A != 0 && (B != 0 || C != 0)) return cmul<A>(a) + cdot2<B, C>(b, c);
+    else if constexpr (A != 0) return cmul<A>(a);
+    else return cdot2<B, C>(b, c);
+}
 
 // ---------------------------------------------------------------- local physics
 // Everything a node needs after phi, grad phi and lap phi are known and the
@@ -299,7 +337,7 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     s.Fy = fr * (R)p.g[1];
     s.Fz = fr * (R)p.g[2];
     const R rho_e = p.hocorr ? s.rho + (R)0.25 * rho_dif * s.lap : s.rho;
-    const R inv_rho_e = (R)1 / rho_e;
+    const R inv_rho_e = recip(rho_e);
     s.ux = (mx + (R)0.5 * (s.mu * s.gx + s.Fx)) * inv_rho_e;
     s.uy = THREE_D ? (my + (R)0.5 * (s.mu * s.gy + s.Fy)) * inv_rho_e : (R)0;
     s.uz = (mz + (R)0.5 * (s.mu * s.gz + s.Fz)) * inv_rho_e;
@@ -329,7 +367,7 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     const R pc = s.phi < (R)0 ? (R)0 : (s.phi > (R)1 ? (R)1 : s.phi);
     s.omega = (R)p.om_L + pc * (R)p.om_dif;
     const R gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
-    const R inv = (R)1 / (gmag + (R)p.eps);
+    const R inv = recip(gmag + (R)p.eps);
     s.nx = s.gx * inv;
     s.ny = s.gy * inv;
     s.nz = s.gz * inv;
@@ -347,21 +385,22 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
     const R w = (R)L::w[I];
-    const R cu = (R)CX * s.ux + (R)CY * s.uy + (R)CZ * s.uz;
+    const R cu = cdot3<CX, CY, CZ>(s.ux, s.uy, s.uz);
     // Gamma_i - w_i formed directly: rho Gamma_i - w_i rho would cancel two
     // O(rho w_i) terms and cost FP32 its precision on P
     const R Gm1 = w * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * s.usq);
     const R G = w + Gm1;
-    const R cgr = (R)CX * s.gx + (R)CY * s.gy + (R)CZ * s.gz;
-    const R cF = (R)CX * s.Fx + (R)CY * s.Fy + (R)CZ * s.Fz;
+    const R cgr = cdot3<CX, CY, CZ>(s.gx, s.gy, s.gz);
+    const R cF = cdot3<CX, CY, CZ>(s.Fx, s.Fy, s.Fz);
     const R K = (Gm1 * (R)p.rho_dif + (R)3 * G * s.mu) * (cgr - s.ug) + (R)3 * G * (cF - s.uF);
-    R ccPi = (R)(CX * CX) * s.pxx + (R)(CY * CY) * s.pyy + (R)(CZ * CZ) * s.pzz
-           + (R)(2 * CX * CY) * s.pxy + (R)(2 * CX * CZ) * s.pxz + (R)(2 * CY * CZ) * s.pyz;
+    // c_i c_i : Pi, diagonal and off-diagonal parts
+    const R ccPi = cdot3<CX * CX, CY * CY, CZ * CZ>(s.pxx, s.pyy, s.pzz)
+                 + (R)2 * cdot3<CX * CY, CX * CZ, CY * CZ>(s.pxy, s.pxz, s.pyz);
     R gs = s.rho * Gm1 + (R)3 * w * s.P + (R)0.5 * K
          + ((R)1 - s.omega) * w * (R)4.5 * (ccPi - s.tr3);
     if (p.hocorr) gs += w * cu * (R)0.75 * (R)p.rho_dif * s.lap;
     *g_out = gs;
-    const R cn = (R)CX * s.nx + (R)CY * s.ny + (R)CZ * s.nz;
+    const R cn = cdot3<CX, CY, CZ>(s.nx, s.ny, s.nz);
     const R heq = s.phi * G + s.theta * w * cn;
     *h_out = h_in + (heq - h_in) * (R)p.inv_tau_phi;
 }
@@ -378,7 +417,11 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
 //       planes, the moments of g, the local state, and writes h*, g*.
 // Four slots make one barrier per plane enough: the slot written in
 // iteration j+2 was last read in iteration j, before iteration j+1's barrier.
-template <int LAT, int ST, int TX, int TY, int MINB>
+// HOIST: the g loads of a plane are issued before the phi fill and held in
+// registers across it (two latencies overlap, more registers); otherwise the
+// fill, the g moments and the collision run as three phases (fewer registers,
+// more resident warps to hide the latency).
+template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool WALLS>
 __global__ void __launch_bounds__(TX * TY, MINB)
 step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<typename Storage<ST>::R> p,
             int LZ) {
@@ -430,18 +473,9 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
         int zoff[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, z + 1 - k) + G.GZ) * G.PXY;
-        // (1) g of this node (streamed, overlapping the phi fill's h loads)
-        R gv[Q];
-        if (active) {
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr double W = L::w[i];
-                gv[i] = St::load(pull_pad<LAT, i, true>(D.gin, G, zoff, rb), (R)W * p.g_shift, p.g_inv_scale);
-            });
-        }
-        fill(z + 1, (j + 2) & 3);
+        // (1) g of this node (streamed) and the phi fill of the next plane
         R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
-        if (active) {
+        auto g_moments = [&](const R* gv) {
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
@@ -454,6 +488,26 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
                 if (CX * CZ) mxz += (R)(CX * CZ) * v;
                 if (CY * CZ) myz += (R)(CY * CZ) * v;
             });
+        };
+        auto g_load = [&](R* gv) {
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                gv[i] = St::load(pull_pad<LAT, i, true>(D.gin, G, zoff, rb), (R)W * p.g_shift, p.g_inv_scale);
+            });
+        };
+        if (HOIST) {
+            R gv[Q];
+            if (active) g_load(gv);
+            fill(z + 1, (j + 2) & 3);
+            if (active) g_moments(gv);
+        } else {
+            fill(z + 1, (j + 2) & 3);
+            if (active) {
+                R gv[Q];
+                g_load(gv);
+                g_moments(gv);
+            }
         }
         __syncthreads();
         if (active) {
@@ -482,7 +536,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             s.gz = gz * (R)3;
             s.lap = lap * (R)6;
             node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
-            const bool edge = is_edge<LAT>(G, x, y, z);
+            const NodeWrites nw = node_writes<LAT>(G, x, y, z);
             const int own = (z + G.GZ) * G.PXY + rb;
             // moving directions first; the rest population closes sum_i h*_i = phi
             // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
@@ -495,15 +549,15 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
                 hsum += hs;
-                write_dir<LAT, i>(D.hout, G, x, y, z, own, edge, St::store(hs, (R)W * p.h_shift, (R)1));
-                write_dir<LAT, i>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W * p.g_shift, p.g_scale));
+                write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
+                write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
             });
             {
                 constexpr double W0 = L::w[0];
                 R hs, gs;
                 collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
-                write_dir<LAT, 0>(D.hout, G, x, y, z, own, edge, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
-                write_dir<LAT, 0>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
+                write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
+                write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
             }
         }
     }
@@ -703,6 +757,46 @@ __global__ void set_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
         pull_cell<LAT, i>(G, x, y, z, &tx, &ty, &tz);
         store_rep(D.hout[i], G, tx, ty, tz, St::store((R)h[(long long)i * G.N + n], (R)(W * p.h_shift), (R)1));
         store_rep(D.gout[i], G, tx, ty, tz, St::store((R)g[(long long)i * G.N + n], (R)(W * p.g_shift), (R)p.g_scale));
+    });
+}
+
+// Periodic images of the ghost band after a step: every ghost cell within
+// kRep of the nodes in x (GY in y) that lies outside them along a periodic
+// axis gets the values of the cell it wraps to (a node's cell, or a
+// bounce-back cell across a wall along the other axis).  One thread per band
+// cell and plane (planes -1 and NZ too when z is walled: their bounce-back
+// cells have images as well).
+template <int LAT, int ST>
+__global__ void halo_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G) {
+    using L = Lattice<LAT>;
+    const int Ry = G.GY < kRep ? G.GY : kRep;
+    const int BXW = G.NX + 2 * kRep, BYW = G.NY + 2 * Ry;
+    const int ring = BXW * BYW - G.NX * G.NY;
+    const int z0 = G.wall[2] ? -1 : 0, nz = G.NZ + (G.wall[2] ? 2 : 0);
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)ring * nz) return;
+    const int z = z0 + (int)(k / ring);
+    int r = (int)(k % ring);
+    int x, y;
+    // ring order: Ry rows below, the NY middle rows (2 kRep cells each), Ry rows above
+    if (r < Ry * BXW) { y = -Ry + r / BXW; x = -kRep + r % BXW; }
+    else if ((r -= Ry * BXW) < G.NY * 2 * kRep) {
+        y = r / (2 * kRep);
+        const int c = r % (2 * kRep);
+        x = c < kRep ? -kRep + c : G.NX + (c - kRep);
+    } else {
+        r -= G.NY * 2 * kRep;
+        y = G.NY + r / BXW; x = -kRep + r % BXW;
+    }
+    int xs = x, ys = y;   // full modulo: grids narrower than kRep wrap more than once
+    if (!G.wall[0]) xs = ((x % G.NX) + G.NX) % G.NX;
+    if (!G.wall[1]) ys = ((y % G.NY) + G.NY) % G.NY;
+    if (xs == x && ys == y) return;                      // a bounce-back cell itself
+    const int dst = pidx(G, x, y, z), src = pidx(G, xs, ys, z);
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        D.hout[i][dst] = D.hout[i][src];
+        D.gout[i][dst] = D.gout[i][src];
     });
 }
 

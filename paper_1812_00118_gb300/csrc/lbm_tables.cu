@@ -17,10 +17,10 @@ namespace {
 // D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
 // the bulk tensor copy pipeline.
 #define LBM_TILES(X)        \
-    X(0, step, 32, 4, 4)    \
-    X(1, step, 32, 8, 2)    \
-    X(2, step, 64, 4, 2)    \
-    X(3, step, 32, 4, 5)    \
+    X(0, hoist, 32, 4, 4)   \
+    X(1, split, 32, 4, 8)   \
+    X(2, split, 32, 8, 4)   \
+    X(3, split, 32, 4, 6)   \
     X(4, tma, 32, 4, 2)     \
     X(5, tma, 32, 8, 1)     \
     X(6, tma, 64, 4, 1)     \
@@ -28,17 +28,18 @@ namespace {
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 #define LBM_TILES(X)        \
-    X(0, step, 128, 1, 4)   \
-    X(1, step, 256, 1, 2)   \
-    X(2, step, 64, 1, 8)    \
-    X(3, step, 32, 1, 8)    \
+    X(0, hoist, 128, 1, 4)  \
+    X(1, split, 128, 1, 8)  \
+    X(2, split, 256, 1, 4)  \
+    X(3, split, 64, 1, 16)  \
     X(4, tma, 128, 1, 2)    \
     X(5, tma, 64, 1, 4)     \
     X(6, tma, 192, 1, 1)    \
     X(7, tma, 32, 1, 6)
 #endif
 
-#define LBM_LAUNCH_step(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
+#define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true>(a)
+#define LBM_LAUNCH_split(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false>(a)
 #define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
@@ -50,7 +51,8 @@ cudaError_t step_dispatch(const StepArgs& a) {
     }
 }
 
-#define LBM_MAPS_step(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_hoist(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_split(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
 #define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_MAPS_##KIND(TX, TY);
@@ -62,7 +64,8 @@ cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, 
     }
 }
 
-#define LBM_OK_step(TX, TY) false
+#define LBM_OK_hoist(TX, TY) false
+#define LBM_OK_split(TX, TY) false
 #define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_OK_##KIND(TX, TY);
@@ -76,14 +79,16 @@ bool ok_dispatch(int tile, const Geom& G) {
 
 #define LBM_TX(ID, KIND, TX, TY, MB) TX,
 #define LBM_TY(ID, KIND, TX, TY, MB) TY,
-#define LBM_ISTMA_step 0
+#define LBM_ISTMA_hoist 0
+#define LBM_ISTMA_split 0
 #define LBM_ISTMA_tma 1
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
 
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
                             Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
-                            Launchers<LBM_LAT, LBM_ST>::set, 8, {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
+                            Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo, 8,
+                            {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
                             {LBM_TILES(LBM_TMA)}};
 
 }  // namespace

@@ -19,8 +19,9 @@
 // Every wait is bounded: on timeout a flag is raised, the CTA waits
 // (bounded) for its copies in flight and returns.
 //
-// Work is a flat range of tile-planes per persistent CTA, so every CTA
-// gets the same number of planes (a range may span two tiles).
+// Work items are (z chunk, tile) pairs ordered chunk-major, dealt round-robin
+// to persistent CTAs: the CTAs running at one time hold neighbouring tiles
+// at the same depth, so the halo rows one tile re-reads are still in L2.
 #pragma once
 #include <cuda.h>
 
@@ -121,10 +122,10 @@ struct TmaCfg {
 };
 
 // ------------------------------------------------------------ kernel
-template <int LAT, int ST, int TX, int TY, int MINB>
+template <int LAT, int ST, int TX, int TY, int MINB, bool WALLS>
 __global__ void __launch_bounds__(TX * TY, MINB)
 step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D,
-                Geom G, PhysT<typename Storage<ST>::R> p, int* error_flag) {
+                Geom G, PhysT<typename Storage<ST>::R> p, int chunk, int* error_flag) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using S = typename St::S;
@@ -150,9 +151,9 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
     __syncthreads();
 
     const int ntx = (G.NX + TX - 1) / TX, nty = (G.NY + TY - 1) / TY;
-    const long long total = (long long)ntx * nty * G.NZ;     // tile-planes
-    const long long begin = total * blockIdx.x / gridDim.x;
-    const long long end = total * (blockIdx.x + 1) / gridDim.x;
+    const int ntiles = ntx * nty;
+    const int nchunks = (G.NZ + chunk - 1) / chunk;
+    const long long items = (long long)ntiles * nchunks;   // (chunk, tile), tile fastest
     uint32_t hcount = 0, gcount = 0;                          // ring uses so far (parity = use & 1)
     bool failed = false;
 
@@ -216,12 +217,10 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
         }
     };
 
-    long long t = begin;
-    while (t < end && !failed) {
-        const long long tile = t / G.NZ;
-        const int z0 = (int)(t % G.NZ);
-        const long long seg_end = (tile + 1) * (long long)G.NZ;
-        const int z1 = (int)((end < seg_end ? end : seg_end) - tile * (long long)G.NZ);
+    for (long long it = blockIdx.x; it < items && !failed; it += gridDim.x) {
+        const int tile = (int)(it % ntiles);
+        const int z0 = (int)(it / ntiles) * chunk;
+        const int z1 = min(z0 + chunk, G.NZ);
         const int LZ = z1 - z0;
         const int x0 = (int)(tile % ntx) * TX, y0 = (int)(tile / ntx) * TY;
         const int x = x0 + tx, y = y0 + ty;
@@ -293,7 +292,7 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
                 s.gz = gz * (R)3;
                 s.lap = lap * (R)6;
                 node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
-                const bool edge = is_edge<LAT>(G, x, y, z);
+                const NodeWrites nw = node_writes<LAT>(G, x, y, z);
                 const int own = (z + G.GZ) * G.PXY + rb;
                 R hsum = 0;
                 Unroll<1, Q>::run([&](auto ic) {
@@ -304,22 +303,21 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
                     R hs, gs;
                     collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
                     hsum += hs;
-                    write_dir<LAT, i>(D.hout, G, x, y, z, own, edge, St::store(hs, (R)W * p.h_shift, (R)1));
-                    write_dir<LAT, i>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W * p.g_shift, p.g_scale));
+                    write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
+                    write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
                 });
                 {
                     constexpr double W0 = L::w[0];
                     R hs, gs;
                     collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
-                    write_dir<LAT, 0>(D.hout, G, x, y, z, own, edge, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
-                    write_dir<LAT, 0>(D.gout, G, x, y, z, own, edge, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
+                    write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
+                    write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
                 }
             }
         }
         if (failed) break;
         hcount = hb0 + (uint32_t)(LZ + 2);
         gcount = gb0 + (uint32_t)LZ;
-        t += LZ;
     }
     if (failed) {
         if (tid == 0) atomicExch(error_flag, 1);
