@@ -763,7 +763,9 @@ __global__ void set_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
 // Periodic images of the ghost band after a step: every ghost cell within
 // kRep of the nodes in x (GY in y) that lies outside them along a periodic
 // axis gets the values of the cell it wraps to (a node's cell, or a
-// bounce-back cell across a wall along the other axis).  One thread per band
+// bounce-back cell across a wall along the other axis) -- except, per
+// population, a cell across a wall that a node pulls directly (it holds that
+// node's bounce-back value).  One thread per band
 // cell and plane (planes -1 and NZ too when z is walled: their bounce-back
 // cells have images as well).
 template <int LAT, int ST>
@@ -793,10 +795,20 @@ __global__ void halo_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
     if (!G.wall[1]) ys = ((y % G.NY) + G.NY) % G.NY;
     if (xs == x && ys == y) return;                      // a bounce-back cell itself
     const int dst = pidx(G, x, y, z), src = pidx(G, xs, ys, z);
+    const bool wall_out = (G.wall[0] && (x < 0 || x >= G.NX)) || (G.wall[1] && (y < 0 || y >= G.NY)) ||
+                          (G.wall[2] && (z < 0 || z >= G.NZ));
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        D.hout[i][dst] = D.hout[i][src];
-        D.gout[i][dst] = D.gout[i][src];
+        constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+        // a cell across a wall whose pull reader (cell + c_i) is a node holds
+        // that node's bounce-back value, written by the step: not an image
+        const int rx = x + CX, ry = y + CY, rz = z + CZ;
+        const bool reader_node = rx >= 0 && rx < G.NX && ry >= 0 && ry < G.NY &&
+                                 (!G.wall[2] || (rz >= 0 && rz < G.NZ));
+        if (!(wall_out && reader_node)) {
+            D.hout[i][dst] = D.hout[i][src];
+            D.gout[i][dst] = D.gout[i][src];
+        }
     });
 }
 
