@@ -116,8 +116,10 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const doub
                     int on_device);
 
 /* Advance n >= 0 time steps: each step is one launch of the fused
- * collide-and-pull-stream kernel (Eqs. 1-13) followed by a buffer swap.
- * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails. */
+ * collide-and-pull-stream kernel (Eqs. 1-13), one launch of the small kernel
+ * that refreshes the periodic images in the ghost layer of the buffer just
+ * written, and a buffer swap.  Asynchronous on the context stream; returns
+ * LBM_ECUDA if a launch fails. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Macroscopic fields of the current state (time t, before its collision):
@@ -172,6 +174,15 @@ void* lbm_stream(const lbm_ctx* ctx);
  * bulk-copy tile this grid or storage type cannot use. */
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
 int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
+
+/* Autotuner: times every compiled tile (those the grid supports) with lz in
+ * {4, 8, 16, 32} for `steps` steps each on the current state, keeps the
+ * fastest configuration, and restores the state it started from (the state
+ * is saved to, and copied back from, a temporary device copy).  Reports the
+ * choice and its time per step (step kernel plus ghost update) in ms; any
+ * output pointer may be NULL.  Synchronises.  Errors: LBM_EINVAL (steps < 1),
+ * LBM_ENOMEM, LBM_ECUDA. */
+int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* best_ms);
 
 void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_strerror(int status);

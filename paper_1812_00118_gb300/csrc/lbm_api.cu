@@ -552,6 +552,61 @@ int lbm_laplace(lbm_ctx* c, const double centre[3], double r_in, double r_out, d
     return LBM_OK;
 }
 
+int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* best_ms) {
+    if (!c || steps < 1) return LBM_EINVAL;
+    // the trials advance the state: keep a copy and restore it afterwards
+    const int Q = c->lattice == LBM_D2Q9 ? 9 : 19;
+    const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
+    void* save_h = nullptr;
+    void* save_g = nullptr;
+    if (cudaMallocAsync(&save_h, bytes, c->stream) != cudaSuccess) return LBM_ENOMEM;
+    if (cudaMallocAsync(&save_g, bytes, c->stream) != cudaSuccess) {
+        cudaFreeAsync(save_h, c->stream);
+        return LBM_ENOMEM;
+    }
+    int rc = check_cuda(cudaMemcpyAsync(save_h, c->h[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(save_g, c->g[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int lzs[4] = {4, 8, 16, 32};
+    int bt = c->tile, bl = c->lz;
+    float bms = 1e30f;
+    for (int t = 0; t < c->K->n_tiles && !rc; ++t) {
+        if (c->K->tile_tma[t] && !c->K->tma_ok(t, c->G)) continue;
+        for (int k = 0; k < 4 && !rc; ++k) {
+            c->tile = t;
+            c->lz = lzs[k];
+            rc = lbm_step(c, 2);
+            if (rc) break;
+            cudaEventRecord(e0, c->stream);
+            rc = lbm_step(c, steps);
+            cudaEventRecord(e1, c->stream);
+            if (rc) break;
+            rc = check_cuda(cudaEventSynchronize(e1));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < bms) { bms = ms; bt = t; bl = lzs[k]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) {
+        rc = check_cuda(cudaMemcpyAsync(c->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        c->cur = 0;
+    }
+    cudaFreeAsync(save_h, c->stream);
+    cudaFreeAsync(save_g, c->stream);
+    c->tile = bt;
+    c->lz = bl;
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(c->stream));
+    if (best_tile) *best_tile = bt;
+    if (best_lz) *best_lz = bl;
+    if (best_ms) *best_ms = (double)bms / steps;
+    return rc;
+}
+
 long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
 
 void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }

@@ -140,8 +140,8 @@ struct Launchers {
     }
     static cudaError_t halo(void* hout, void* gout, const Geom& G, cudaStream_t s) {
         const int Ry = G.GY < kRep ? G.GY : kRep;
-        const long long ring = (long long)(G.NX + 2 * kRep) * (G.NY + 2 * Ry) - (long long)G.NX * G.NY;
-        const long long n = ring * (G.NZ + (G.wall[2] ? 2 : 0));
+        const long long band = (long long)(G.NX + 2 * kRep) * (G.NY + 2 * Ry);
+        const long long n = (band - (long long)G.NX * G.NY) * G.NZ + (G.wall[2] ? 2 * band : 0);
         if (G.wall[0] && (G.wall[1] || G.GY == 0)) return cudaSuccess;   // no periodic x/y axis
         halo_kernel<LAT, ST><<<blocks_for(n, 256), 256, 0, s>>>(dir_ptrs<S, Q>(hout, gout, hout, gout, G.NP), G);
         return cudaGetLastError();

@@ -760,52 +760,69 @@ __global__ void set_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
     });
 }
 
-// Periodic images of the ghost band after a step: every ghost cell within
-// kRep of the nodes in x (GY in y) that lies outside them along a periodic
-// axis gets the values of the cell it wraps to (a node's cell, or a
-// bounce-back cell across a wall along the other axis) -- except, per
-// population, a cell across a wall that a node pulls directly (it holds that
-// node's bounce-back value).  One thread per band
-// cell and plane (planes -1 and NZ too when z is walled: their bounce-back
-// cells have images as well).
+// Periodic images of the ghost band after a step.  A ghost cell c of
+// population i is pulled by r = c + c_i (a node, or a halo position of a CTA
+// tile).  Let R be r wrapped along the periodic axes; if R is not a node the
+// cell is never needed.  Otherwise the value R pulls is the one the step
+// stored for it: at S = R - c_i if that pull crosses a wall (R's bounce-back
+// write; a periodic z is wrapped there too), else at S wrapped along the
+// periodic axes (the node's own cell).
+// The halo copies that cell into c when they differ.  Band: x within kRep of
+// the nodes, y within GY, every plane (ring cells only), plus the whole band
+// area of the ghost planes behind z walls.
 template <int LAT, int ST>
 __global__ void halo_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G) {
     using L = Lattice<LAT>;
     const int Ry = G.GY < kRep ? G.GY : kRep;
     const int BXW = G.NX + 2 * kRep, BYW = G.NY + 2 * Ry;
     const int ring = BXW * BYW - G.NX * G.NY;
-    const int z0 = G.wall[2] ? -1 : 0, nz = G.NZ + (G.wall[2] ? 2 : 0);
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= (long long)ring * nz) return;
-    const int z = z0 + (int)(k / ring);
-    int r = (int)(k % ring);
-    int x, y;
-    // ring order: Ry rows below, the NY middle rows (2 kRep cells each), Ry rows above
-    if (r < Ry * BXW) { y = -Ry + r / BXW; x = -kRep + r % BXW; }
-    else if ((r -= Ry * BXW) < G.NY * 2 * kRep) {
-        y = r / (2 * kRep);
-        const int c = r % (2 * kRep);
-        x = c < kRep ? -kRep + c : G.NX + (c - kRep);
+    const long long nA = (long long)ring * G.NZ;
+    const long long nB = G.wall[2] ? 2LL * BXW * BYW : 0;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= nA + nB) return;
+    int x, y, z;
+    if (k < nA) {
+        z = (int)(k / ring);
+        int r = (int)(k % ring);
+        // ring order: Ry rows below, the NY middle rows (2 kRep cells each), Ry rows above
+        if (r < Ry * BXW) { y = -Ry + r / BXW; x = -kRep + r % BXW; }
+        else if ((r -= Ry * BXW) < G.NY * 2 * kRep) {
+            y = r / (2 * kRep);
+            const int c = r % (2 * kRep);
+            x = c < kRep ? -kRep + c : G.NX + (c - kRep);
+        } else {
+            r -= G.NY * 2 * kRep;
+            y = G.NY + r / BXW; x = -kRep + r % BXW;
+        }
     } else {
-        r -= G.NY * 2 * kRep;
-        y = G.NY + r / BXW; x = -kRep + r % BXW;
+        k -= nA;
+        z = k < BXW * BYW ? -1 : G.NZ;
+        const int a = (int)(k % (BXW * BYW));
+        x = -kRep + a % BXW;
+        y = -Ry + a / BXW;
     }
-    int xs = x, ys = y;   // full modulo: grids narrower than kRep wrap more than once
-    if (!G.wall[0]) xs = ((x % G.NX) + G.NX) % G.NX;
-    if (!G.wall[1]) ys = ((y % G.NY) + G.NY) % G.NY;
-    if (xs == x && ys == y) return;                      // a bounce-back cell itself
-    const int dst = pidx(G, x, y, z), src = pidx(G, xs, ys, z);
-    const bool wall_out = (G.wall[0] && (x < 0 || x >= G.NX)) || (G.wall[1] && (y < 0 || y >= G.NY)) ||
-                          (G.wall[2] && (z < 0 || z >= G.NZ));
+    auto wrap = [](int v, int n) { return ((v % n) + n) % n; };
+    const int dst = pidx(G, x, y, z);
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-        // a cell across a wall whose pull reader (cell + c_i) is a node holds
-        // that node's bounce-back value, written by the step: not an image
-        const int rx = x + CX, ry = y + CY, rz = z + CZ;
-        const bool reader_node = rx >= 0 && rx < G.NX && ry >= 0 && ry < G.NY &&
-                                 (!G.wall[2] || (rz >= 0 && rz < G.NZ));
-        if (!(wall_out && reader_node)) {
+        int Rx = x + CX, Ry_ = y + CY, Rz = z + CZ;
+        if (!G.wall[0]) Rx = wrap(Rx, G.NX);
+        if (!G.wall[1]) Ry_ = wrap(Ry_, G.NY);
+        if (!G.wall[2]) Rz = wrap(Rz, G.NZ);
+        if (Rx < 0 || Rx >= G.NX || Ry_ < 0 || Ry_ >= G.NY || Rz < 0 || Rz >= G.NZ) return;
+        int Sx = Rx - CX, Sy = Ry_ - CY, Sz = Rz - CZ;
+        const bool bounce = (G.wall[0] && (Sx < 0 || Sx >= G.NX)) || (G.wall[1] && (Sy < 0 || Sy >= G.NY)) ||
+                            (G.wall[2] && (Sz < 0 || Sz >= G.NZ));
+        // the bounce-back write keeps x and y as ghost coordinates and wraps a
+        // periodic z (write_dir); a node's own cell is wrapped on every axis
+        if (!G.wall[2]) Sz = wrap(Sz, G.NZ);
+        if (!bounce) {
+            if (!G.wall[0]) Sx = wrap(Sx, G.NX);
+            if (!G.wall[1]) Sy = wrap(Sy, G.NY);
+        }
+        const int src = pidx(G, Sx, Sy, Sz);
+        if (src != dst) {
             D.hout[i][dst] = D.hout[i][src];
             D.gout[i][dst] = D.gout[i][src];
         }

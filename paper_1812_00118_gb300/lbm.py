@@ -67,6 +67,7 @@ SIGNATURES = [
     ("lbm_stream", _VP, [_VP]),
     ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
+    ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -247,6 +248,14 @@ class Simulation:
         _check(load().lbm_get_tile(self._ctx, ctypes.byref(t), ctypes.byref(lz), ctypes.byref(tx),
                                    ctypes.byref(ty)), "lbm_get_tile")
         return t.value, lz.value, tx.value, ty.value
+
+    def autotune(self, steps=20):
+        """Pick the fastest tile/lz for this grid (state is restored); returns
+        (tile, lz, ms_per_step)."""
+        t, lz, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().lbm_autotune(self._ctx, int(steps), ctypes.byref(t), ctypes.byref(lz), ctypes.byref(ms)),
+               "lbm_autotune")
+        return t.value, lz.value, ms.value
 
     @property
     def ctx(self):
