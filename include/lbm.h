@@ -122,6 +122,12 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const doub
  * LBM_ECUDA if a launch fails. */
 int lbm_step(lbm_ctx* ctx, int n);
 
+/* lbm_step with CUDA events recorded on the context stream around every
+ * launch of the fused step kernel; *kernel_ms receives the summed duration of
+ * those launches (the ghost-update launches excluded).  Synchronises.  Used
+ * to relate the step kernel's own time to its algorithmic traffic. */
+int lbm_step_profiled(lbm_ctx* ctx, int n, double* kernel_ms);
+
 /* Macroscopic fields of the current state (time t, before its collision):
  * phi = sum h, P and rho u by the formulas after Eq. 12, where rho u is
  * rho(phi) times the velocity the collision uses.  Any output pointer may be

@@ -413,7 +413,32 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
     return check_cuda(cudaStreamSynchronize(c->stream));
 }
 
-int lbm_step(lbm_ctx* c, int n) {
+static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev);
+
+int lbm_step(lbm_ctx* c, int n) { return step_impl(c, n, nullptr); }
+
+int lbm_step_profiled(lbm_ctx* c, int n, double* kernel_ms) {
+    if (!c || n < 0 || !kernel_ms) return LBM_EINVAL;
+    cudaEvent_t* ev = (cudaEvent_t*)calloc(2 * (size_t)(n > 0 ? n : 1), sizeof(cudaEvent_t));
+    if (!ev) return LBM_ENOMEM;
+    int rc = LBM_OK;
+    for (int k = 0; k < 2 * n && !rc; ++k) rc = check_cuda(cudaEventCreate(&ev[k]));
+    if (!rc) rc = step_impl(c, n, ev);
+    if (!rc && n > 0) rc = check_cuda(cudaEventSynchronize(ev[2 * n - 1]));
+    double total = 0;
+    for (int k = 0; k < n && !rc; ++k) {
+        float ms = 0;
+        rc = check_cuda(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+        total += ms;
+    }
+    for (int k = 0; k < 2 * n; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+    free(ev);
+    *kernel_ms = total;
+    return rc;
+}
+
+static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
     if (!c || n < 0) return LBM_EINVAL;
     const bool tma = c->K->tile_tma[c->tile] != 0;
     if (tma && c->maps_tile != c->tile) {
@@ -432,7 +457,9 @@ int lbm_step(lbm_ctx* c, int n) {
         const int i = c->cur, o = 1 - c->cur;
         a.hin = c->h[i]; a.gin = c->g[i]; a.hout = c->h[o]; a.gout = c->g[o];
         a.maps = &c->maps[i];
+        if (ev) cudaEventRecord(ev[2 * s], c->stream);
         if (check_cuda(c->K->step(a))) return LBM_ECUDA;
+        if (ev) cudaEventRecord(ev[2 * s + 1], c->stream);
         if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
         c->cur = o;
         c->launches += 2;

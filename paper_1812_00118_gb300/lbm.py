@@ -57,6 +57,7 @@ SIGNATURES = [
                                   ctypes.POINTER(_VP)]),
     ("lbm_init_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_step_profiled", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     ("lbm_macro", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     ("lbm_get_populations", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     ("lbm_set_populations", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
@@ -191,6 +192,12 @@ class Simulation:
 
     def step(self, n=1):
         _check(load().lbm_step(self._ctx, int(n)), "lbm_step")
+
+    def step_profiled(self, n):
+        """n steps; returns the summed duration (ms) of the step-kernel launches."""
+        ms = ctypes.c_double()
+        _check(load().lbm_step_profiled(self._ctx, int(n), ctypes.byref(ms)), "lbm_step_profiled")
+        return ms.value
 
     def macro(self, phi=None, P=None, rho_u=None):
         """Fill the given outputs (host arrays or device tensors); allocate host
