@@ -116,10 +116,10 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const doub
                     int on_device);
 
 /* Advance n >= 0 time steps: each step is one launch of the fused
- * collide-and-pull-stream kernel (Eqs. 1-13), one launch of the small kernel
- * that refreshes the periodic images in the ghost layer of the buffer just
- * written, and a buffer swap.  Asynchronous on the context stream; returns
- * LBM_ECUDA if a launch fails. */
+ * collide-and-pull-stream kernel (Eqs. 1-13) and a buffer swap; the
+ * bulk-copy tiles (see lbm_set_tile) add one launch of a small kernel that
+ * writes the periodic images into the ghost layer of the buffer just written.
+ * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* lbm_step with CUDA events recorded on the context stream around every

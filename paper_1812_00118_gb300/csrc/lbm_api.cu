@@ -34,6 +34,7 @@ struct lbm_ctx {
     int lz = 16;           // planes per CTA chunk
     TmaMaps maps[2];       // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
     int maps_tile = -1;    // tile the maps were made for
+    bool ghosts[2] = {false, false};   // ghost band of buffer b holds the periodic images
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
     double* fields = nullptr;    // scratch: phi, P, ux, uy, uz (5 N doubles)
     double* partial = nullptr;   // scratch: reduction partials
@@ -409,6 +410,7 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
     if (check_cuda(c->K->init(c->h[0], c->g[0], c->G, c->P, f_phi(c), f_u(c, 0), f_u(c, 1), f_u(c, 2), f_P(c),
                               c->stream)))
         return LBM_ECUDA;
+    c->ghosts[0] = true;   // the initialisation writes the periodic images too
     c->launches += 1;
     return check_cuda(cudaStreamSynchronize(c->stream));
 }
@@ -457,12 +459,24 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
         const int i = c->cur, o = 1 - c->cur;
         a.hin = c->h[i]; a.gin = c->g[i]; a.hout = c->h[o]; a.gout = c->g[o];
         a.maps = &c->maps[i];
+        // bulk-copy tiles read the ghost band unwrapped: it must hold the
+        // periodic images (per-thread-load tiles wrap their pulls instead)
+        if (tma && !c->ghosts[i]) {
+            if (check_cuda(c->K->halo(c->h[i], c->g[i], c->G, c->stream))) return LBM_ECUDA;
+            c->ghosts[i] = true;
+            c->launches += 1;
+        }
         if (ev) cudaEventRecord(ev[2 * s], c->stream);
         if (check_cuda(c->K->step(a))) return LBM_ECUDA;
         if (ev) cudaEventRecord(ev[2 * s + 1], c->stream);
-        if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
+        c->launches += 1;
+        c->ghosts[o] = false;
+        if (tma) {
+            if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
+            c->ghosts[o] = true;
+            c->launches += 1;
+        }
         c->cur = o;
-        c->launches += 2;
     }
     return LBM_OK;
 }
@@ -535,6 +549,7 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
     }
     c->cur = 0;
     int rc = check_cuda(c->K->set(c->h[0], c->g[0], c->G, c->P, dh, dg, c->stream));
+    c->ghosts[0] = true;
     c->launches += 1;
     if (th) { cudaFreeAsync(th, c->stream); cudaFreeAsync(tg, c->stream); }
     if (!rc && c->P.force_mode == 1) {
@@ -591,6 +606,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         cudaFreeAsync(save_h, c->stream);
         return LBM_ENOMEM;
     }
+    const bool saved_ghosts = c->ghosts[c->cur];
     int rc = check_cuda(cudaMemcpyAsync(save_h, c->h[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     if (!rc) rc = check_cuda(cudaMemcpyAsync(save_g, c->g[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t e0, e1;
@@ -622,6 +638,8 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         rc = check_cuda(cudaMemcpyAsync(c->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, c->stream));
         if (!rc) rc = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
         c->cur = 0;
+        c->ghosts[0] = saved_ghosts;
+        c->ghosts[1] = false;
     }
     cudaFreeAsync(save_h, c->stream);
     cudaFreeAsync(save_g, c->stream);

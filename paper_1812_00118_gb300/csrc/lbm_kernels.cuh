@@ -8,15 +8,13 @@
 // Memory layout (ghost-padded SoA): every population array covers a padded
 // grid PX x PY x PZ around the NX x NY x NZ nodes, x fastest; node (x, y, z)
 // sits at ((z + GZ) PY + (y + GY)) PX + (x + GX), population i at offset
-// i * NP.  The ghost cells make every pull a fixed offset with no wrap or
-// wall test in x and y:
-//   * periodic axis: a value written within R = 2 nodes of a face is also
-//     written at its periodic image in the ghost layer;
-//   * wall axis (halfway bounce-back): the node next to the wall writes its
-//     outgoing f*_j into array opp(j) at x + c_j, the ghost cell its own pull
-//     of opp(j) reads, so the pull returns f*_j(x) reflected.
-// Along z (the axis every kernel marches over) a periodic pull wraps the
-// plane index and a wall pull reads the ghost plane (GZ = 1).
+// i * NP.  A pull from x - c_i wraps the coordinate along a periodic axis and
+// reads the ghost layer across a wall (halfway bounce-back): the node next to
+// the wall writes its outgoing f*_j into array opp(j) at x + c_j, the ghost
+// cell its own pull of opp(j) reads, so the pull returns f*_j(x) reflected.
+// The bulk-copy kernels (lbm_tma.cuh) read whole boxes, unwrapped: for them
+// halo_kernel also fills the ghost band (kRep = 2 cells) with the periodic
+// images of the cells the step wrote.
 // GX >= 2 is also 32 bytes of storage (rows padded to 32 bytes) so that every
 // row of nodes starts on a 32-byte sector: a warp's 32 consecutive stores
 // then fill whole sectors, and bulk tensor copies start 16-byte aligned.
@@ -212,14 +210,36 @@ inline DirPtrs<S, Q> dir_ptrs(const void* hin, const void* gin, void* hout, void
     return d;
 }
 
-// Pull of direction I at node (x, y, z): zoff[0..2] are the padded offsets of
-// the planes z+1, z, z-1 as pulls read them (index 1 - cz), rbase the padded
-// offset of (x, y) within a plane.
+// Offsets of the cells the pulls of node (x, y, z) read: for c in {-1, 0, 1}
+// along each axis, the coordinate x - c wrapped along a periodic axis (so no
+// ghost image is needed) or left in the ghost layer across a wall (where the
+// bounce-back value is stored); z uses pull_plane.  Index 1 + c.
+struct PullOffsets {
+    int z[3], r[3], c[3];
+};
+
+__device__ __forceinline__ int wrap1(int v, int n, int wall) {
+    if (wall) return v;
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+__device__ __forceinline__ PullOffsets pull_offsets(const Geom& G, int x, int y, int z) {
+    PullOffsets o;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int c = k - 1;
+        o.z[k] = (pull_plane(G, z - c) + G.GZ) * G.PXY;
+        o.r[k] = (wrap1(y - c, G.NY, G.wall[1]) + G.GY) * G.PX;
+        o.c[k] = wrap1(x - c, G.NX, G.wall[0]) + G.GX;
+    }
+    return o;
+}
+
 template <int LAT, int I, bool STREAM, typename S>
-__device__ __forceinline__ S pull_pad(const S* const* arr, const Geom& G, const int* zoff, int rbase) {
+__device__ __forceinline__ S pull_pad(const S* const* arr, const PullOffsets& o) {
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
-    const S* p = arr[I] + zoff[1 + CZ] + rbase - CY * G.PX - CX;
+    const S* p = arr[I] + (o.z[1 + CZ] + o.r[1 + CY] + o.c[1 + CX]);
     return STREAM ? ld_stream(p) : ld_keep(p);
 }
 
@@ -254,9 +274,11 @@ __device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, i
             const bool wall_cross = (CX != 0 && G.wall[0] && (tx < 0 || tx >= G.NX)) ||
                                     (CY != 0 && G.wall[1] && (ty < 0 || ty >= G.NY)) ||
                                     (CZ != 0 && G.wall[2] && (tz < 0 || tz >= G.NZ));
-            // the ghost cell lies across a wall; along a periodic z the pull wraps
-            // the plane, so the cell does too (x and y ghosts are ghost cells)
-            if (wall_cross) arr[L::opp(J)][pidx(G, tx, ty, G.wall[2] ? tz : pull_plane(G, tz))] = v;
+            // the ghost cell lies across a wall; along the periodic axes the
+            // pull wraps, so the cell does too
+            if (wall_cross)
+                arr[L::opp(J)][pidx(G, wrap1(tx, G.NX, G.wall[0]), wrap1(ty, G.NY, G.wall[1]),
+                                    wrap1(tz, G.NZ, G.wall[2]))] = v;
         }
     }
 }
@@ -443,19 +465,16 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
     // mapped to the node whose phi it holds (periodic image or wall mirror)
     auto fill = [&](int zp, int slot) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
-        int zoff[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, zz + 1 - k) + G.GZ) * G.PXY;
         for (int k = tid; k < SX * SY; k += TX * TY) {
             const int lx = k % SX, ly = k / SX;
             const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
             const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
-            const int rb = (yy + G.GY) * G.PX + xx + G.GX;
+            const PullOffsets po = pull_offsets(G, xx, yy, zz);
             R phi = (R)0;
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                phi += St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)W * p.h_shift, (R)1);
+                phi += St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
             });
             phis[slot][ly][lx] = phi;
         }
@@ -470,9 +489,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
 
     for (int z = z0; z < z1; ++z) {
         const int j = z - z0;
-        int zoff[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, z + 1 - k) + G.GZ) * G.PXY;
+        const PullOffsets po = pull_offsets(G, x, y, z);
         // (1) g of this node (streamed) and the phi fill of the next plane
         R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
         auto g_moments = [&](const R* gv) {
@@ -493,7 +510,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                gv[i] = St::load(pull_pad<LAT, i, true>(D.gin, G, zoff, rb), (R)W * p.g_shift, p.g_inv_scale);
+                gv[i] = St::load(pull_pad<LAT, i, true>(D.gin, po), (R)W * p.g_shift, p.g_inv_scale);
             });
         };
         if (HOIST) {
@@ -545,7 +562,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                const R hv = St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)W * p.h_shift, (R)1);
+                const R hv = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
                 hsum += hs;
@@ -570,11 +587,6 @@ __device__ __forceinline__ void node_coords(const Geom& G, long long n, int* x, 
     *z = (int)(n / ((long long)G.NX * G.NY));
 }
 
-__device__ __forceinline__ void pull_planes(const Geom& G, int z, int* zoff) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) zoff[k] = (pull_plane(G, z + 1 - k) + G.GZ) * G.PXY;
-}
-
 // phi = sum_i of the pulled h at every node (double output, node order).
 template <int LAT, int ST>
 __global__ void phi_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p, double* phi) {
@@ -585,14 +597,12 @@ __global__ void phi_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
     if (n >= G.N) return;
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
-    int zoff[3];
-    pull_planes(G, z, zoff);
-    const int rb = (y + G.GY) * G.PX + x + G.GX;
+    const PullOffsets po = pull_offsets(G, x, y, z);
     double acc = 0;
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr double W = L::w[i];
-        acc += (double)St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)(W * p.h_shift), (R)1);
+        acc += (double)St::load(pull_pad<LAT, i, false>(D.hin, po), (R)(W * p.h_shift), (R)1);
     });
     phi[n] = acc;
 }
@@ -630,9 +640,7 @@ __global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>
     if (n >= G.N) return;
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
-    int zoff[3];
-    pull_planes(G, z, zoff);
-    const int rb = (y + G.GY) * G.PX + x + G.GX;
+    const PullOffsets po = pull_offsets(G, x, y, z);
     NodeState<double> s;
     s.phi = phi[n];
     stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
@@ -641,7 +649,7 @@ __global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         constexpr double W = L::w[i];
-        const double v = (double)St::load(pull_pad<LAT, i, false>(D.gin, G, zoff, rb), (R)(W * p.g_shift),
+        const double v = (double)St::load(pull_pad<LAT, i, false>(D.gin, po), (R)(W * p.g_shift),
                                           (R)p.g_inv_scale);
         m0 += v;
         mx += CX * v; my += CY * v; mz += CZ * v;
@@ -728,14 +736,12 @@ __global__ void get_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
     if (n >= G.N) return;
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
-    int zoff[3];
-    pull_planes(G, z, zoff);
-    const int rb = (y + G.GY) * G.PX + x + G.GX;
+    const PullOffsets po = pull_offsets(G, x, y, z);
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr double W = L::w[i];
-        h[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.hin, G, zoff, rb), (R)(W * p.h_shift), (R)1);
-        g[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.gin, G, zoff, rb), (R)(W * p.g_shift),
+        h[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.hin, po), (R)(W * p.h_shift), (R)1);
+        g[(long long)i * G.N + n] = (double)St::load(pull_pad<LAT, i, false>(D.gin, po), (R)(W * p.g_shift),
                                                      (R)p.g_inv_scale);
     });
 }
@@ -764,9 +770,8 @@ __global__ void set_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
 // population i is pulled by r = c + c_i (a node, or a halo position of a CTA
 // tile).  Let R be r wrapped along the periodic axes; if R is not a node the
 // cell is never needed.  Otherwise the value R pulls is the one the step
-// stored for it: at S = R - c_i if that pull crosses a wall (R's bounce-back
-// write; a periodic z is wrapped there too), else at S wrapped along the
-// periodic axes (the node's own cell).
+// stored for it, at S = R - c_i wrapped along the periodic axes (the node's
+// own cell, or R's bounce-back cell if the pull crosses a wall).
 // The halo copies that cell into c when they differ.  Band: x within kRep of
 // the nodes, y within GY, every plane (ring cells only), plus the whole band
 // area of the ghost planes behind z walls.
@@ -811,16 +816,12 @@ __global__ void halo_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
         if (!G.wall[1]) Ry_ = wrap(Ry_, G.NY);
         if (!G.wall[2]) Rz = wrap(Rz, G.NZ);
         if (Rx < 0 || Rx >= G.NX || Ry_ < 0 || Ry_ >= G.NY || Rz < 0 || Rz >= G.NZ) return;
+        // the cell the step stored it in: a node's own cell or R's bounce-back
+        // cell across a wall, wrapped along every periodic axis either way
         int Sx = Rx - CX, Sy = Ry_ - CY, Sz = Rz - CZ;
-        const bool bounce = (G.wall[0] && (Sx < 0 || Sx >= G.NX)) || (G.wall[1] && (Sy < 0 || Sy >= G.NY)) ||
-                            (G.wall[2] && (Sz < 0 || Sz >= G.NZ));
-        // the bounce-back write keeps x and y as ghost coordinates and wraps a
-        // periodic z (write_dir); a node's own cell is wrapped on every axis
+        if (!G.wall[0]) Sx = wrap(Sx, G.NX);
+        if (!G.wall[1]) Sy = wrap(Sy, G.NY);
         if (!G.wall[2]) Sz = wrap(Sz, G.NZ);
-        if (!bounce) {
-            if (!G.wall[0]) Sx = wrap(Sx, G.NX);
-            if (!G.wall[1]) Sy = wrap(Sy, G.NY);
-        }
         const int src = pidx(G, Sx, Sy, Sz);
         if (src != dst) {
             D.hout[i][dst] = D.hout[i][src];
