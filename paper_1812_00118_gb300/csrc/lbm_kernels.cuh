@@ -455,6 +455,10 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
     constexpr int HY = L::kHasY ? 1 : 0;
     constexpr int SX = TX + 2, SY = TY + 2 * HY;
     __shared__ R phis[4][SY][SX];
+    // pulled h of the thread's own node on the last two filled planes: the fill
+    // of plane z+1 loads them anyway, the collision of the next iteration
+    // reads them back (each thread touches only its own column: no barrier)
+    __shared__ R hown[2][Q][TX * TY];
 
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -463,10 +467,36 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
 
     // phi of plane zp (unwrapped) into ring slot: every halo position is
     // mapped to the node whose phi it holds (periodic image or wall mirror)
-    auto fill = [&](int zp, int slot) {
+    constexpr int NRING = SX * SY - TX * TY;   // halo positions of the phi tile
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // the thread's own position first (its pulled h kept in hown[hs]), then
+    // its share of the halo ring
+    auto fill = [&](int zp, int slot, int hs) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
-        for (int k = tid; k < SX * SY; k += TX * TY) {
-            const int lx = k % SX, ly = k / SX;
+        {
+            const int xx = stencil_coord(x0 + tx, G.NX, G.wall[0]);
+            const int yy = HY ? stencil_coord(y0 + ty, G.NY, G.wall[1]) : y0;
+            const PullOffsets po = pull_offsets(G, xx, yy, zz);
+            R phi = (R)0;
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr double W = L::w[i];
+                const R v = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
+                hown[hs][i][tid] = v;
+                phi += v;
+            });
+            phis[slot][ty + HY][tx + 1] = phi;
+        }
+        for (int k = tid; k < NRING; k += TX * TY) {
+            int lx, ly;
+            if (HY) {
+                if (k < SX) { lx = k; ly = 0; }
+                else if (k < 2 * SX) { lx = k - SX; ly = SY - 1; }
+                else { const int r = k - 2 * SX; lx = (r & 1) ? SX - 1 : 0; ly = 1 + (r >> 1); }
+            } else {
+                lx = k == 0 ? 0 : SX - 1;
+                ly = 0;
+            }
             const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
             const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
             const PullOffsets po = pull_offsets(G, xx, yy, zz);
@@ -480,9 +510,8 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
         }
     };
 
-    fill(z0 - 1, 0);
-    fill(z0, 1);
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    fill(z0 - 1, 0, 0);
+    fill(z0, 1, 1);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < G.NX && y < G.NY;
     const int rb = (y + G.GY) * G.PX + x + G.GX;
@@ -516,10 +545,10 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
         if (HOIST) {
             R gv[Q];
             if (active) g_load(gv);
-            fill(z + 1, (j + 2) & 3);
+            fill(z + 1, (j + 2) & 3, j & 1);
             if (active) g_moments(gv);
         } else {
-            fill(z + 1, (j + 2) & 3);
+            fill(z + 1, (j + 2) & 3, j & 1);
             if (active) {
                 R gv[Q];
                 g_load(gv);
@@ -562,7 +591,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                const R hv = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
+                const R hv = hown[(j + 1) & 1][i][tid];
                 R hs, gs;
                 collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
                 hsum += hs;
