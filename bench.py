@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=list(BYTES_PER_LU), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=None, help="fixed step tile (skips the autotuner)")
+    ap.add_argument("--lz", type=int, default=16, help="planes per CTA chunk with --tile")
     return ap.parse_args()
 
 
@@ -223,7 +225,11 @@ def run_ours(args):
         sim = lbm.Simulation(lbm.D3Q19, SHAPE, prm, stream=stream.cuda_stream)
         sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
                         np.ascontiguousarray(P.reshape(-1)))
-        tile, lz, tune_ms = sim.autotune(10)
+        if args.tile is None:
+            tile, lz, tune_ms = sim.autotune(10)
+        else:
+            sim.set_tile(args.tile, args.lz)
+            tile, lz = args.tile, args.lz
         sim.step(args.warmup)
         stream.synchronize()
         # --- device-timed region
