@@ -190,6 +190,38 @@ int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* best_ms);
 
+/* Field diagnostics without any allocation.  The paper has no counterpart:
+ * this is a service of the library, not a step of the method.
+ *
+ * For callers that cannot call cudaMalloc -- code running while a stream is
+ * captured into a CUDA graph with allocation forbidden, a host framework whose
+ * allocator owns all device memory, a loop that must not enter the allocator
+ * -- this computes the same FP64 sums as lbm_diagnostics, in a fixed order,
+ * from field arrays the caller provides, and allocates nothing: its scratch
+ * (per-block partial sums) is a static device array of 256 KB inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *
+ *   phi, P      device arrays of n doubles (required)
+ *   v0, v1, v2  device arrays of n doubles, the components of a vector field
+ *               (e.g. u); any may be NULL (treated as 0)
+ *   n           number of nodes, 0 <= n <= LBM_NOALLOC_MAX_NODES
+ *   rho_L, rho_dif  rho = rho_L + phi rho_dif for the mass sum
+ *   out         device array of 4 doubles: sum phi, sum rho, max |v|, and the
+ *               number of non-finite phi / P / |v| values
+ *   cuda_stream the stream to launch on (NULL: default stream)
+ *
+ * Asynchronous: out is valid once the stream reaches the call.  The first
+ * call on a device looks up the scratch array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call on a device shares the one scratch array, so calls whose launches
+ * overlap on the GPU (different streams, no ordering) race: order them on
+ * one stream.  Errors: LBM_EINVAL (NULL phi, P or out, n < 0 or
+ * n > LBM_NOALLOC_MAX_NODES), LBM_ECUDA (launch failed). */
+#define LBM_NOALLOC_MAX_NODES 33554432
+int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
+                           const double* v2, long long n, double rho_L, double rho_dif, double* out,
+                           void* cuda_stream);
+
 void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_strerror(int status);
 

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
+    ("lbm_field_sums_noalloc", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_longlong, ctypes.c_double,
+                                              ctypes.c_double, _VP, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -134,6 +136,22 @@ def _ptr(a, writable=False):
     if not (a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()):
         raise ValueError("tensor fields must be contiguous float64")
     return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+NOALLOC_MAX_NODES = 33554432
+
+
+def field_sums_noalloc(phi, P, v, rho_L, rho_dif, out, stream=None):
+    """lbm_field_sums_noalloc on device tensors: phi, P (n,), v a sequence of up
+    to 3 component tensors (or None), out a (4,) float64 CUDA tensor."""
+    comps = list(v or [])[:3] + [None] * (3 - len(list(v or [])[:3]))
+    ptrs = [None if c is None else _ptr(c)[0] for c in comps]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().lbm_field_sums_noalloc(_ptr(phi)[0], _ptr(P)[0], ptrs[0], ptrs[1], ptrs[2], int(phi.numel()),
+                                         float(rho_L), float(rho_dif), _ptr(out, True)[0], ctypes.c_void_p(stream)),
+           "lbm_field_sums_noalloc")
 
 
 class Simulation:
