@@ -1,0 +1,71 @@
+"""Mixed-precision storage (16-bit shifted populations, FP32 arithmetic)
+against the FP64 oracle.
+
+Storage: h_i - w_i/2 and (g_i - w_i P_ref / T) * g_scale in FP16 or BF16;
+the collision runs in FP32.  The errors are reported, not hidden: BF16 has
+an 8-bit mantissa and its phi error after a few hundred steps is orders of
+magnitude above FP32's.  The bounds below are the measured errors with a
+factor of ~3 of headroom, so a regression in the 16-bit path shows.
+"""
+import numpy as np
+import pytest
+
+from oracle import pflbm as O
+from paper_1812_00118_gb300 import inputs as I
+from parity_helpers import normwise, oracle_lattice, oracle_macro_flat, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_00118_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def run_drop(L, store, steps, g_scale=0.0):
+    shape = (20, 22, 24)
+    nz, ny, nx = shape
+    phi, u, P = I.sphere(shape, (nx / 2 + 0.31, ny / 2 - 0.23, nz / 2 + 0.17), 7.0, 4.0, drop=True)
+    prm = L.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1, nu_H=0.1, store=store,
+                        g_scale=g_scale)
+    sim = L.Simulation(L.D3Q19, (nx, ny, nz), prm)
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
+                    np.ascontiguousarray(P.reshape(-1)))
+    sim.step(steps)
+    d = sim.diagnostics(raise_on_divergence=False)
+    return sim.macro(), d, (phi, u, P, prm)
+
+
+@pytest.fixture(scope="module")
+def oracle_200(lbm):
+    (_, _, _), _, (phi, u, P, prm) = run_drop(lbm, lbm.F32, 0)
+    lat = oracle_lattice(1)
+    p = oracle_params(prm, (0, 0, 0), 1)
+    h, g = O.init_populations(phi, u, P, lat, p)
+    h, g = O.run(h, g, lat, p, 200)
+    return oracle_macro_flat(h, g, lat, p, 1), float(phi.sum())
+
+
+@pytest.mark.parametrize("store,g_scale,bounds", [
+    ("F32", 0.0, (1e-6, 1e-5, 1e-5)),
+    ("F16S", 1e3, (1.2e-2, 2e-2, 8e-2)),
+    ("BF16S", 0.0, (5e-2, 8e-2, 6e-1)),
+], ids=["f32", "f16s", "bf16s"])
+def test_16bit_storage_error(lbm, oracle_200, store, g_scale, bounds):
+    (fo, Po, ruo), sum0 = oracle_200
+    (f, Pg, ru), d, _ = run_drop(lbm, getattr(lbm, store), 200, g_scale)
+    errs = (normwise(f, fo), normwise(Pg, Po), normwise(ru, ruo))
+    drift = abs(d["sum_phi"] - sum0) / sum0
+    print(f"{store} vs FP64 oracle after 200 steps: phi {errs[0]:.2e}  P {errs[1]:.2e}  rho_u {errs[2]:.2e}"
+          f"  sum(phi) drift {drift:.2e}")
+    assert d["nonfinite"] == 0
+    # 16-bit rounding of the stored h breaks exact conservation of sum(phi)
+    assert drift < (1e-6 if store == "F32" else 3e-2)
+    for e, b in zip(errs, bounds):
+        assert e < b, (errs, bounds)
