@@ -165,17 +165,22 @@ long long lbm_launch_count(const lbm_ctx* ctx);
 /* The CUDA stream of the context (as given to lbm_create). */
 void* lbm_stream(const lbm_ctx* ctx);
 
-/* Step kernel configuration.  `tile` indexes the compiled CTA shapes of the
- * lattice: 0-3 load the pulled populations per thread (D3Q19: 32x4, 32x8,
- * 64x4, 32x4 threads in x-y; D2Q9: 128, 256, 64, 32 threads along x), 4-7
- * stage them with bulk tensor copies into a shared-memory pipeline (D3Q19:
- * 32x4, 32x8, 64x4, 32x2; D2Q9: 128, 64, 192, 32).  `lz` >= 1 is the number
- * of planes along the march axis (z in 3-D, y in 2-D) one CTA of tiles 0-3
- * processes, and the planes of one work item of the persistent CTAs of
- * tiles 4-7.
- * Every shape computes the same arithmetic.  lbm_create picks tile 4 when
- * the grid allows it (at least 4 nodes along x and y, shared memory fits),
- * else tile 0.  lbm_get_tile reports the current choice and its CTA shape.
+/* Step kernel configuration.  `tile` indexes the compiled step kernels of
+ * the lattice:
+ *   0-3   per-thread loads, grid = tile columns x chunks of `lz` planes.
+ *         D3Q19 CTAs (x-y): 32x4 (g loads held across the phi fill), 32x4,
+ *         32x8, 32x4 (the last three in phases, for 8, 4 and 6 CTAs per SM);
+ *         D2Q9 CTAs (along x): 128 (held), 128, 256, 64.
+ *   4-7   bulk tensor copies into a shared-memory pipeline, persistent CTAs
+ *         taking work items of `lz` planes (D3Q19: 32x4, 32x8, 64x4, 32x2;
+ *         D2Q9: 128, 64, 192, 32).
+ *   8-11  tiles 0-3 launched as one wave: every column split into the same
+ *         number of chunks, as many as the resident CTAs allow, each at
+ *         least `lz` planes long.
+ * `lz` >= 1 is the number of planes along the march axis (z in 3-D, y in
+ * 2-D) as above.  Every tile computes the same arithmetic.  lbm_create picks
+ * tile 1 with lz = 16; lbm_get_tile reports the current choice and its CTA
+ * shape.
  * Errors: LBM_EINVAL for an unknown tile or lz < 1, LBM_ENOTSUP for a
  * bulk-copy tile this grid or storage type cannot use. */
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);

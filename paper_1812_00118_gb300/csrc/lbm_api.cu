@@ -331,9 +331,9 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
         c->K = table_for(1, params->store);
         c->lz = 16;
     }
-    // ghost padding (see lbm_kernels.cuh): x ghosts of at least 2 cells and a
-    // multiple of 16 bytes, rows padded to 16 bytes; y ghosts 2 cells (D3Q19);
-    // one ghost plane at each z end
+    // ghost padding (see lbm_kernels.cuh): x ghosts of 32 bytes (at least 2
+    // cells), rows padded to 32 bytes; y ghosts 2 cells (D3Q19); one ghost
+    // plane at each z end
     {
         // x ghosts: 32 bytes of storage (at least 2 cells), so every row of
         // nodes starts on a 32-byte sector and warps write whole sectors
@@ -368,8 +368,9 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
     }
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) { lbm_destroy(c); return LBM_ECUDA; }
-    // default: the bulk-copy pipeline when it can run this grid
-    c->tile = c->K->tma_ok(4, c->G) ? 4 : 0;
+    // default: per-thread loads in phases, 8 CTAs per SM (the fastest tile on
+    // the measured grids; lbm_autotune picks per grid)
+    c->tile = 1;
     *out = c;
     return LBM_OK;
 }

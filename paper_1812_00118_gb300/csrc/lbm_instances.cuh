@@ -9,18 +9,40 @@
 
 namespace lbm {
 
-template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST>
+// Grid = tile columns x chunks along z.  Chunks of lz planes, or with BAL
+// (one-wave launch) as many equal chunks as the resident slots (occupancy x
+// SMs, looked up once per instantiation) allow for every column, with at
+// least lz planes each.
+template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool BAL>
 cudaError_t launch_step_tile(const StepArgs& a) {
     using S = typename Storage<ST>::S;
     const Geom& G = a.G;
+    const bool walls = G.wall[0] || G.wall[1] || G.wall[2];
+    auto kern = walls ? step_kernel<LAT, ST, TX, TY, MINB, HOIST, BAL, true>
+                      : step_kernel<LAT, ST, TX, TY, MINB, HOIST, BAL, false>;
     dim3 block(TX, TY);
     dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
+    if (BAL) {
+        static int slots_v[2] = {-1, -1};
+        int& slots = slots_v[walls ? 1 : 0];
+        if (slots < 0) {
+            int dev = 0, sms = 0, occ = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX * TY, 0);
+            if (e != cudaSuccess) return e;
+            if (occ < 1) return cudaErrorInvalidConfiguration;
+            slots = sms * occ;
+        }
+        long long nzc = slots / ((long long)grid.x * grid.y);
+        const long long by_lz = (G.NZ + a.lz - 1) / a.lz;
+        if (nzc > by_lz) nzc = by_lz;
+        if (nzc < 1) nzc = 1;
+        grid.z = (unsigned)nzc;
+    }
     const auto d = dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP);
     const auto ph = phys_as<typename Storage<ST>::R>(a.p);
-    if (G.wall[0] || G.wall[1] || G.wall[2])
-        step_kernel<LAT, ST, TX, TY, MINB, HOIST, true><<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
-    else
-        step_kernel<LAT, ST, TX, TY, MINB, HOIST, false><<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
+    kern<<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@ namespace lbm {
 
 struct TmaMaps;
 
+constexpr int kMaxTiles = 12;   // step kernel variants per (lattice, storage)
+
 // Everything one step launch needs.
 struct StepArgs {
     const void* hin;
@@ -42,8 +44,8 @@ struct KernelTable {
     // periodic images of the ghost band of a freshly written buffer pair
     cudaError_t (*halo)(void* hout, void* gout, const Geom& G, cudaStream_t s);
     int n_tiles;            // number of compiled step tile shapes
-    int tile_tx[8], tile_ty[8];
-    int tile_tma[8];        // 1: bulk tensor copy pipeline, 0: per-thread loads
+    int tile_tx[kMaxTiles], tile_ty[kMaxTiles];
+    int tile_tma[kMaxTiles];   // 1: bulk tensor copy pipeline, 0: per-thread loads
 };
 
 // One table per (lattice, storage), each defined in its own compilation of

@@ -427,6 +427,91 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
     *h_out = h_in + (heq - h_in) * (R)p.inv_tau_phi;
 }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// A direction I and its opposite J = opp(I) share every even term of the
+// collision (c c : Pi, (c.u)^2, w_i) and see the odd ones (c.u, c.grad phi,
+// c.F, c.n) with opposite signs.  FP32 kernels collide the pair in the two
+// lanes of float2 registers (lane x: I, lane y: J) with the paired FP32
+// instructions of sm_100 and later, one instruction for two directions.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Node quantities the pair collision reads, broadcast to both lanes once per
+// node.  w3P, thw, hoc depend on w_i: index 0 for the axis weight, 1 for the
+// diagonal weight (D3Q19: 1/18, 1/36; D2Q9: 1/9, 1/36).
+struct PairState {
+    float2 rho, mu3, rho_dif, neg_ug, neg_uF, neg_usq15, phi, inv_tau;
+    float2 w3P[2], thw[2], hoc[2];
+    float om45, tr3;   // (1 - 1/tau_mix) * 4.5 and tr(Pi)/3
+};
+
+template <int LAT>
+__device__ __forceinline__ PairState pair_state(const NodeState<float>& s, const PhysT<float>& p) {
+    using L = Lattice<LAT>;
+    constexpr int IA = 1, ID = 4;   // an axis and a diagonal direction
+    static_assert(L::cx[IA] * L::cx[IA] + L::cy[IA] * L::cy[IA] + L::cz[IA] * L::cz[IA] == 1, "axis");
+    static_assert(L::cx[ID] * L::cx[ID] + L::cy[ID] * L::cy[ID] + L::cz[ID] * L::cz[ID] == 2, "diagonal");
+    PairState q;
+    q.rho = dup2(s.rho);
+    q.mu3 = dup2(3.0f * s.mu);
+    q.rho_dif = dup2(p.rho_dif);
+    q.neg_ug = dup2(-s.ug);
+    q.neg_uF = dup2(-s.uF);
+    q.neg_usq15 = dup2(-1.5f * s.usq);
+    q.phi = dup2(s.phi);
+    q.inv_tau = dup2(p.inv_tau_phi);
+    const float wk[2] = {(float)L::w[IA], (float)L::w[ID]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        q.w3P[k] = dup2(3.0f * wk[k] * s.P);
+        q.thw[k] = dup2(s.theta * wk[k]);
+        q.hoc[k] = dup2(p.hocorr ? wk[k] * 0.75f * p.rho_dif * s.lap : 0.0f);
+    }
+    q.om45 = (1.0f - s.omega) * 4.5f;
+    q.tr3 = s.tr3;
+    return q;
+}
+
+// Post-collision g* and h* of the pair (I, opp(I)): the arithmetic of
+// collide_dir, two directions per instruction.  hin holds the pulled h of I
+// and opp(I) in its lanes.
+template <int LAT, int I>
+__device__ __forceinline__ void collide_pair(const NodeState<float>& s, const PairState& q, float2 hin,
+                                             float2* h_out, float2* g_out) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
+    constexpr int K2 = CX * CX + CY * CY + CZ * CZ;
+    constexpr int WK = K2 == 1 ? 0 : 1;
+    const float2 w = dup2((float)L::w[I]);
+    const float cu = cdot3<CX, CY, CZ>(s.ux, s.uy, s.uz);
+    const float cg = cdot3<CX, CY, CZ>(s.gx, s.gy, s.gz);
+    const float cF = cdot3<CX, CY, CZ>(s.Fx, s.Fy, s.Fz);
+    const float cn = cdot3<CX, CY, CZ>(s.nx, s.ny, s.nz);
+    const float2 a = make_float2(cu, -cu);
+    // Gamma - w = w (3 c.u + 4.5 (c.u)^2 - 1.5 u.u), formed directly (see collide_dir)
+    float2 t = fma2(a, dup2(4.5f), dup2(3.0f));
+    t = fma2(t, a, q.neg_usq15);
+    const float2 Gm1 = mul2(t, w);
+    const float2 G = add2(Gm1, w);
+    // K = (Gm1 rho_dif + 3 G mu)(c.grad phi - u.grad phi) + 3 G (c.F - u.F)
+    const float2 A = fma2(Gm1, q.rho_dif, mul2(G, q.mu3));
+    const float2 B = add2(make_float2(cg, -cg), q.neg_ug);
+    const float2 C = add2(make_float2(cF, -cF), q.neg_uF);
+    const float2 K = fma2(A, B, mul2(mul2(G, dup2(3.0f)), C));
+    // c c : Pi, even in c
+    const float ccPi = cdot3<CX * CX, CY * CY, CZ * CZ>(s.pxx, s.pyy, s.pzz) +
+                       2.0f * cdot3<CX * CY, CX * CZ, CY * CZ>(s.pxy, s.pxz, s.pyz);
+    const float filt = (ccPi - q.tr3) * (q.om45 * (float)L::w[I]);
+    float2 gs = fma2(q.rho, Gm1, add2(q.w3P[WK], dup2(filt)));
+    gs = fma2(K, dup2(0.5f), gs);
+    gs = fma2(a, q.hoc[WK], gs);
+    *g_out = gs;
+    const float2 heq = fma2(q.phi, G, mul2(q.thw[WK], make_float2(cn, -cn)));
+    *h_out = fma2(add2(heq, make_float2(-hin.x, -hin.y)), q.inv_tau, hin);
+}
+
 // ---------------------------------------------------------------- fused step
 // One CTA owns a TX x TY column of nodes in the x-y plane and marches along
 // z over a chunk of LZ planes.  Per plane it
@@ -443,7 +528,13 @@ __device__ __forceinline__ void collide_dir(const NodeState<R>& s, const PhysT<R
 // registers across it (two latencies overlap, more registers); otherwise the
 // fill, the g moments and the collision run as three phases (fewer registers,
 // more resident warps to hide the latency).
-template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool WALLS>
+// The grid is tile columns x chunks along z.  Every column uses the same
+// chunk boundaries, so CTAs of neighbouring columns march through the same
+// planes at the same time and their halo-ring and chunk-edge re-reads of h
+// hit L2.  BAL (one-wave launch): gridDim.z chunks of NZ / gridDim.z planes
+// (rounded), the host choosing gridDim.z so that the whole grid is resident
+// at once; otherwise chunks of LZ planes.
+template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool BAL, bool WALLS>
 __global__ void __launch_bounds__(TX * TY, MINB)
 step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<typename Storage<ST>::R> p,
             int LZ) {
@@ -462,8 +553,8 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
 
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * LZ;
-    const int z1 = min(z0 + LZ, G.NZ);
+    const int z0 = BAL ? (int)((long long)blockIdx.z * G.NZ / gridDim.z) : blockIdx.z * LZ;
+    const int z1 = BAL ? (int)((long long)(blockIdx.z + 1) * G.NZ / gridDim.z) : min(z0 + LZ, G.NZ);
 
     // phi of plane zp (unwrapped) into ring slot: every halo position is
     // mapped to the node whose phi it holds (periodic image or wall mirror)
@@ -521,18 +612,24 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
         const PullOffsets po = pull_offsets(G, x, y, z);
         // (1) g of this node (streamed) and the phi fill of the next plane
         R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+        // over opposite pairs (I, J): the odd moments take g_I - g_J, the
+        // even ones g_I + g_J
         auto g_moments = [&](const R* gv) {
-            Unroll<0, Q>::run([&](auto ic) {
+            m0 = gv[0];
+            Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                const R v = gv[i];
-                m0 += v;
-                if (CX) { mx += (R)CX * v; mxx += v; }
-                if (CY) { my += (R)CY * v; myy += v; }
-                if (CZ) { mz += (R)CZ * v; mzz += v; }
-                if (CX * CY) mxy += (R)(CX * CY) * v;
-                if (CX * CZ) mxz += (R)(CX * CZ) * v;
-                if (CY * CZ) myz += (R)(CY * CZ) * v;
+                constexpr int o = L::op[i];
+                if constexpr (i < o) {
+                    constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+                    const R sp = gv[i] + gv[o], dm = gv[i] - gv[o];
+                    m0 += sp;
+                    if (CX) { mx += cmul<CX>(dm); mxx += sp; }
+                    if (CY) { my += cmul<CY>(dm); myy += sp; }
+                    if (CZ) { mz += cmul<CZ>(dm); mzz += sp; }
+                    if (CX * CY) mxy += cmul<CX * CY>(sp);
+                    if (CX * CZ) mxz += cmul<CX * CZ>(sp);
+                    if (CY * CZ) myz += cmul<CY * CZ>(sp);
+                }
             });
         };
         auto g_load = [&](R* gv) {
@@ -564,18 +661,25 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             // central differences (stencils after Eq. 12):
             // grad phi = sum_i c_i w_i phi(x + c_i) / T  (the -c_i half of the
             // paper's symmetric sum equals the +c_i half), lap = 2 sum w (phi_nb - phi) / T
+            // per opposite pair (I, J): phi(x + c_I) - phi(x + c_J) feeds the
+            // gradient, phi(x + c_I) + phi(x + c_J) - 2 phi the Laplacian
             R gx = 0, gy = 0, gz = 0, lap = 0;
             Unroll<1, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                constexpr double W = L::w[i];
-                const int slot = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
-                const R v = phis[slot][ly + CY][lx + CX];
-                const R wv = (R)W * v;
-                if (CX) gx += (R)CX * wv;
-                if (CY) gy += (R)CY * wv;
-                if (CZ) gz += (R)CZ * wv;
-                lap += (R)W * (v - s.phi);
+                constexpr int o = L::op[i];
+                if constexpr (i < o) {
+                    constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+                    constexpr double W = L::w[i];
+                    const int slot_p = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
+                    const int slot_m = CZ == 0 ? s0 : (CZ > 0 ? sm : sp);
+                    const R vp = phis[slot_p][ly + CY][lx + CX];
+                    const R vm = phis[slot_m][ly - CY][lx - CX];
+                    const R wd = (R)W * (vp - vm);
+                    if (CX) gx += cmul<CX>(wd);
+                    if (CY) gy += cmul<CY>(wd);
+                    if (CZ) gz += cmul<CZ>(wd);
+                    lap += (R)W * ((vp - s.phi) + (vm - s.phi));
+                }
             });
             s.gx = gx * (R)3;
             s.gy = gy * (R)3;
@@ -588,16 +692,38 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
             // sum_i Gamma_i = 1 from biasing the global phi)
             R hsum = 0;
-            Unroll<1, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr double W = L::w[i];
-                const R hv = hown[(j + 1) & 1][i][tid];
-                R hs, gs;
-                collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
-                hsum += hs;
-                write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
-                write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
-            });
+            if constexpr (std::is_same<R, float>::value) {
+                const PairState q = pair_state<LAT>(s, p);
+                float2 hsum2 = make_float2(0.0f, 0.0f);
+                Unroll<1, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    constexpr int o = L::op[i];
+                    if constexpr (i < o) {
+                        constexpr double W = L::w[i];
+                        const float2 hv = make_float2(hown[(j + 1) & 1][i][tid], hown[(j + 1) & 1][o][tid]);
+                        float2 hs, gs;
+                        collide_pair<LAT, i>(s, q, hv, &hs, &gs);
+                        hsum2 = add2(hsum2, hs);
+                        const R hsh = (R)W * p.h_shift, gsh = (R)W * p.g_shift;
+                        write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.x, hsh, (R)1));
+                        write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.y, hsh, (R)1));
+                        write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.x, gsh, p.g_scale));
+                        write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.y, gsh, p.g_scale));
+                    }
+                });
+                hsum = hsum2.x + hsum2.y;
+            } else {
+                Unroll<1, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    constexpr double W = L::w[i];
+                    const R hv = hown[(j + 1) & 1][i][tid];
+                    R hs, gs;
+                    collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
+                    hsum += hs;
+                    write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
+                    write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
+                });
+            }
             {
                 constexpr double W0 = L::w[0];
                 R hs, gs;

@@ -15,31 +15,42 @@ namespace {
 
 #if LBM_LAT == 1
 // D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
-// the bulk tensor copy pipeline.
-#define LBM_TILES(X)        \
-    X(0, hoist, 32, 4, 4)   \
-    X(1, split, 32, 4, 8)   \
-    X(2, split, 32, 8, 4)   \
-    X(3, split, 32, 4, 6)   \
-    X(4, tma, 32, 4, 2)     \
-    X(5, tma, 32, 8, 1)     \
-    X(6, tma, 64, 4, 1)     \
-    X(7, tma, 32, 2, 3)
+// the bulk tensor copy pipeline, 8-11 are tiles 0-3 as a balanced persistent
+// launch.
+#define LBM_TILES(X)         \
+    X(0, hoist, 32, 4, 4)    \
+    X(1, split, 32, 4, 8)    \
+    X(2, split, 32, 8, 4)    \
+    X(3, split, 32, 4, 6)    \
+    X(4, tma, 32, 4, 2)      \
+    X(5, tma, 32, 8, 1)      \
+    X(6, tma, 64, 4, 1)      \
+    X(7, tma, 32, 2, 3)      \
+    X(8, hoistbal, 32, 4, 4) \
+    X(9, splitbal, 32, 4, 8) \
+    X(10, splitbal, 32, 8, 4) \
+    X(11, splitbal, 32, 4, 6)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
-#define LBM_TILES(X)        \
-    X(0, hoist, 128, 1, 4)  \
-    X(1, split, 128, 1, 8)  \
-    X(2, split, 256, 1, 4)  \
-    X(3, split, 64, 1, 16)  \
-    X(4, tma, 128, 1, 2)    \
-    X(5, tma, 64, 1, 4)     \
-    X(6, tma, 192, 1, 1)    \
-    X(7, tma, 32, 1, 6)
+#define LBM_TILES(X)           \
+    X(0, hoist, 128, 1, 4)     \
+    X(1, split, 128, 1, 8)     \
+    X(2, split, 256, 1, 4)     \
+    X(3, split, 64, 1, 16)     \
+    X(4, tma, 128, 1, 2)       \
+    X(5, tma, 64, 1, 4)        \
+    X(6, tma, 192, 1, 1)       \
+    X(7, tma, 32, 1, 6)        \
+    X(8, hoistbal, 128, 1, 4)  \
+    X(9, splitbal, 128, 1, 8)  \
+    X(10, splitbal, 256, 1, 4) \
+    X(11, splitbal, 64, 1, 16)
 #endif
 
-#define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true>(a)
-#define LBM_LAUNCH_split(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false>(a)
+#define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false>(a)
+#define LBM_LAUNCH_split(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false>(a)
+#define LBM_LAUNCH_hoistbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, true>(a)
+#define LBM_LAUNCH_splitbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true>(a)
 #define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
@@ -53,6 +64,8 @@ cudaError_t step_dispatch(const StepArgs& a) {
 
 #define LBM_MAPS_hoist(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_split(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_hoistbal(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_splitbal(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
 #define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_MAPS_##KIND(TX, TY);
@@ -66,6 +79,8 @@ cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, 
 
 #define LBM_OK_hoist(TX, TY) false
 #define LBM_OK_split(TX, TY) false
+#define LBM_OK_hoistbal(TX, TY) false
+#define LBM_OK_splitbal(TX, TY) false
 #define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_OK_##KIND(TX, TY);
@@ -81,13 +96,15 @@ bool ok_dispatch(int tile, const Geom& G) {
 #define LBM_TY(ID, KIND, TX, TY, MB) TY,
 #define LBM_ISTMA_hoist 0
 #define LBM_ISTMA_split 0
+#define LBM_ISTMA_hoistbal 0
+#define LBM_ISTMA_splitbal 0
 #define LBM_ISTMA_tma 1
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
 
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
                             Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
-                            Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo, 8,
+                            Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
                             {LBM_TILES(LBM_TMA)}};
 

@@ -236,16 +236,17 @@ def test_config1_static_droplet_f64(lbm):
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_tile_shapes_agree(lbm, lat_id, shape, bc):
     """Every compiled CTA shape (per-thread loads, tiles 0-3; bulk tensor
-    copies, tiles 4-7) and z-chunk length computes the same arithmetic: FP64
-    results agree to rounding (the compiler may contract a*b+c differently
-    per instantiation)."""
+    copies, tiles 4-7; balanced persistent launches of tiles 0-3, tiles 8-11)
+    and z-chunk length computes the same arithmetic: FP64 results agree to
+    rounding (the compiler may contract a*b+c differently per instantiation)."""
     ref = None
-    for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (5, 1), (6, 1), (7, 1)):
+    for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (5, 1), (6, 1), (7, 1),
+                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            assert e.code == lbm.ENOTSUP and tile >= 4
+            assert e.code == lbm.ENOTSUP and 4 <= tile <= 7
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
