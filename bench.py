@@ -14,6 +14,10 @@ and no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--workload batch512 times instead 512 uneven D2Q9 grids (sides 32-512,
+48.3 M nodes) stepped as one batch: one persistent launch per step, replayed
+from a CUDA graph, against one single-grid launch per grid and step.
+
 N > 1 runs one independent replica per GPU (launched by torchrun; weak
 scaling): the single-domain step has no data-parallel split without a halo
 exchange, which this build does not implement.
@@ -52,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="fixed step tile (skips the autotuner)")
     ap.add_argument("--lz", type=int, default=16, help="planes per CTA chunk with --tile")
+    ap.add_argument("--workload", choices=["bubble128", "batch512"], default="bubble128",
+                    help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
+                         "stepped as one batch")
     return ap.parse_args()
 
 
@@ -311,9 +318,192 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batch512
+BATCH_METRIC = "D2Q9 batched phase-field LB throughput (GLUPS), 512 uneven static drop/bubble grids"
+BATCH_WORKLOAD = ("512 independent periodic D2Q9 grids, side L uniform in [32, 512], drop or bubble of radius "
+                  "L/4 +- U(0, L/16), density ratio log-uniform in [10, 1000], tau uniform in [0.51, 0.8], "
+                  "W in {3, 4, 5}, sigma = 0.01, M = 0.1; one persistent launch per step over all grids")
+
+
+def batch_inputs(lbm, store):
+    from paper_1812_00118_gb300 import inputs as I
+    cases = I.batch_cases(512)
+    shapes, params, fields = [], [], []
+    for c in cases:
+        L = c["L"]
+        nu = (c["tau"] - 0.5) / 3.0
+        params.append(lbm.make_params(M=0.1, W=c["W"], sigma=0.01, rho_L=1.0 / c["rho_ratio"], rho_H=1.0,
+                                      nu_L=nu, nu_H=nu, store=store))
+        shapes.append((L, L))
+        fields.append(I.sphere((1, L, L), (L / 2 + 0.31, L / 2 - 0.23, 0), c["R"], c["W"], drop=c["drop"]))
+    return cases, shapes, params, fields
+
+
+def batch_oracle_glups(n_cases, steps):
+    """The FP64 oracle on the first n_cases grids of the workload, `steps` steps each."""
+    from oracle import lattice as OL
+    from oracle import pflbm as O
+    from paper_1812_00118_gb300 import inputs as I
+    cases = I.batch_cases(512)[:n_cases]
+    t, nodes = 0.0, 0
+    for c in cases:
+        L = c["L"]
+        nu = (c["tau"] - 0.5) / 3.0
+        p = O.Params(M=0.1, W=c["W"], sigma=0.01, rho_L=1.0 / c["rho_ratio"], rho_H=1.0, nu_L=nu, nu_H=nu,
+                     bc=("periodic", "periodic", "periodic"))
+        phi, u, P = I.sphere((1, L, L), (L / 2 + 0.31, L / 2 - 0.23, 0), c["R"], c["W"], drop=c["drop"])
+        h, g = O.init_populations(phi, u, P, OL.D2Q9, p)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            h, g = O.step(h, g, OL.D2Q9, p)
+        t += time.perf_counter() - t0
+        nodes += L * L
+    return nodes * steps / t / 1e9, t, nodes
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1812_00118_gb300 import build, lbm
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    lbm.load()
+    store = {"f64": lbm.F64, "f32": lbm.F32, "f16s": lbm.F16S, "bf16s": lbm.BF16S}[args.store]
+    cases, shapes, params, fields = batch_inputs(lbm, store)
+    N = sum(a * b for a, b in shapes)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = lbm.Batch(shapes, params, stream=stream.cuda_stream)
+        for k, (phi, u, P) in enumerate(fields):
+            b.grid(k).init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u[:2].reshape(-1)),
+                                  np.ascontiguousarray(P.reshape(-1)))
+        if args.tile is None:
+            tile, lz, _ = b.autotune(5)
+        else:
+            b.set_tile(args.tile, args.lz)
+            tile, lz = args.tile, args.lz
+        b.set_graph(10)
+        b.step(args.warmup)
+        stream.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        time.sleep(0.3)
+        n0 = b.launch_count()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        b.step(args.steps)
+        end.record(stream)
+        end.synchronize()
+        launches = b.launch_count() - n0
+        clk = clocks.stop()
+        ms = start.elapsed_time(end)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        # the same grids as one launch of the single-grid kernel per grid and step
+        k_seq = max(3, min(args.steps, 20))
+        b.step_sequential(2)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        b.step_sequential(k_seq)
+        s1.record(stream)
+        s1.synchronize()
+        seq_ms = s0.elapsed_time(s1) / k_seq
+        diag = [b.grid(k).diagnostics(raise_on_divergence=False) for k in range(len(shapes))]
+        # end to end: pinned host fields of every grid in, K steps, every grid's fields out
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host_in = [(pin(phi.reshape(-1)), pin(u[:2].reshape(-1)), pin(P.reshape(-1))) for phi, u, P in fields]
+        host_out = [tuple(torch.empty(n, dtype=torch.float64).pin_memory() for n in (a * c, a * c, 2 * a * c))
+                    for a, c in shapes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, (hp, hu, hP) in enumerate(host_in):
+            b.grid(k).init_fields(hp, hu, hP)
+        b.step(args.steps)
+        for k, (op, oP, ou) in enumerate(host_out):
+            b.grid(k).macro(op, oP, ou)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+    total_lu = float(N) * args.steps * world
+    glups = total_lu / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    per_launch_ms = ms / args.steps
+    alg_bytes = BYTES_PER_LU[args.store] * 9 // 19 * N
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": BATCH_METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.store, "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "nodes": N, "grids": len(shapes), "parallelism": f"replicas x{world}",
+                   "tile": {"id": tile, "lz": lz, "cta": b.get_tile()[2], "items": b.get_tile()[3]},
+                   "graph_steps": 10,
+                   "l2": "inputs larger than L2 (%.1f GB of populations move per step)" % (alg_bytes / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "persistent batch step kernel (D2Q9)",
+                     "alg_bytes_per_launch": alg_bytes, "mean_launch_ms": per_launch_ms},
+        "sequential": {"value": float(N) / (seq_ms * 1e-3) / 1e9, "unit": "GLUPS", "ms_per_step": seq_ms,
+                       "launches_per_step": len(shapes),
+                       "note": "one single-grid step launch per grid and step, same storage"},
+        "clocks": clk,
+        "e2e": {"value": total_lu / e2e_s / 1e9, "unit": "GLUPS",
+                "h2d_bytes_per_step": 4 * 8 * N / args.steps, "d2h_bytes_per_step": 4 * 8 * N / args.steps,
+                "note": "init of every grid from pinned host phi,u,P + K steps + every grid's fields to pinned host"},
+        "gpu_launches": launches,
+        "diagnostics": {"nonfinite": sum(d["nonfinite"] for d in diag),
+                        "max_u": max(d["max_u"] for d in diag)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, dt, nodes = batch_oracle_glups(8, 3)
+        line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"3 oracle steps on the first 8 grids ({nodes} nodes, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_batch_reference(args):
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return
+    # grids of the workload in order, as many as fit ~90 s over warmup + steps at ~3 us/node
+    from paper_1812_00118_gb300 import inputs as I
+    budget, cost = 90.0 / max(1, args.steps + args.warmup), 3e-6
+    n, acc = 0, 0
+    for c in I.batch_cases(512):
+        if n > 0 and (acc + c["L"] ** 2) * cost > budget:
+            break
+        acc += c["L"] ** 2
+        n += 1
+    batch_oracle_glups(n, args.warmup) if args.warmup else None
+    glups, dt, nodes = batch_oracle_glups(n, args.steps)
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "sample": f"the first {n} grids ({nodes} nodes) per step"},
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps on the first {n} grids ({nodes} nodes)"},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "batch512":
+        (run_batch_reference if args.impl == "reference" else run_batch)(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -56,6 +56,7 @@ enum lbm_status {
 };
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 
 /* Grid: nx, ny, nz >= 1 (nz == 1 for D2Q9).  bc[a] is the boundary type of
  * both ends of axis a (0 = x, 1 = y, 2 = z).  A walled axis has halfway
@@ -226,6 +227,75 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
 int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
                            const double* v2, long long n, double rho_L, double rho_dif, double* out,
                            void* cuda_stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent D2Q9 grids stepped together (the paper runs its 2-D cases
+ * one at a time; batching them is a service of the library, the arithmetic
+ * of every grid is that of lbm_step).  The grids share one set of population
+ * arrays, each grid in its own ghost-padded block.  A step is ONE launch of a
+ * persistent kernel whose CTAs take work items (grid, tile column, chunk of
+ * planes) from a list in device memory, so that grids of any size mix
+ * without idle launches.
+ *
+ * lbm_batch_create: n >= 1 grids, grids[i] and params[i] as for lbm_create
+ * with lattice LBM_D2Q9 (nz = 1).  Every params[i].store must be the same.
+ * Arrays are copied; the caller keeps ownership.  Allocates the population
+ * arrays of all grids (4 x 9 x sum of padded grid sizes values).  Errors:
+ * LBM_EINVAL (n < 1, a bad grid or parameter block, mixed storage, padded
+ * total >= 2^31 cells), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_create(int n, const lbm_grid* grids, const lbm_params* params, void* cuda_stream,
+                     lbm_batch** out);
+
+/* The context of grid i of the batch, owned by the batch (NULL if i is out
+ * of range).  It accepts every per-grid call: lbm_init_fields,
+ * lbm_set_populations, lbm_get_populations, lbm_macro, lbm_diagnostics,
+ * lbm_laplace, lbm_get_tile.  lbm_step, lbm_step_profiled, lbm_autotune and
+ * lbm_set_tile on it return LBM_EINVAL (the batch steps all its grids), and
+ * lbm_destroy on it does nothing. */
+lbm_ctx* lbm_batch_grid(lbm_batch* b, int i);
+
+/* Advance every grid by n >= 0 steps: one persistent launch per step, or,
+ * after lbm_batch_set_graph(b, k) with k >= 1, replays of a CUDA graph of k
+ * steps (and single launches for the remainder).  Stream-ordered.  Errors:
+ * LBM_EINVAL, LBM_ECUDA. */
+int lbm_batch_step(lbm_batch* b, int n);
+
+/* The same n steps as one launch of the single-grid step kernel (tile 1,
+ * lz 16) per grid and step: the reference to compare the batch against.  */
+int lbm_batch_step_sequential(lbm_batch* b, int n);
+
+/* Batch step kernel: tile 0-3 = CTAs of 64, 128, 32 threads along x (in
+ * phases) and 128 (g loads held across the phi fill); lz >= 1 planes per
+ * work item.  Rebuilds the work list.  lbm_batch_get_tile also reports the
+ * CTA width and the number of work items (any pointer may be NULL).
+ * Errors: LBM_EINVAL. */
+int lbm_batch_set_tile(lbm_batch* b, int tile, int lz);
+int lbm_batch_get_tile(const lbm_batch* b, int* tile, int* lz, int* tx, int* n_items);
+
+/* k >= 1: lbm_batch_step replays a CUDA graph of k step launches (captured
+ * on a private stream on first use for each buffer parity, launched on the
+ * batch stream); k = 0: single launches.  Errors: LBM_EINVAL (k < 0). */
+int lbm_batch_set_graph(lbm_batch* b, int k);
+
+/* Times every batch tile with lz in {4, 8, 16, 32} for `steps` steps each,
+ * keeps the fastest, and restores the state it started from.  Reports the
+ * choice and its time per step in ms (any pointer may be NULL).
+ * Synchronises.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_autotune(lbm_batch* b, int steps, int* best_tile, int* best_lz, double* best_ms);
+
+/* Kernel launches issued by the batch steps (graph replays count their
+ * kernels). */
+long long lbm_batch_launch_count(const lbm_batch* b);
+
+/* The work list of a batch, computed on the host (no GPU needed): for grids
+ * (D2Q9, internal axes x = user x, z = user y), CTA width tx >= 1 and lz >= 1,
+ * the items in launch order, 4 ints each: grid index, first x, first z,
+ * end z (exclusive); per grid, z chunks in order and within a chunk the
+ * tile columns in order.  Writes at most max_items items (items may be NULL
+ * with max_items = 0) and returns the total number of items, or LBM_EINVAL. */
+int lbm_batch_plan(int n, const lbm_grid* grids, int tx, int lz, int* items, int max_items);
+
+void lbm_batch_destroy(lbm_batch* b);
 
 void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_strerror(int status);

@@ -16,38 +16,7 @@
 
 using namespace lbm;
 
-struct lbm_ctx {
-    int lattice = 0;
-    int store = 0;
-    int dim = 3;
-    lbm_grid grid{};       // user grid
-    lbm_params params{};
-    Geom G{};              // internal grid
-    Phys P{};
-    const KernelTable* K = nullptr;
-    cudaStream_t stream = nullptr;
-    size_t elem = 0;       // bytes per stored population value
-    void* h[2] = {nullptr, nullptr};
-    void* g[2] = {nullptr, nullptr};
-    int cur = 0;           // buffer holding the current state
-    int tile = 0;          // step tile shape index
-    int lz = 16;           // planes per CTA chunk
-    TmaMaps maps[2];       // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
-    int maps_tile = -1;    // tile the maps were made for
-    bool ghosts[2] = {false, false};   // ghost band of buffer b holds the periodic images
-    int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
-    double* fields = nullptr;    // scratch: phi, P, ux, uy, uz (5 N doubles)
-    double* partial = nullptr;   // scratch: reduction partials
-    int n_partial_blocks = 0;
-    long long launches = 0;
-};
-
-namespace {
-
-constexpr double kT = 1.0 / 3.0;
-
-int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
-
+namespace lbm {
 const KernelTable* table_for(int lattice, int store) {
     switch (lattice * 4 + store) {
         case 0: return table_l0_s0();
@@ -61,6 +30,15 @@ const KernelTable* table_for(int lattice, int store) {
         default: return nullptr;
     }
 }
+}  // namespace lbm
+
+
+namespace {
+
+constexpr double kT = 1.0 / 3.0;
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
 
 size_t elem_size(int store) {
     switch (store) {
@@ -262,6 +240,65 @@ int update_rho_bar(lbm_ctx* c) {
 
 }  // namespace
 
+namespace lbm {
+
+// Everything of lbm_create but the device buffers: checks, model constants,
+// internal geometry (ghost-padded, base 0) and kernel table.
+int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream) {
+    if (!grid || !params) return LBM_EINVAL;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return LBM_EINVAL;
+    if (lattice == LBM_D2Q9 && grid->nz != 1) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (grid->bc[a] != LBM_PERIODIC && grid->bc[a] != LBM_WALL) return LBM_EINVAL;
+    Phys P;
+    int rc = derive(*params, lattice, &P);
+    if (rc) return rc;
+    c->lattice = lattice;
+    c->store = params->store;
+    c->dim = lattice == LBM_D2Q9 ? 2 : 3;
+    c->grid = *grid;
+    c->params = *params;
+    c->P = P;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->elem = elem_size(params->store);
+    if (lattice == LBM_D2Q9) {
+        c->G.NX = grid->nx; c->G.NY = 1; c->G.NZ = grid->ny;
+        c->G.wall[0] = grid->bc[0] == LBM_WALL; c->G.wall[1] = 0; c->G.wall[2] = grid->bc[1] == LBM_WALL;
+        c->K = table_for(0, params->store);
+        c->lz = 16;
+    } else {
+        c->G.NX = grid->nx; c->G.NY = grid->ny; c->G.NZ = grid->nz;
+        for (int a = 0; a < 3; ++a) c->G.wall[a] = grid->bc[a] == LBM_WALL;
+        c->K = table_for(1, params->store);
+        c->lz = 16;
+    }
+    // ghost padding (see lbm_kernels.cuh): x ghosts of 32 bytes (at least 2
+    // cells), rows padded to 32 bytes; y ghosts 2 cells (D3Q19); one ghost
+    // plane at each z end
+    {
+        // x ghosts: 32 bytes of storage (at least 2 cells), so every row of
+        // nodes starts on a 32-byte sector and warps write whole sectors
+        const int A32 = (int)(32 / c->elem);            // elements per 32 bytes
+        c->G.GX = A32 > 2 ? A32 : 2;
+        c->G.GY = lattice == LBM_D2Q9 ? 0 : 2;
+        c->G.GZ = 1;
+        c->G.PX = ((c->G.NX + A32 - 1) / A32) * A32 + 2 * c->G.GX;
+        c->G.PY = c->G.NY + 2 * c->G.GY;
+        c->G.PZ = c->G.NZ + 2 * c->G.GZ;
+        c->G.PXY = c->G.PX * c->G.PY;
+        c->G.NP = (long long)c->G.PXY * c->G.PZ;
+    }
+    c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
+    if (!c->K || c->G.NP >= (1LL << 31)) return LBM_EINVAL;
+    // default: per-thread loads in phases, 8 CTAs per SM (the fastest tile on
+    // the measured grids; lbm_autotune picks per grid)
+    c->tile = 1;
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_strerror(int s) {
@@ -300,55 +337,12 @@ int lbm_lattice_info(int lattice, int* Q, int* c, double* w) {
 }
 
 int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream, lbm_ctx** out) {
-    if (!grid || !params || !out) return LBM_EINVAL;
+    if (!out) return LBM_EINVAL;
     *out = nullptr;
-    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return LBM_EINVAL;
-    if (lattice == LBM_D2Q9 && grid->nz != 1) return LBM_EINVAL;
-    for (int a = 0; a < 3; ++a)
-        if (grid->bc[a] != LBM_PERIODIC && grid->bc[a] != LBM_WALL) return LBM_EINVAL;
-    Phys P;
-    int rc = derive(*params, lattice, &P);
-    if (rc) return rc;
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ENOMEM;
-    c->lattice = lattice;
-    c->store = params->store;
-    c->dim = lattice == LBM_D2Q9 ? 2 : 3;
-    c->grid = *grid;
-    c->params = *params;
-    c->P = P;
-    c->stream = (cudaStream_t)cuda_stream;
-    c->elem = elem_size(params->store);
-    if (lattice == LBM_D2Q9) {
-        c->G.NX = grid->nx; c->G.NY = 1; c->G.NZ = grid->ny;
-        c->G.wall[0] = grid->bc[0] == LBM_WALL; c->G.wall[1] = 0; c->G.wall[2] = grid->bc[1] == LBM_WALL;
-        c->K = table_for(0, params->store);
-        c->lz = 16;
-    } else {
-        c->G.NX = grid->nx; c->G.NY = grid->ny; c->G.NZ = grid->nz;
-        for (int a = 0; a < 3; ++a) c->G.wall[a] = grid->bc[a] == LBM_WALL;
-        c->K = table_for(1, params->store);
-        c->lz = 16;
-    }
-    // ghost padding (see lbm_kernels.cuh): x ghosts of 32 bytes (at least 2
-    // cells), rows padded to 32 bytes; y ghosts 2 cells (D3Q19); one ghost
-    // plane at each z end
-    {
-        // x ghosts: 32 bytes of storage (at least 2 cells), so every row of
-        // nodes starts on a 32-byte sector and warps write whole sectors
-        const int A32 = (int)(32 / c->elem);            // elements per 32 bytes
-        c->G.GX = A32 > 2 ? A32 : 2;
-        c->G.GY = lattice == LBM_D2Q9 ? 0 : 2;
-        c->G.GZ = 1;
-        c->G.PX = ((c->G.NX + A32 - 1) / A32) * A32 + 2 * c->G.GX;
-        c->G.PY = c->G.NY + 2 * c->G.GY;
-        c->G.PZ = c->G.NZ + 2 * c->G.GZ;
-        c->G.PXY = c->G.PX * c->G.PY;
-        c->G.NP = (long long)c->G.PXY * c->G.PZ;
-    }
-    c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
-    if (!c->K || c->G.NP >= (1LL << 31)) { delete c; return LBM_EINVAL; }
+    int rc = ctx_setup(c, grid, lattice, params, cuda_stream);
+    if (rc) { delete c; return rc; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
     const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
     for (int b = 0; b < 2; ++b) {
@@ -368,15 +362,12 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
     }
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) { lbm_destroy(c); return LBM_ECUDA; }
-    // default: per-thread loads in phases, 8 CTAs per SM (the fastest tile on
-    // the measured grids; lbm_autotune picks per grid)
-    c->tile = 1;
     *out = c;
     return LBM_OK;
 }
 
 void lbm_destroy(lbm_ctx* c) {
-    if (!c) return;
+    if (!c || c->owner) return;
     for (int b = 0; b < 2; ++b) {
         if (c->h[b]) cudaFreeAsync(c->h[b], c->stream);
         if (c->g[b]) cudaFreeAsync(c->g[b], c->stream);
@@ -407,11 +398,13 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
         if (rc) return rc;
         c->P.rho_bar = c->P.rho_L + c->P.rho_dif * d[0] / (double)N;
     }
-    c->cur = 0;
-    if (check_cuda(c->K->init(c->h[0], c->g[0], c->G, c->P, f_phi(c), f_u(c, 0), f_u(c, 1), f_u(c, 2), f_P(c),
+    // the state is written into the current buffer (for a grid of a batch,
+    // the buffer all its grids hold the state in)
+    const int b = c->cur;
+    if (check_cuda(c->K->init(c->h[b], c->g[b], c->G, c->P, f_phi(c), f_u(c, 0), f_u(c, 1), f_u(c, 2), f_P(c),
                               c->stream)))
         return LBM_ECUDA;
-    c->ghosts[0] = true;   // the initialisation writes the periodic images too
+    c->ghosts[b] = true;   // the initialisation writes the periodic images too
     c->launches += 1;
     return check_cuda(cudaStreamSynchronize(c->stream));
 }
@@ -421,7 +414,7 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev);
 int lbm_step(lbm_ctx* c, int n) { return step_impl(c, n, nullptr); }
 
 int lbm_step_profiled(lbm_ctx* c, int n, double* kernel_ms) {
-    if (!c || n < 0 || !kernel_ms) return LBM_EINVAL;
+    if (!c || n < 0 || !kernel_ms || c->owner) return LBM_EINVAL;
     cudaEvent_t* ev = (cudaEvent_t*)calloc(2 * (size_t)(n > 0 ? n : 1), sizeof(cudaEvent_t));
     if (!ev) return LBM_ENOMEM;
     int rc = LBM_OK;
@@ -442,7 +435,7 @@ int lbm_step_profiled(lbm_ctx* c, int n, double* kernel_ms) {
 }
 
 static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
-    if (!c || n < 0) return LBM_EINVAL;
+    if (!c || n < 0 || c->owner) return LBM_EINVAL;
     const bool tma = c->K->tile_tma[c->tile] != 0;
     if (tma && c->maps_tile != c->tile) {
         for (int b = 0; b < 2; ++b)
@@ -548,9 +541,9 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
         cudaMemcpyAsync(tg, g, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         dh = th; dg = tg;
     }
-    c->cur = 0;
-    int rc = check_cuda(c->K->set(c->h[0], c->g[0], c->G, c->P, dh, dg, c->stream));
-    c->ghosts[0] = true;
+    const int b = c->cur;
+    int rc = check_cuda(c->K->set(c->h[b], c->g[b], c->G, c->P, dh, dg, c->stream));
+    c->ghosts[b] = true;
     c->launches += 1;
     if (th) { cudaFreeAsync(th, c->stream); cudaFreeAsync(tg, c->stream); }
     if (!rc && c->P.force_mode == 1) {
@@ -596,7 +589,7 @@ int lbm_laplace(lbm_ctx* c, const double centre[3], double r_in, double r_out, d
 }
 
 int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* best_ms) {
-    if (!c || steps < 1) return LBM_EINVAL;
+    if (!c || steps < 1 || c->owner) return LBM_EINVAL;
     // the trials advance the state: keep a copy and restore it afterwards
     const int Q = c->lattice == LBM_D2Q9 ? 9 : 19;
     const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
@@ -659,7 +652,7 @@ void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
 // Step tile shape and z-chunk length (used by the tuner and the tests).
 int lbm_set_tile(lbm_ctx* c, int tile, int lz) {
-    if (!c || tile < 0 || tile >= c->K->n_tiles || lz < 1) return LBM_EINVAL;
+    if (!c || tile < 0 || tile >= c->K->n_tiles || lz < 1 || c->owner) return LBM_EINVAL;
     if (c->K->tile_tma[tile] && !c->K->tma_ok(tile, c->G)) return LBM_ENOTSUP;
     c->tile = tile;
     c->lz = lz;

@@ -4,6 +4,8 @@
 #pragma once
 #include <cudaTypedefs.h>
 
+#include <new>
+
 #include "lbm_internal.h"
 #include "lbm_tma.cuh"
 
@@ -44,6 +46,46 @@ cudaError_t launch_step_tile(const StepArgs& a) {
     const auto ph = phys_as<typename Storage<ST>::R>(a.p);
     kern<<<grid, block, 0, a.stream>>>(d, G, ph, a.lz);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batches
+// One CTA per resident slot (occupancy x SMs, looked up once per
+// instantiation), at most one per work item.
+template <int LAT, int ST, int TX, int MINB, bool HOIST>
+cudaError_t launch_batch_tile(const BatchArgs& a) {
+    using S = typename Storage<ST>::S;
+    using R = typename Storage<ST>::R;
+    auto kern = batch_step_kernel<LAT, ST, TX, MINB, HOIST>;
+    static int slots = -1;
+    if (slots < 0) {
+        int dev = 0, sms = 0, occ = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, 0);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        slots = sms * occ;
+    }
+    if (a.n_items < 1) return cudaSuccess;
+    const int nb = a.n_items < slots ? a.n_items : slots;
+    kern<<<nb, TX, 0, a.stream>>>(dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, a.NP),
+                                  (const BatchCase<R>*)a.cases, (const BatchItem*)a.items, a.n_items, a.counters);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t batch_upload(const Geom* G, const Phys* P, int n, void* d_cases, cudaStream_t s) {
+    using R = typename Storage<ST>::R;
+    BatchCase<R>* h = new (std::nothrow) BatchCase<R>[n > 0 ? n : 1];
+    if (!h) return cudaErrorMemoryAllocation;
+    for (int i = 0; i < n; ++i) {
+        h[i].G = G[i];
+        h[i].p = phys_as<R>(P[i]);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_cases, h, sizeof(BatchCase<R>) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] h;
+    return e;
 }
 
 // ---------------------------------------------------------------- bulk-copy tiles

@@ -3,7 +3,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -24,6 +26,23 @@ struct StepArgs {
     const TmaMaps* maps;   // tensor maps of (hin, gin) for a bulk-copy tile
     int* error_flag;       // raised by a bounded wait that gave up
 };
+
+// Everything one batch step launch needs (see batch_step_kernel).
+struct BatchArgs {
+    const void* hin;
+    const void* gin;
+    void* hout;
+    void* gout;
+    long long NP;          // stride between population arrays of the batch
+    const void* cases;     // device array of BatchCase<R>, one per grid
+    const void* items;     // device array of BatchItem
+    int n_items;
+    int* counters;         // two device ints, zero between launches
+    int tile;
+    cudaStream_t stream;
+};
+
+constexpr int kMaxBatchTiles = 4;
 
 struct KernelTable {
     cudaError_t (*step)(const StepArgs& a);
@@ -46,6 +65,13 @@ struct KernelTable {
     int n_tiles;            // number of compiled step tile shapes
     int tile_tx[kMaxTiles], tile_ty[kMaxTiles];
     int tile_tma[kMaxTiles];   // 1: bulk tensor copy pipeline, 0: per-thread loads
+    // batches of grids (D2Q9; null and 0 for D3Q19)
+    cudaError_t (*batch_step)(const BatchArgs& a);
+    // BatchCase<R> of n grids from their geometries and parameters into d_cases
+    cudaError_t (*batch_upload)(const Geom* G, const Phys* P, int n, void* d_cases, cudaStream_t s);
+    size_t batch_case_bytes;
+    int n_batch_tiles;
+    int batch_tile_tx[kMaxBatchTiles];
 };
 
 // One table per (lattice, storage), each defined in its own compilation of
@@ -61,4 +87,40 @@ const KernelTable* table_l1_s1();
 const KernelTable* table_l1_s2();
 const KernelTable* table_l1_s3();
 
+}  // namespace lbm
+
+// State of one simulation (host side of the C-ABI handle).
+struct lbm_ctx {
+    int lattice = 0;
+    int store = 0;
+    int dim = 3;
+    lbm_grid grid{};       // user grid
+    lbm_params params{};
+    lbm::Geom G{};         // internal grid
+    lbm::Phys P{};
+    const lbm::KernelTable* K = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t elem = 0;       // bytes per stored population value
+    void* h[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;           // buffer holding the current state
+    int tile = 0;          // step tile shape index
+    int lz = 16;           // planes per CTA chunk
+    lbm::TmaMaps maps[2];  // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
+    int maps_tile = -1;    // tile the maps were made for
+    bool ghosts[2] = {false, false};   // ghost band of buffer b holds the periodic images
+    int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
+    double* fields = nullptr;    // scratch: phi, P, ux, uy, uz (5 N doubles)
+    double* partial = nullptr;   // scratch: reduction partials
+    int n_partial_blocks = 0;
+    long long launches = 0;
+    lbm_batch* owner = nullptr;  // set for the view of one grid of a batch: the
+                                 // buffers and scratch belong to the batch,
+                                 // which alone steps them
+};
+
+namespace lbm {
+const KernelTable* table_for(int lattice, int store);
+// lbm_create without the buffers (checks, constants, geometry, tables)
+int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream);
 }  // namespace lbm

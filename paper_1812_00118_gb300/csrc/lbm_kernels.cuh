@@ -37,9 +37,13 @@ struct Geom {
     int GX, GY, GZ;   // ghost widths
     int PX, PY, PZ;   // padded extents
     int PXY;          // PX * PY
-    long long NP;     // PX * PY * PZ (< 2^31, checked on the host)
+    long long NP;     // stride between population arrays (< 2^31, checked on
+                      // the host): PX * PY * PZ, or for a grid of a batch the
+                      // padded size of all its grids
     long long N;      // NX * NY * NZ
     int wall[3];
+    int base;         // offset of this grid's padded block in each population
+                      // array (0, or the sum of the blocks before it in a batch)
 };
 
 // ---------------------------------------------------------------- parameters
@@ -145,7 +149,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(co
 
 // Padded flat offset of (possibly ghost) coordinates.
 __device__ __forceinline__ int pidx(const Geom& G, int x, int y, int z) {
-    return ((z + G.GZ) * G.PY + (y + G.GY)) * G.PX + (x + G.GX);
+    return G.base + ((z + G.GZ) * G.PY + (y + G.GY)) * G.PX + (x + G.GX);
 }
 
 // Plane a pull from z - cz reads: wrapped when z is periodic, the ghost plane
@@ -228,7 +232,7 @@ __device__ __forceinline__ PullOffsets pull_offsets(const Geom& G, int x, int y,
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int c = k - 1;
-        o.z[k] = (pull_plane(G, z - c) + G.GZ) * G.PXY;
+        o.z[k] = G.base + (pull_plane(G, z - c) + G.GZ) * G.PXY;
         o.r[k] = (wrap1(y - c, G.NY, G.wall[1]) + G.GY) * G.PX;
         o.c[k] = wrap1(x - c, G.NX, G.wall[0]) + G.GX;
     }
@@ -534,27 +538,32 @@ __device__ __forceinline__ void collide_pair(const NodeState<float>& s, const Pa
 // hit L2.  BAL (one-wave launch): gridDim.z chunks of NZ / gridDim.z planes
 // (rounded), the host choosing gridDim.z so that the whole grid is resident
 // at once; otherwise chunks of LZ planes.
-template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool BAL, bool WALLS>
-__global__ void __launch_bounds__(TX * TY, MINB)
-step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<typename Storage<ST>::R> p,
-            int LZ) {
+template <int LAT, int ST, int TX, int TY>
+struct MarchSmem {
+    using R = typename Storage<ST>::R;
+    static constexpr int HY = Lattice<LAT>::kHasY ? 1 : 0;
+    R phis[4][TY + 2 * HY][TX + 2];
+    // pulled h of the thread's own node on the last two filled planes: the fill
+    // of plane z+1 loads them anyway, the collision of the next iteration
+    // reads them back (each thread touches only its own column: no barrier)
+    R hown[2][Lattice<LAT>::Q][TX * TY];
+};
+
+// The march of one CTA over planes [z0, z1) of the tile column at (x0, y0).
+// Every thread of the CTA calls it with the same arguments.
+template <int LAT, int ST, int TX, int TY, bool HOIST, bool WALLS>
+__device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q>& D, const Geom& G,
+                                      const PhysT<typename Storage<ST>::R>& p, int x0, int y0, int z0, int z1,
+                                      MarchSmem<LAT, ST, TX, TY>& sm) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
-    using S = typename St::S;
     using R = typename St::R;
     constexpr int Q = L::Q;
     constexpr int HY = L::kHasY ? 1 : 0;
     constexpr int SX = TX + 2, SY = TY + 2 * HY;
-    __shared__ R phis[4][SY][SX];
-    // pulled h of the thread's own node on the last two filled planes: the fill
-    // of plane z+1 loads them anyway, the collision of the next iteration
-    // reads them back (each thread touches only its own column: no barrier)
-    __shared__ R hown[2][Q][TX * TY];
-
+    auto& phis = sm.phis;
+    auto& hown = sm.hown;
     const int tid = threadIdx.x + TX * threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = BAL ? (int)((long long)blockIdx.z * G.NZ / gridDim.z) : blockIdx.z * LZ;
-    const int z1 = BAL ? (int)((long long)(blockIdx.z + 1) * G.NZ / gridDim.z) : min(z0 + LZ, G.NZ);
 
     // phi of plane zp (unwrapped) into ring slot: every halo position is
     // mapped to the node whose phi it holds (periodic image or wall mirror)
@@ -687,7 +696,7 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
             s.lap = lap * (R)6;
             node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
             const NodeWrites nw = node_writes<LAT>(G, x, y, z);
-            const int own = (z + G.GZ) * G.PXY + rb;
+            const int own = G.base + (z + G.GZ) * G.PXY + rb;
             // moving directions first; the rest population closes sum_i h*_i = phi
             // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
             // sum_i Gamma_i = 1 from biasing the global phi)
@@ -731,6 +740,66 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
                 write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
                 write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
             }
+        }
+    }
+}
+
+template <int LAT, int ST, int TX, int TY, int MINB, bool HOIST, bool BAL, bool WALLS>
+__global__ void __launch_bounds__(TX * TY, MINB)
+step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<typename Storage<ST>::R> p,
+            int LZ) {
+    __shared__ MarchSmem<LAT, ST, TX, TY> sm;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = BAL ? (int)((long long)blockIdx.z * G.NZ / gridDim.z) : blockIdx.z * LZ;
+    const int z1 = BAL ? (int)((long long)(blockIdx.z + 1) * G.NZ / gridDim.z) : min(z0 + LZ, G.NZ);
+    march<LAT, ST, TX, TY, HOIST, WALLS>(D, G, p, x0, y0, z0, z1, sm);
+}
+
+// ---------------------------------------------------------------- batch
+// One grid of a batch: its geometry (base = its block in the shared
+// population arrays) and its parameters in the kernel's arithmetic type.
+template <typename R>
+struct BatchCase {
+    Geom G;
+    PhysT<R> p;
+};
+
+// Work item: grid c, tile column x0 (y0 = 0), planes [z0, z1).
+struct BatchItem {
+    int c, x0, z0, z1;
+};
+
+// Persistent step over a work list of many grids: CTAs take items in list
+// order from an atomic counter (counters[0]) until the list is exhausted; the
+// last CTA to finish (counted in counters[1]) sets both back to zero for the
+// next launch.  Grids of one batch share the population arrays (population i
+// of every grid at D.*[i], grid c from its base), so one parameter block
+// serves every item.  Walls are handled per grid (WALLS = true).
+template <int LAT, int ST, int TX, int MINB, bool HOIST>
+__global__ void __launch_bounds__(TX, MINB)
+batch_step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D,
+                  const BatchCase<typename Storage<ST>::R>* __restrict__ cases, const BatchItem* __restrict__ items,
+                  int n_items, int* counters) {
+    using R = typename Storage<ST>::R;
+    __shared__ MarchSmem<LAT, ST, TX, 1> sm;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&counters[0], 1);
+        __syncthreads();
+        const int k = s_item;
+        if (k >= n_items) break;
+        const BatchItem it = items[k];
+        const Geom G = cases[it.c].G;
+        const PhysT<R> p = cases[it.c].p;
+        march<LAT, ST, TX, 1, HOIST, true>(D, G, p, it.x0, 0, it.z0, it.z1, sm);
+        // the next item's fills overwrite the phi ring, and thread 0 s_item
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // every CTA counted here has made its last claim on counters[0]
+        if (atomicAdd(&counters[1], 1) == (int)gridDim.x - 1) {
+            counters[0] = 0;
+            counters[1] = 0;
         }
     }
 }

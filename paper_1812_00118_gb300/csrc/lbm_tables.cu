@@ -92,6 +92,29 @@ bool ok_dispatch(int tile, const Geom& G) {
     }
 }
 
+#if LBM_LAT == 0
+// Batches of D2Q9 grids: CTA widths along x (the grids of a batch are often
+// narrower than the single-grid tiles).
+#define LBM_BATCH_TILES(X)  \
+    X(0, false, 64, 16)     \
+    X(1, false, 128, 8)     \
+    X(2, false, 32, 32)     \
+    X(3, true, 128, 4)
+#define LBM_BATCH_CASE(ID, HOIST, TX, MB) \
+    case ID: return launch_batch_tile<LBM_LAT, LBM_ST, TX, MB, HOIST>(a);
+cudaError_t batch_dispatch(const BatchArgs& a) {
+    switch (a.tile) {
+        LBM_BATCH_TILES(LBM_BATCH_CASE)
+        default: return cudaErrorInvalidValue;
+    }
+}
+#define LBM_BATCH_TX(ID, HOIST, TX, MB) TX,
+#define LBM_BATCH_FIELDS batch_dispatch, batch_upload<LBM_ST>, sizeof(BatchCase<Storage<LBM_ST>::R>), \
+                         kMaxBatchTiles, {LBM_BATCH_TILES(LBM_BATCH_TX)}
+#else
+#define LBM_BATCH_FIELDS nullptr, nullptr, 0, 0, {0, 0, 0, 0}
+#endif
+
 #define LBM_TX(ID, KIND, TX, TY, MB) TX,
 #define LBM_TY(ID, KIND, TX, TY, MB) TY,
 #define LBM_ISTMA_hoist 0
@@ -106,7 +129,7 @@ const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
                             Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
-                            {LBM_TILES(LBM_TMA)}};
+                            {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS};
 
 }  // namespace
 

@@ -71,6 +71,19 @@ SIGNATURES = [
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
     ("lbm_field_sums_noalloc", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_longlong, ctypes.c_double,
                                               ctypes.c_double, _VP, _VP]),
+    ("lbm_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_params), _VP,
+                                        ctypes.POINTER(_VP)]),
+    ("lbm_batch_grid", _VP, [_VP, ctypes.c_int]),
+    ("lbm_batch_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_batch_step_sequential", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_batch_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("lbm_batch_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
+    ("lbm_batch_set_graph", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_batch_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
+    ("lbm_batch_launch_count", ctypes.c_longlong, [_VP]),
+    ("lbm_batch_plan", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.c_int, _IP,
+                                      ctypes.c_int]),
+    ("lbm_batch_destroy", None, [_VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -285,3 +298,130 @@ class Simulation:
     @property
     def ctx(self):
         return self._ctx
+
+
+class _GridView(Simulation):
+    """Grid i of a Batch: the per-grid calls of Simulation on the batch's
+    view context (stepping it raises; the batch steps all grids)."""
+
+    def __init__(self, batch, ctx, shape, params):
+        self.lattice = D2Q9
+        self.dim = 2
+        self.shape = (shape[0], shape[1], 1)
+        self.N = shape[0] * shape[1]
+        self.Q = 9
+        self.params = params
+        self._stream = batch._stream
+        self._ctx = ctx
+        self._batch = batch   # keeps the batch (owner of the context) alive
+
+    def close(self):
+        self._ctx = None
+
+
+def _grids(shapes, bcs):
+    arr = (lbm_grid * len(shapes))()
+    for i, sh in enumerate(shapes):
+        arr[i].nx, arr[i].ny, arr[i].nz = int(sh[0]), int(sh[1]), 1
+        bc = bcs[i] if bcs is not None else (PERIODIC, PERIODIC)
+        for a in range(3):
+            arr[i].bc[a] = bc[a] if a < len(bc) else PERIODIC
+    return arr
+
+
+def plan(shapes, tx, lz):
+    """Work list of a batch of D2Q9 grids (host computation): (m, 4) int array of
+    (grid, x0, z0, z1) with internal z = user y."""
+    lib = load()
+    g = _grids(shapes, None)
+    m = lib.lbm_batch_plan(len(shapes), g, int(tx), int(lz), None, 0)
+    if m < 0:
+        _check(m, "lbm_batch_plan")
+    out = (ctypes.c_int * (4 * max(m, 1)))()
+    _check(min(0, lib.lbm_batch_plan(len(shapes), g, int(tx), int(lz), out, m)), "lbm_batch_plan")
+    return np.array(out[: 4 * m], dtype=np.int64).reshape(m, 4)
+
+
+class Batch:
+    """Many D2Q9 grids in one set of population arrays, stepped by one
+    persistent launch per step (owns an lbm_batch).
+
+    shapes: sequence of (nx, ny); params: one lbm_params for all grids or a
+    sequence (same storage type); bcs: optional per-grid (bc_x, bc_y)."""
+
+    def __init__(self, shapes, params, bcs=None, stream=None):
+        lib = load()
+        n = len(shapes)
+        plist = list(params) if isinstance(params, (list, tuple)) else [params] * n
+        if len(plist) != n:
+            raise ValueError("one parameter block per grid")
+        parr = (lbm_params * n)(*plist)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = stream
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        self.params = plist
+        b = ctypes.c_void_p()
+        _check(lib.lbm_batch_create(n, _grids(shapes, bcs), parr, ctypes.c_void_p(stream), ctypes.byref(b)),
+               "lbm_batch_create")
+        self._b = b
+        self._views = [None] * n
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            for v in self._views:
+                if v is not None:
+                    v.close()
+            load().lbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def grid(self, i):
+        if self._views[i] is None:
+            ctx = load().lbm_batch_grid(self._b, int(i))
+            if not ctx:
+                raise IndexError(i)
+            self._views[i] = _GridView(self, ctypes.c_void_p(ctx), self.shapes[i], self.params[i])
+        return self._views[i]
+
+    def step(self, n=1):
+        _check(load().lbm_batch_step(self._b, int(n)), "lbm_batch_step")
+
+    def step_sequential(self, n=1):
+        _check(load().lbm_batch_step_sequential(self._b, int(n)), "lbm_batch_step_sequential")
+
+    def set_tile(self, tile, lz):
+        _check(load().lbm_batch_set_tile(self._b, int(tile), int(lz)), "lbm_batch_set_tile")
+
+    def get_tile(self):
+        t, lz, tx, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().lbm_batch_get_tile(self._b, ctypes.byref(t), ctypes.byref(lz), ctypes.byref(tx),
+                                         ctypes.byref(m)), "lbm_batch_get_tile")
+        return t.value, lz.value, tx.value, m.value
+
+    def set_graph(self, k):
+        _check(load().lbm_batch_set_graph(self._b, int(k)), "lbm_batch_set_graph")
+
+    def autotune(self, steps=10):
+        t, lz, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().lbm_batch_autotune(self._b, int(steps), ctypes.byref(t), ctypes.byref(lz), ctypes.byref(ms)),
+               "lbm_batch_autotune")
+        return t.value, lz.value, ms.value
+
+    def launch_count(self):
+        return load().lbm_batch_launch_count(self._b)
