@@ -107,6 +107,22 @@ def dist_setup():
     return world, rank, local, dist
 
 
+def max_over_ranks(x, dist):
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(nodes_per_rank, steps, world, seconds):
+    """Lattice updates of all ranks (replicas of equal size) per second, in G."""
+    return float(nodes_per_rank) * steps * world / seconds / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -256,10 +272,8 @@ def run_ours(args):
         clk = clocks.stop()
         ms = start.elapsed_time(end)
         per_launch_ms = kernel_ms / args.steps
+        ms = max_over_ranks(ms, dist)
         if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         diag = sim.diagnostics(raise_on_divergence=False)
         # --- end-to-end region: host (pinned) fields in, K steps, fields out
@@ -276,14 +290,9 @@ def run_ours(args):
         sim.step(args.steps)
         sim.macro(o_phi, o_P, o_ru)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-    total_lu = float(N) * args.steps * world
-    glups = total_lu / (ms * 1e-3) / 1e9
-    e2e_glups = total_lu / e2e_s / 1e9
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    glups = whole_job_glups(N, args.steps, world, ms * 1e-3)
+    e2e_glups = whole_job_glups(N, args.steps, world, e2e_s)
     peak, peak_kind = measured_peak()
     alg_bytes = BYTES_PER_LU[args.store] * N
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
@@ -403,11 +412,7 @@ def run_batch(args):
         end.synchronize()
         launches = b.launch_count() - n0
         clk = clocks.stop()
-        ms = start.elapsed_time(end)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(start.elapsed_time(end), dist)
         # the same grids as one launch of the single-grid kernel per grid and step
         k_seq = max(3, min(args.steps, 20))
         b.step_sequential(2)
@@ -431,9 +436,8 @@ def run_batch(args):
         for k, (op, oP, ou) in enumerate(host_out):
             b.grid(k).macro(op, oP, ou)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-    total_lu = float(N) * args.steps * world
-    glups = total_lu / (ms * 1e-3) / 1e9
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    glups = whole_job_glups(N, args.steps, world, ms * 1e-3)
     peak, peak_kind = measured_peak()
     per_launch_ms = ms / args.steps
     alg_bytes = BYTES_PER_LU[args.store] * 9 // 19 * N
@@ -453,7 +457,7 @@ def run_batch(args):
                        "launches_per_step": len(shapes),
                        "note": "one single-grid step launch per grid and step, same storage"},
         "clocks": clk,
-        "e2e": {"value": total_lu / e2e_s / 1e9, "unit": "GLUPS",
+        "e2e": {"value": whole_job_glups(N, args.steps, world, e2e_s), "unit": "GLUPS",
                 "h2d_bytes_per_step": 4 * 8 * N / args.steps, "d2h_bytes_per_step": 4 * 8 * N / args.steps,
                 "note": "init of every grid from pinned host phi,u,P + K steps + every grid's fields to pinned host"},
         "gpu_launches": launches,
