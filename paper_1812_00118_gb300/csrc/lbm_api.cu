@@ -610,7 +610,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
     int bt = c->tile, bl = c->lz;
     float bms = 1e30f;
     for (int t = 0; t < c->K->n_tiles && !rc; ++t) {
-        if (c->K->tile_tma[t] && !c->K->tma_ok(t, c->G)) continue;
+        if (!c->K->tile_ok(t, c->G)) continue;
         for (int k = 0; k < 4 && !rc; ++k) {
             c->tile = t;
             c->lz = lzs[k];
@@ -653,7 +653,7 @@ void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }
 // Step tile shape and z-chunk length (used by the tuner and the tests).
 int lbm_set_tile(lbm_ctx* c, int tile, int lz) {
     if (!c || tile < 0 || tile >= c->K->n_tiles || lz < 1 || c->owner) return LBM_EINVAL;
-    if (c->K->tile_tma[tile] && !c->K->tma_ok(tile, c->G)) return LBM_ENOTSUP;
+    if (!c->K->tile_ok(tile, c->G)) return LBM_ENOTSUP;
     c->tile = tile;
     c->lz = lz;
     return LBM_OK;

@@ -48,6 +48,37 @@ cudaError_t launch_step_tile(const StepArgs& a) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- asynchronous-load tiles (FP32)
+template <int LAT, int TX, int TY>
+constexpr size_t async_smem_bytes() { return sizeof(AsyncSmem<LAT, TX, TY>); }
+
+template <int LAT, int ST, int TX, int TY>
+bool async_tile_ok(const Geom&) {
+    return ST == ST_F32 && async_smem_bytes<LAT, TX, TY>() <= 227 * 1024;
+}
+
+template <int LAT, int ST, int TX, int TY, int MINB>
+cudaError_t launch_async_tile(const StepArgs& a) {
+    if constexpr (ST != ST_F32) {
+        return cudaErrorNotSupported;
+    } else {
+        const Geom& G = a.G;
+        const bool walls = G.wall[0] || G.wall[1] || G.wall[2];
+        auto kern = walls ? step_async_kernel<LAT, TX, TY, MINB, true> : step_async_kernel<LAT, TX, TY, MINB, false>;
+        constexpr size_t bytes = async_smem_bytes<LAT, TX, TY>();
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[walls ? 1 : 0]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (e != cudaSuccess) return e;
+            attr_set[walls ? 1 : 0] = true;
+        }
+        dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
+        kern<<<grid, dim3(TX, TY), bytes, a.stream>>>(dir_ptrs<float, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP),
+                                                      G, phys_as<float>(a.p), a.lz);
+        return cudaGetLastError();
+    }
+}
+
 // ---------------------------------------------------------------- batches
 // One CTA per resident slot (occupancy x SMs, looked up once per
 // instantiation), at most one per work item.

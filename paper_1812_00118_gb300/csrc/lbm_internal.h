@@ -11,7 +11,7 @@ namespace lbm {
 
 struct TmaMaps;
 
-constexpr int kMaxTiles = 12;   // step kernel variants per (lattice, storage)
+constexpr int kMaxTiles = 14;   // step kernel variants per (lattice, storage)
 
 // Everything one step launch needs.
 struct StepArgs {
@@ -48,8 +48,9 @@ struct KernelTable {
     cudaError_t (*step)(const StepArgs& a);
     // tensor maps of one input buffer pair for bulk-copy tile `tile`
     cudaError_t (*make_maps)(int tile, TmaMaps* out, const void* h, const void* g, const Geom& G);
-    // true if bulk-copy tile `tile` can run this grid (shared memory, sizes)
-    bool (*tma_ok)(int tile, const Geom& G);
+    // true if tile `tile` can run this grid and storage type (shared memory,
+    // sizes; bulk-copy and asynchronous-load tiles have limits)
+    bool (*tile_ok)(int tile, const Geom& G);
     cudaError_t (*phi)(const void* hin, const Geom& G, const Phys& p, double* phi, cudaStream_t s);
     cudaError_t (*macro)(const void* gin, const Geom& G, const Phys& p, const double* phi, double* P,
                          double* ux, double* uy, double* uz, cudaStream_t s);

@@ -239,6 +239,14 @@ __device__ __forceinline__ PullOffsets pull_offsets(const Geom& G, int x, int y,
     return o;
 }
 
+// Address of the value a pull of direction I reads.
+template <int LAT, int I, typename S>
+__device__ __forceinline__ const S* pull_ptr(const S* const* arr, const PullOffsets& o) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[I], CY = L::cy[I], CZ = L::cz[I];
+    return arr[I] + (o.z[1 + CZ] + o.r[1 + CY] + o.c[1 + CX]);
+}
+
 template <int LAT, int I, bool STREAM, typename S>
 __device__ __forceinline__ S pull_pad(const S* const* arr, const PullOffsets& o) {
     using L = Lattice<LAT>;
@@ -538,6 +546,140 @@ __device__ __forceinline__ void collide_pair(const NodeState<float>& s, const Pa
 // hit L2.  BAL (one-wave launch): gridDim.z chunks of NZ / gridDim.z planes
 // (rounded), the host choosing gridDim.z so that the whole grid is resident
 // at once; otherwise chunks of LZ planes.
+// ---------------------------------------------------------------- asynchronous loads (FP32)
+// 4-byte global -> shared copies that complete in the background (cp.async,
+// sm_80 and later): the loads of the next planes stay in flight while the
+// CTA collides the current one, with no register held for them.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Moments of the pulled g: m0 = sum g, m1 = sum c g, m2 = sum c c g.
+template <typename R>
+struct Moments {
+    R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+};
+
+// Over opposite pairs (I, J): the odd moments take g_I - g_J, the even ones
+// g_I + g_J.  gv(i) returns the pulled g of direction i.
+template <int LAT, typename GA>
+__device__ __forceinline__ auto g_moments(GA gv) {
+    using L = Lattice<LAT>;
+    using R = decltype(gv(0));
+    Moments<R> m;
+    m.m0 = gv(0);
+    Unroll<1, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int o = L::op[i];
+        if constexpr (i < o) {
+            constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+            const R sp = gv(i) + gv(o), dm = gv(i) - gv(o);
+            m.m0 += sp;
+            if (CX) { m.mx += cmul<CX>(dm); m.mxx += sp; }
+            if (CY) { m.my += cmul<CY>(dm); m.myy += sp; }
+            if (CZ) { m.mz += cmul<CZ>(dm); m.mzz += sp; }
+            if (CX * CY) m.mxy += cmul<CX * CY>(sp);
+            if (CX * CZ) m.mxz += cmul<CX * CZ>(sp);
+            if (CY * CZ) m.myz += cmul<CY * CZ>(sp);
+        }
+    });
+    return m;
+}
+
+// Everything of one node after its plane's phi is in the shared ring and the
+// moments of its pulled g are known: stencils (three planes of the ring, slots
+// sm, s0, sp for z-1, z, z+1; (lx, ly) the node's position in the ring),
+// local state, collisions and the writes.  hv(i) returns the node's pulled
+// h_i.
+template <int LAT, int ST, bool WALLS, int SY, int SX, typename HA>
+__device__ __forceinline__ void collide_node(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q>& D,
+                                             const Geom& G, const PhysT<typename Storage<ST>::R>& p,
+                                             const typename Storage<ST>::R (*phis)[SY][SX], int sm, int s0, int sp,
+                                             int lx, int ly, const Moments<typename Storage<ST>::R>& m, HA hv, int x,
+                                             int y, int z, int rb) {
+    using L = Lattice<LAT>;
+    using St = Storage<ST>;
+    using R = typename St::R;
+    constexpr int Q = L::Q;
+    NodeState<R> s;
+    s.phi = phis[s0][ly][lx];
+    // central differences (stencils after Eq. 12):
+    // grad phi = sum_i c_i w_i phi(x + c_i) / T  (the -c_i half of the
+    // paper's symmetric sum equals the +c_i half), lap = 2 sum w (phi_nb - phi) / T
+    // per opposite pair (I, J): phi(x + c_I) - phi(x + c_J) feeds the
+    // gradient, phi(x + c_I) + phi(x + c_J) - 2 phi the Laplacian
+    R gx = 0, gy = 0, gz = 0, lap = 0;
+    Unroll<1, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int o = L::op[i];
+        if constexpr (i < o) {
+            constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
+            constexpr double W = L::w[i];
+            const int slot_p = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
+            const int slot_m = CZ == 0 ? s0 : (CZ > 0 ? sm : sp);
+            const R vp = phis[slot_p][ly + CY][lx + CX];
+            const R vm = phis[slot_m][ly - CY][lx - CX];
+            const R wd = (R)W * (vp - vm);
+            if (CX) gx += cmul<CX>(wd);
+            if (CY) gy += cmul<CY>(wd);
+            if (CZ) gz += cmul<CZ>(wd);
+            lap += (R)W * ((vp - s.phi) + (vm - s.phi));
+        }
+    });
+    s.gx = gx * (R)3;
+    s.gy = gy * (R)3;
+    s.gz = gz * (R)3;
+    s.lap = lap * (R)6;
+    node_state<R, L::kHasY>(s, p, m.m0, m.mx, m.my, m.mz, m.mxx, m.myy, m.mzz, m.mxy, m.mxz, m.myz);
+    const NodeWrites nw = node_writes<LAT>(G, x, y, z);
+    const int own = G.base + (z + G.GZ) * G.PXY + rb;
+    // moving directions first; the rest population closes sum_i h*_i = phi
+    // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
+    // sum_i Gamma_i = 1 from biasing the global phi)
+    R hsum = 0;
+    if constexpr (std::is_same<R, float>::value) {
+        const PairState q = pair_state<LAT>(s, p);
+        float2 hsum2 = make_float2(0.0f, 0.0f);
+        Unroll<1, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int o = L::op[i];
+            if constexpr (i < o) {
+                constexpr double W = L::w[i];
+                float2 hs, gs;
+                collide_pair<LAT, i>(s, q, make_float2(hv(i), hv(o)), &hs, &gs);
+                hsum2 = add2(hsum2, hs);
+                const R hsh = (R)W * p.h_shift, gsh = (R)W * p.g_shift;
+                write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.x, hsh, (R)1));
+                write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.y, hsh, (R)1));
+                write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.x, gsh, p.g_scale));
+                write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.y, gsh, p.g_scale));
+            }
+        });
+        hsum = hsum2.x + hsum2.y;
+    } else {
+        Unroll<1, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr double W = L::w[i];
+            R hs, gs;
+            collide_dir<LAT, i, R>(s, p, hv(i), &hs, &gs);
+            hsum += hs;
+            write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
+            write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
+        });
+    }
+    {
+        constexpr double W0 = L::w[0];
+        R hs, gs;
+        collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
+        write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
+        write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
+    }
+}
+
 template <int LAT, int ST, int TX, int TY>
 struct MarchSmem {
     using R = typename Storage<ST>::R;
@@ -610,37 +752,17 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
         }
     };
 
-    fill(z0 - 1, 0, 0);
-    fill(z0, 1, 1);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < G.NX && y < G.NY;
     const int rb = (y + G.GY) * G.PX + x + G.GX;
+    fill(z0 - 1, 0, 0);
+    fill(z0, 1, 1);
 
     for (int z = z0; z < z1; ++z) {
         const int j = z - z0;
         const PullOffsets po = pull_offsets(G, x, y, z);
         // (1) g of this node (streamed) and the phi fill of the next plane
-        R m0 = 0, mx = 0, my = 0, mz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
-        // over opposite pairs (I, J): the odd moments take g_I - g_J, the
-        // even ones g_I + g_J
-        auto g_moments = [&](const R* gv) {
-            m0 = gv[0];
-            Unroll<1, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr int o = L::op[i];
-                if constexpr (i < o) {
-                    constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                    const R sp = gv[i] + gv[o], dm = gv[i] - gv[o];
-                    m0 += sp;
-                    if (CX) { mx += cmul<CX>(dm); mxx += sp; }
-                    if (CY) { my += cmul<CY>(dm); myy += sp; }
-                    if (CZ) { mz += cmul<CZ>(dm); mzz += sp; }
-                    if (CX * CY) mxy += cmul<CX * CY>(sp);
-                    if (CX * CZ) mxz += cmul<CX * CZ>(sp);
-                    if (CY * CZ) myz += cmul<CY * CZ>(sp);
-                }
-            });
-        };
+        Moments<R> m;
         auto g_load = [&](R* gv) {
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
@@ -652,95 +774,19 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
             R gv[Q];
             if (active) g_load(gv);
             fill(z + 1, (j + 2) & 3, j & 1);
-            if (active) g_moments(gv);
+            if (active) m = g_moments<LAT>([&](int i) { return gv[i]; });
         } else {
             fill(z + 1, (j + 2) & 3, j & 1);
             if (active) {
                 R gv[Q];
                 g_load(gv);
-                g_moments(gv);
+                m = g_moments<LAT>([&](int i) { return gv[i]; });
             }
         }
         __syncthreads();
-        if (active) {
-            const int sm = j & 3, s0 = (j + 1) & 3, sp = (j + 2) & 3;
-            const int lx = tx + 1, ly = ty + HY;
-            NodeState<R> s;
-            s.phi = phis[s0][ly][lx];
-            // central differences (stencils after Eq. 12):
-            // grad phi = sum_i c_i w_i phi(x + c_i) / T  (the -c_i half of the
-            // paper's symmetric sum equals the +c_i half), lap = 2 sum w (phi_nb - phi) / T
-            // per opposite pair (I, J): phi(x + c_I) - phi(x + c_J) feeds the
-            // gradient, phi(x + c_I) + phi(x + c_J) - 2 phi the Laplacian
-            R gx = 0, gy = 0, gz = 0, lap = 0;
-            Unroll<1, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr int o = L::op[i];
-                if constexpr (i < o) {
-                    constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-                    constexpr double W = L::w[i];
-                    const int slot_p = CZ == 0 ? s0 : (CZ > 0 ? sp : sm);
-                    const int slot_m = CZ == 0 ? s0 : (CZ > 0 ? sm : sp);
-                    const R vp = phis[slot_p][ly + CY][lx + CX];
-                    const R vm = phis[slot_m][ly - CY][lx - CX];
-                    const R wd = (R)W * (vp - vm);
-                    if (CX) gx += cmul<CX>(wd);
-                    if (CY) gy += cmul<CY>(wd);
-                    if (CZ) gz += cmul<CZ>(wd);
-                    lap += (R)W * ((vp - s.phi) + (vm - s.phi));
-                }
-            });
-            s.gx = gx * (R)3;
-            s.gy = gy * (R)3;
-            s.gz = gz * (R)3;
-            s.lap = lap * (R)6;
-            node_state<R, L::kHasY>(s, p, m0, mx, my, mz, mxx, myy, mzz, mxy, mxz, myz);
-            const NodeWrites nw = node_writes<LAT>(G, x, y, z);
-            const int own = G.base + (z + G.GZ) * G.PXY + rb;
-            // moving directions first; the rest population closes sum_i h*_i = phi
-            // (Eq. 1 conserves phi at every node; closing it keeps FP32 rounding of
-            // sum_i Gamma_i = 1 from biasing the global phi)
-            R hsum = 0;
-            if constexpr (std::is_same<R, float>::value) {
-                const PairState q = pair_state<LAT>(s, p);
-                float2 hsum2 = make_float2(0.0f, 0.0f);
-                Unroll<1, Q>::run([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    constexpr int o = L::op[i];
-                    if constexpr (i < o) {
-                        constexpr double W = L::w[i];
-                        const float2 hv = make_float2(hown[(j + 1) & 1][i][tid], hown[(j + 1) & 1][o][tid]);
-                        float2 hs, gs;
-                        collide_pair<LAT, i>(s, q, hv, &hs, &gs);
-                        hsum2 = add2(hsum2, hs);
-                        const R hsh = (R)W * p.h_shift, gsh = (R)W * p.g_shift;
-                        write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.x, hsh, (R)1));
-                        write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.y, hsh, (R)1));
-                        write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.x, gsh, p.g_scale));
-                        write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.y, gsh, p.g_scale));
-                    }
-                });
-                hsum = hsum2.x + hsum2.y;
-            } else {
-                Unroll<1, Q>::run([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    constexpr double W = L::w[i];
-                    const R hv = hown[(j + 1) & 1][i][tid];
-                    R hs, gs;
-                    collide_dir<LAT, i, R>(s, p, hv, &hs, &gs);
-                    hsum += hs;
-                    write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
-                    write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
-                });
-            }
-            {
-                constexpr double W0 = L::w[0];
-                R hs, gs;
-                collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
-                write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
-                write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
-            }
-        }
+        if (active)
+            collide_node<LAT, ST, WALLS>(D, G, p, phis, j & 3, (j + 1) & 3, (j + 2) & 3, tx + 1, ty + HY, m,
+                                         [&](int i) { return hown[(j + 1) & 1][i][tid]; }, x, y, z, rb);
     }
 }
 
@@ -753,6 +799,141 @@ step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, P
     const int z0 = BAL ? (int)((long long)blockIdx.z * G.NZ / gridDim.z) : blockIdx.z * LZ;
     const int z1 = BAL ? (int)((long long)(blockIdx.z + 1) * G.NZ / gridDim.z) : min(z0 + LZ, G.NZ);
     march<LAT, ST, TX, TY, HOIST, WALLS>(D, G, p, x0, y0, z0, z1, sm);
+}
+
+// Halo-ring position k of a TX x TY tile (ring of SX x SY, SX = TX + 2,
+// SY = TY + 2 HY): the top row, the bottom row, then the side columns.
+template <int TX, int TY, int HY>
+__device__ __forceinline__ void ring_pos(int k, int* lx, int* ly) {
+    constexpr int SX = TX + 2, SY = TY + 2 * HY;
+    if (HY) {
+        if (k < SX) { *lx = k; *ly = 0; }
+        else if (k < 2 * SX) { *lx = k - SX; *ly = SY - 1; }
+        else { const int r = k - 2 * SX; *lx = (r & 1) ? SX - 1 : 0; *ly = 1 + (r >> 1); }
+    } else {
+        *lx = k == 0 ? 0 : SX - 1;
+        *ly = 0;
+    }
+}
+
+template <int LAT, int TX, int TY>
+struct AsyncSmem {
+    static constexpr int Q = Lattice<LAT>::Q;
+    static constexpr int HY = Lattice<LAT>::kHasY ? 1 : 0;
+    static constexpr int SX = TX + 2, SY = TY + 2 * HY;
+    static constexpr int NT = TX * TY;
+    static constexpr int NRING = SX * SY - NT;
+    float phis[4][SY][SX];
+    float hown[3][Q][NT];    // own pulled h of plane q in slot q % 3 (collided, summed, in flight)
+    float gbuf[Q][NT];       // own pulled g of the next plane to reduce
+    float ring[Q][NRING];    // pulled h of the halo ring positions of the next plane to sum
+};
+
+// The march of march() with every population load issued as cp.async ahead
+// of its use: in the iteration of plane z, once the copies of plane z + 1's
+// h and plane z's g have landed and been reduced (phi into the shared ring,
+// g into its moments), the copies of plane z + 2's h (own position and halo
+// ring) and plane z + 1's g are issued, and stay in flight through the
+// barrier and the collision of plane z.  Every thread reads back only its own
+// copies (cp.async.wait_group suffices); phi goes through the shared ring and
+// the one barrier per plane, as in march().  Storage FP32.
+template <int LAT, int TX, int TY, bool WALLS>
+__device__ __forceinline__ void march_async(const DirPtrs<float, Lattice<LAT>::Q>& D, const Geom& G,
+                                            const PhysT<float>& p, int x0, int y0, int z0, int z1,
+                                            AsyncSmem<LAT, TX, TY>& sm) {
+    using L = Lattice<LAT>;
+    using Sm = AsyncSmem<LAT, TX, TY>;
+    constexpr int Q = L::Q;
+    constexpr int HY = Sm::HY, NT = Sm::NT, NRING = Sm::NRING;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + TX * ty;
+    const int xo = stencil_coord(x0 + tx, G.NX, G.wall[0]);
+    const int yo = HY ? stencil_coord(y0 + ty, G.NY, G.wall[1]) : y0;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < G.NX && y < G.NY;
+    const int rb = (y + G.GY) * G.PX + x + G.GX;
+
+    // copies of the pulled h of plane zp: own position into hown[hs], the
+    // thread's halo-ring positions into ring
+    auto issue_fill = [&](int zp, int hs) {
+        const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
+        const PullOffsets po = pull_offsets(G, xo, yo, zz);
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            cp_async4(&sm.hown[hs][i][tid], pull_ptr<LAT, i>(D.hin, po));
+        });
+        for (int r = tid; r < NRING; r += NT) {
+            int lx, ly;
+            ring_pos<TX, TY, HY>(r, &lx, &ly);
+            const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
+            const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
+            const PullOffsets pr = pull_offsets(G, xx, yy, zz);
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                cp_async4(&sm.ring[i][r], pull_ptr<LAT, i>(D.hin, pr));
+            });
+        }
+    };
+    // phi of the landed plane (own h in hown[hs]) into ring slot `slot`
+    auto sum_fill = [&](int slot, int hs) {
+        float phi = 0.0f;
+        Unroll<0, Q>::run([&](auto ic) { phi += sm.hown[hs][decltype(ic)::value][tid]; });
+        sm.phis[slot][ty + HY][tx + 1] = phi;
+        for (int r = tid; r < NRING; r += NT) {
+            int lx, ly;
+            ring_pos<TX, TY, HY>(r, &lx, &ly);
+            float v = 0.0f;
+            Unroll<0, Q>::run([&](auto ic) { v += sm.ring[decltype(ic)::value][r]; });
+            sm.phis[slot][ly][lx] = v;
+        }
+    };
+    auto issue_g = [&](int zg) {
+        if (!active) return;
+        const PullOffsets po = pull_offsets(G, x, y, zg);
+        Unroll<0, Q>::run([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            cp_async4(&sm.gbuf[i][tid], pull_ptr<LAT, i>(D.gin, po));
+        });
+    };
+
+    // plane index q = z - z0 + 1 (plane z0 - 1 is q = 0); one copy group in flight
+    issue_fill(z0 - 1, 0);
+    cp_async_commit();
+    cp_async_wait<0>();
+    sum_fill(0, 0);
+    issue_fill(z0, 1);
+    cp_async_commit();
+    cp_async_wait<0>();
+    sum_fill(1, 1);
+    issue_fill(z0 + 1, 2);
+    issue_g(z0);
+    cp_async_commit();
+    for (int z = z0; z < z1; ++z) {
+        const int q = z - z0 + 1;
+        cp_async_wait<0>();   // plane z + 1's h and plane z's g have landed
+        sum_fill((q + 1) & 3, (q + 1) % 3);
+        Moments<float> m;
+        if (active) m = g_moments<LAT>([&](int i) { return sm.gbuf[i][tid]; });
+        if (z + 2 <= z1) issue_fill(z + 2, (q + 2) % 3);
+        if (z + 1 < z1) issue_g(z + 1);
+        cp_async_commit();
+        __syncthreads();
+        if (active)
+            collide_node<LAT, ST_F32, WALLS>(D, G, p, sm.phis, (q - 1) & 3, q & 3, (q + 1) & 3, tx + 1, ty + HY, m,
+                                             [&](int i) { return sm.hown[q % 3][i][tid]; }, x, y, z, rb);
+    }
+    cp_async_wait<0>();
+}
+
+template <int LAT, int TX, int TY, int MINB, bool WALLS>
+__global__ void __launch_bounds__(TX * TY, MINB)
+step_async_kernel(const DirPtrs<float, Lattice<LAT>::Q> D, Geom G, PhysT<float> p, int LZ) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<AsyncSmem<LAT, TX, TY>*>(smem_raw);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * LZ;
+    const int z1 = min(z0 + LZ, G.NZ);
+    march_async<LAT, TX, TY, WALLS>(D, G, p, x0, y0, z0, z1, sm);
 }
 
 // ---------------------------------------------------------------- batch

@@ -15,8 +15,8 @@ namespace {
 
 #if LBM_LAT == 1
 // D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
-// the bulk tensor copy pipeline, 8-11 are tiles 0-3 as a balanced persistent
-// launch.
+// the bulk tensor copy pipeline, 8-11 are tiles 0-3 as a one-wave launch,
+// 12-13 load through cp.async ahead of use (FP32 storage only).
 #define LBM_TILES(X)         \
     X(0, hoist, 32, 4, 4)    \
     X(1, split, 32, 4, 8)    \
@@ -29,7 +29,9 @@ namespace {
     X(8, hoistbal, 32, 4, 4) \
     X(9, splitbal, 32, 4, 8) \
     X(10, splitbal, 32, 8, 4) \
-    X(11, splitbal, 32, 4, 6)
+    X(11, splitbal, 32, 4, 6) \
+    X(12, async, 32, 4, 4)    \
+    X(13, async, 32, 2, 8)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 #define LBM_TILES(X)           \
@@ -44,13 +46,16 @@ namespace {
     X(8, hoistbal, 128, 1, 4)  \
     X(9, splitbal, 128, 1, 8)  \
     X(10, splitbal, 256, 1, 4) \
-    X(11, splitbal, 64, 1, 16)
+    X(11, splitbal, 64, 1, 16) \
+    X(12, async, 128, 1, 8)    \
+    X(13, async, 256, 1, 4)
 #endif
 
 #define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false>(a)
 #define LBM_LAUNCH_split(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false>(a)
 #define LBM_LAUNCH_hoistbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, true>(a)
 #define LBM_LAUNCH_splitbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true>(a)
+#define LBM_LAUNCH_async(TX, TY, MB) launch_async_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
@@ -66,6 +71,7 @@ cudaError_t step_dispatch(const StepArgs& a) {
 #define LBM_MAPS_split(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_hoistbal(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_splitbal(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_async(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
 #define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_MAPS_##KIND(TX, TY);
@@ -77,10 +83,11 @@ cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, 
     }
 }
 
-#define LBM_OK_hoist(TX, TY) false
-#define LBM_OK_split(TX, TY) false
-#define LBM_OK_hoistbal(TX, TY) false
-#define LBM_OK_splitbal(TX, TY) false
+#define LBM_OK_hoist(TX, TY) true
+#define LBM_OK_split(TX, TY) true
+#define LBM_OK_hoistbal(TX, TY) true
+#define LBM_OK_splitbal(TX, TY) true
+#define LBM_OK_async(TX, TY) async_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_OK_##KIND(TX, TY);
@@ -121,6 +128,7 @@ cudaError_t batch_dispatch(const BatchArgs& a) {
 #define LBM_ISTMA_split 0
 #define LBM_ISTMA_hoistbal 0
 #define LBM_ISTMA_splitbal 0
+#define LBM_ISTMA_async 0
 #define LBM_ISTMA_tma 1
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
 

@@ -241,12 +241,12 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
     rounding (the compiler may contract a*b+c differently per instantiation)."""
     ref = None
     for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (5, 1), (6, 1), (7, 1),
-                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100)):
+                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100), (12, 4)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            assert e.code == lbm.ENOTSUP and 4 <= tile <= 7
+            assert e.code == lbm.ENOTSUP and 4 <= tile <= 7 or tile >= 12
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
@@ -254,6 +254,31 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
             ref = (hg, gg)
         else:
             assert normwise(hg, ref[0]) < 1e-14 and normwise(gg, ref[1]) < 1e-13, (tile, lz)
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
+def test_async_tiles_agree_f32(lbm, lat_id, shape, bc):
+    """The cp.async tiles (12: every load, 13: the g loads; FP32 storage only)
+    against the per-thread-load tile 1 and the oracle: the same FP32
+    arithmetic, so agreement to a few FP32 roundings after 7 steps."""
+    ref, _, _, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    ref.set_tile(1, 16)
+    ref.step(7)
+    hr, gr = ref.get_populations()
+    for tile, lz in ((12, 16), (12, 1), (12, 5), (13, 3), (13, 100), (13, 1)):
+        sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+        sim.set_tile(tile, lz)
+        sim.step(7)
+        hg, gg = sim.get_populations()
+        assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz)
+    for tile in (12, 13):
+        sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+        sim.set_tile(tile, 16)
+        sim.step(1)
+        h, g = O.step(h, g, lat, p)
+        f, Pg, ru = sim.macro()
+        fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+        assert normwise(f, fo) < 1e-5 and normwise(Pg, Po) < 1e-5 and normwise(ru, ruo) < 1e-5, tile
 
 
 @pytest.mark.parametrize("store", ["F64", "F32"])
