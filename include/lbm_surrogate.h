@@ -1,0 +1,111 @@
+/* Kernels of the learned warm-start surrogate (liblbm.so).
+ *
+ * The paper has no network: these are a service of the library.  A small
+ * convolutional network maps the fields (phi, u, P) of a D2Q9 state to the
+ * state many steps later; its training and inference run on these kernels,
+ * and lbm_init_fields rebuilds the populations from its output (equilibria,
+ * Eqs. 2 and 6-7 of the paper).
+ *
+ * Conventions (every function):
+ *   - Tensors are channels-last on the device: pixel p = (n H + y) W + x of
+ *     N images of H x W, element (p, c) at p * stride + c.  A stride larger
+ *     than the channel count reads or writes a slice of a wider tensor (the
+ *     caller passes the slice's first element).  "bf16" tensors are arrays of
+ *     16-bit bfloat16 values (void*), the rest float or double.
+ *   - Convolutions are periodic 3x3, "same" size:
+ *       y[p, co] = bias[co] + sum_{dy, dx, ci} w[co, 3 dy + dx, ci] x[p + (dy - 1, dx - 1), ci]
+ *     (offsets wrap inside each image); w is bf16 [Co][9][Ci].  Ci and Co
+ *     are multiples of 16 (zero-pad), Co <= 64, N H W a multiple of 16.
+ *   - Pooling and upsampling are by LBM_SG_POOL in both directions; H and W
+ *     (always the FULL-resolution size) are multiples of it.
+ *   - The caller owns every buffer; the functions allocate nothing.  All are
+ *     asynchronous on `stream` (NULL: default stream).
+ *   - Return LBM_OK, LBM_EINVAL (NULL pointer, bad size or stride),
+ *     LBM_ECUDA (launch failed).
+ */
+#ifndef LBM_SURROGATE_H
+#define LBM_SURROGATE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_SG_POOL 8
+
+/* y (float) = periodic 3x3 convolution of x (bf16) with w (bf16), plus bias
+ * (float[Co], may be NULL).  BF16 tensor-core products, FP32 sums. */
+int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, float* y, int csy, int N, int H, int W,
+                   int Ci, int Co, void* stream);
+
+/* Floats of scratch lbm_sg_conv3x3_wgrad needs for these sizes. */
+long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co);
+
+/* gw (float [Co][9][Ci]) = gradient of sum_p <gy[p], y[p]> with respect to w
+ * for y = lbm_sg_conv3x3(x, w): gw[co, tap, ci] = sum_p gy[p, co] x[p + d(tap), ci].
+ * x, gy bf16.  Deterministic: fixed-size pixel chunks summed in order. */
+int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float* gw, float* scratch,
+                         long long scratch_floats, int N, int H, int W, int Ci, int Co, void* stream);
+
+/* wt (bf16 [Ci][9][Co]) = w with input and output channels exchanged and the
+ * taps reversed: lbm_sg_conv3x3(gy, wt) is then the gradient with respect to
+ * the convolution's input x. */
+int lbm_sg_weight_flip(const void* w, void* wt, int Ci, int Co, void* stream);
+
+/* gb[c] = sum_p g[p, c] (float); scratch holds at least 64 C floats. */
+int lbm_sg_bias_grad(const float* g, int csg, float* gb, float* scratch, long long npix, int C, void* stream);
+
+/* y (bf16) = max(a, 0). */
+int lbm_sg_relu(const float* a, int csa, void* y, int csy, long long npix, int C, void* stream);
+
+/* ga (float, stride C) = g where a > 0, else 0; ga16 (bf16, stride C, may be
+ * NULL) its bf16 copy. */
+int lbm_sg_relu_bwd(const float* g, int csg, const float* a, int csa, float* ga, void* ga16, long long npix, int C,
+                    void* stream);
+
+/* y (bf16) = a rounded to bf16. */
+int lbm_sg_to_bf16(const float* a, int csa, void* y, int csy, long long npix, int C, void* stream);
+
+/* out = a + b (float). */
+int lbm_sg_add(const float* a, int csa, const float* b, int csb, float* out, int cso, long long npix, int C,
+               void* stream);
+
+/* y (bf16, H/8 x W/8 images) = means of the 8 x 8 blocks of x (bf16, H x W). */
+int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream);
+/* gx (float, H x W) = g (float, H/8 x W/8) / 64 spread over each block. */
+int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream);
+/* y (bf16, H x W) = x (bf16, H/8 x W/8) repeated over each 8 x 8 block. */
+int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream);
+/* gx (float, H/8 x W/8) = sums of g (float, H x W) over each block. */
+int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream);
+
+/* Mean squared error of out = x + delta against target over the first C
+ * channels: *loss (device double) = mean (out - target)^2 (FP64 sums), and
+ * g (float, stride csd) = d loss / d delta (zero in channels C..csd-1).
+ * scratch: 256 doubles. */
+int lbm_sg_mse(const float* x, int csx, const float* delta, int csd, const float* target, int cst, float* g,
+               double* scratch, double* loss, long long npix, int C, void* stream);
+
+/* One Adam update (bias-corrected, step >= 1) of n FP32 master values w with
+ * moments m, v and gradient g; w16 (bf16, may be NULL) receives the rounded
+ * weights the convolutions read. */
+int lbm_sg_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
+                int step, void* w16, void* stream);
+
+/* Network input from one grid's fields (device FP64, x fastest, as
+ * lbm_macro writes them, u as two component arrays): x32 (float, stride
+ * cs32 >= 4) = (phi, ux, uy, P) / scale, x16 (bf16, stride cs16 >= 4) the
+ * same rounded, zero in channels 4..cs16-1. */
+int lbm_sg_pack(const double* phi, const double* ux, const double* uy, const double* P, const double scale[4],
+                float* x32, int cs32, void* x16, int cs16, long long npix, void* stream);
+
+/* Fields from the network output: (phi, ux, uy, P) = (x32 + delta) * scale. */
+int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
+                  double* P, const double scale[4], long long npix, void* stream);
+
+/* a[k] += s (used to restore the exact total of phi after a prediction). */
+int lbm_sg_shift(double* a, long long n, double s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_SURROGATE_H */

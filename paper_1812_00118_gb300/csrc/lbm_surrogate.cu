@@ -1,0 +1,541 @@
+// Kernels of the learned warm-start surrogate (include/lbm_surrogate.h):
+// periodic 3x3 convolutions on BF16 tensor cores with FP32 accumulation, and
+// the elementwise, pooling, loss and optimiser kernels around them.
+//
+// Tensors are channels-last: pixel p = (n H + y) W + x, element (p, c) at
+// p * stride + c (a channel stride larger than the channel count lets a
+// layer read or write a slice of a wider tensor, which is how the skip
+// concatenation is laid out).  Conv weights are [Co][9][Ci] (tap = 3 dy + dx,
+// input channels fastest).  Channel counts of convolutions are multiples of
+// 16 (zero-padded by the caller), pixel counts multiples of 16.
+//
+// The contraction uses the warp-level mma.sync m16n8k16 BF16 instruction:
+// A fragments are gathered straight from the channels-last activations (two
+// adjacent channels per 32-bit register), so a convolution is an implicit
+// GEMM without an im2col buffer.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <stdint.h>
+
+#include "lbm.h"
+#include "lbm_surrogate.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+int check(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t pack_pair(const bf16* lo, const bf16* hi) {
+    const uint32_t a = *reinterpret_cast<const unsigned short*>(lo);
+    const uint32_t b = *reinterpret_cast<const unsigned short*>(hi);
+    return a | (b << 16);
+}
+
+// pixel p shifted by (dy, dx) with periodic wrap inside its image
+__device__ __forceinline__ long long shift_pixel(long long p, int H, int W, int dy, int dx) {
+    const long long hw = (long long)H * W;
+    const long long n = p / hw;
+    const int r = (int)(p - n * hw);
+    int y = r / W + dy, x = r % W + dx;
+    y = y < 0 ? y + H : (y >= H ? y - H : y);
+    x = x < 0 ? x + W : (x >= W ? x - W : x);
+    return n * hw + (long long)y * W + x;
+}
+
+// y[p, co] = b[co] + sum_{tap, ci} w[co, tap, ci] x[shift(p, tap), ci]; one warp per 16 pixels,
+// NT n-tiles of 8 output channels (Co = 8 NT).
+template <int NT>
+__global__ void conv_fwd_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
+                                const float* __restrict__ bias, float* __restrict__ y, int csy, long long M, int H,
+                                int W, int Ci) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long p0 = warp * 16;
+    if (p0 >= M) return;
+    const long long r0 = p0 + g, r1 = p0 + g + 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const bf16* xa0 = x + shift_pixel(r0, H, W, dy, dx) * csx + 2 * t;
+        const bf16* xa1 = x + shift_pixel(r1, H, W, dy, dx) * csx + 2 * t;
+        for (int kc = 0; kc < Ci; kc += 16) {
+            const uint32_t a[4] = {ld_pair(xa0 + kc), ld_pair(xa1 + kc), ld_pair(xa0 + kc + 8), ld_pair(xa1 + kc + 8)};
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const bf16* wb = w + ((long long)(j * 8 + g) * 9 + tap) * Ci + kc + 2 * t;
+                const uint32_t b[2] = {ld_pair(wb), ld_pair(wb + 8)};
+                mma_bf16(acc[j], a, b);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int co = j * 8 + 2 * t;
+        const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
+        y[r0 * csy + co] = acc[j][0] + b0;
+        y[r0 * csy + co + 1] = acc[j][1] + b1;
+        y[r1 * csy + co] = acc[j][2] + b0;
+        y[r1 * csy + co + 1] = acc[j][3] + b1;
+    }
+}
+
+// partial[chunk, co, tap, ci] = sum over the chunk's pixels p of gy[p, co] x[shift(p, tap), ci];
+// one warp per (chunk, tap, 16 output channels, 8 input channels).
+constexpr int kChunk = 1024;   // pixels per partial
+
+__global__ void conv_wgrad_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ gy, int csg,
+                                  float* __restrict__ partial, long long M, int H, int W, int Ci, int Co) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int nco = Co / 16, nci = Ci / 8;
+    const long long per_chunk = 9LL * nco * nci;
+    const long long nchunks = (M + kChunk - 1) / kChunk;
+    if (warp >= nchunks * per_chunk) return;
+    const long long chunk = warp / per_chunk;
+    int rem = (int)(warp - chunk * per_chunk);
+    const int tap = rem / (nco * nci);
+    rem -= tap * nco * nci;
+    const int co0 = (rem / nci) * 16, ci0 = (rem % nci) * 8;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const long long pb = chunk * kChunk;
+    const long long pe = pb + kChunk < M ? pb + kChunk : M;
+    for (long long pk = pb; pk < pe; pk += 16) {
+        // k index = pixel pk + kk; pixel counts are multiples of 16, so no tail
+        const long long q0 = pk + 2 * t, q1 = q0 + 1, q8 = q0 + 8, q9 = q0 + 9;
+        const uint32_t a[4] = {pack_pair(gy + q0 * csg + co0 + g, gy + q1 * csg + co0 + g),
+                               pack_pair(gy + q0 * csg + co0 + g + 8, gy + q1 * csg + co0 + g + 8),
+                               pack_pair(gy + q8 * csg + co0 + g, gy + q9 * csg + co0 + g),
+                               pack_pair(gy + q8 * csg + co0 + g + 8, gy + q9 * csg + co0 + g + 8)};
+        const uint32_t b[2] = {pack_pair(x + shift_pixel(q0, H, W, dy, dx) * csx + ci0 + g,
+                                         x + shift_pixel(q1, H, W, dy, dx) * csx + ci0 + g),
+                               pack_pair(x + shift_pixel(q8, H, W, dy, dx) * csx + ci0 + g,
+                                         x + shift_pixel(q9, H, W, dy, dx) * csx + ci0 + g)};
+        mma_bf16(acc, a, b);
+    }
+    float* out = partial + chunk * (long long)Co * 9 * Ci;
+    const int ci = ci0 + 2 * t;
+    out[((long long)(co0 + g) * 9 + tap) * Ci + ci] = acc[0];
+    out[((long long)(co0 + g) * 9 + tap) * Ci + ci + 1] = acc[1];
+    out[((long long)(co0 + g + 8) * 9 + tap) * Ci + ci] = acc[2];
+    out[((long long)(co0 + g + 8) * 9 + tap) * Ci + ci + 1] = acc[3];
+}
+
+// gw[k] = sum over chunks of partial[chunk, k], in chunk order
+__global__ void sum_chunks_kernel(const float* __restrict__ partial, long long nchunks, long long K,
+                                  float* __restrict__ gw) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    float s = 0.0f;
+    for (long long c = 0; c < nchunks; ++c) s += partial[c * K + k];
+    gw[k] = s;
+}
+
+// wt[ci, 8 - tap, co] = w[co, tap, ci]: the weights of the input-gradient convolution
+__global__ void weight_flip_kernel(const bf16* __restrict__ w, bf16* __restrict__ wt, int Ci, int Co) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)Co * 9 * Ci) return;
+    const int ci = (int)(k % Ci);
+    const int tap = (int)((k / Ci) % 9);
+    const int co = (int)(k / (9LL * Ci));
+    wt[((long long)ci * 9 + (8 - tap)) * Co + co] = w[k];
+}
+
+}  // namespace
+
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// y (bf16) = max(a, 0), channel slices
+__global__ void relu_kernel(const float* __restrict__ a, int csa, bf16* __restrict__ y, int csy, long long npix,
+                            int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix * C) return;
+    const long long p = k / C;
+    const int c = (int)(k - p * C);
+    y[p * csy + c] = __float2bfloat16_rn(fmaxf(a[p * csa + c], 0.0f));
+}
+
+// ga = g where a > 0 else 0 (FP32), and its bf16 copy (optional)
+__global__ void relu_bwd_kernel(const float* __restrict__ g, int csg, const float* __restrict__ a, int csa,
+                                float* __restrict__ ga, bf16* __restrict__ ga16, long long npix, int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix * C) return;
+    const long long p = k / C;
+    const int c = (int)(k - p * C);
+    const float v = a[p * csa + c] > 0.0f ? g[p * csg + c] : 0.0f;
+    ga[k] = v;
+    if (ga16) ga16[k] = __float2bfloat16_rn(v);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, int csa, bf16* __restrict__ y, int csy, long long npix,
+                               int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix * C) return;
+    const long long p = k / C;
+    const int c = (int)(k - p * C);
+    y[p * csy + c] = __float2bfloat16_rn(a[p * csa + c]);
+}
+
+// out = a + b on channel slices
+__global__ void add_kernel(const float* __restrict__ a, int csa, const float* __restrict__ b, int csb,
+                           float* __restrict__ out, int cso, long long npix, int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix * C) return;
+    const long long p = k / C;
+    const int c = (int)(k - p * C);
+    out[p * cso + c] = a[p * csa + c] + b[p * csb + c];
+}
+
+// 8x8 average pooling, bf16 -> bf16; (N, H, W) the full-resolution grid
+__global__ void pool_kernel(const bf16* __restrict__ x, int csx, bf16* __restrict__ y, int csy, int N, int H, int W,
+                            int C) {
+    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)N * Hc * Wc * C) return;
+    const int c = (int)(k % C);
+    const long long q = k / C;
+    const int xc = (int)(q % Wc), yc = (int)((q / Wc) % Hc);
+    const long long n = q / ((long long)Hc * Wc);
+    float s = 0.0f;
+    for (int i = 0; i < LBM_SG_POOL; ++i)
+        for (int j = 0; j < LBM_SG_POOL; ++j) {
+            const long long p = (n * H + yc * LBM_SG_POOL + i) * W + xc * LBM_SG_POOL + j;
+            s += __bfloat162float(x[p * csx + c]);
+        }
+    y[q * csy + c] = __float2bfloat16_rn(s * (1.0f / (LBM_SG_POOL * LBM_SG_POOL)));
+}
+
+// gx[full] = g[coarse] / 64
+__global__ void pool_bwd_kernel(const float* __restrict__ g, int csg, float* __restrict__ gx, int csx, int N, int H,
+                                int W, int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)N * H * W * C) return;
+    const int c = (int)(k % C);
+    const long long p = k / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long long n = p / ((long long)H * W);
+    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+    const long long q = (n * Hc + y / LBM_SG_POOL) * Wc + x / LBM_SG_POOL;
+    gx[p * csx + c] = g[q * csg + c] * (1.0f / (LBM_SG_POOL * LBM_SG_POOL));
+}
+
+// nearest upsampling by 8, bf16 -> bf16; (N, H, W) the full-resolution grid
+__global__ void upsample_kernel(const bf16* __restrict__ x, int csx, bf16* __restrict__ y, int csy, int N, int H,
+                                int W, int C) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)N * H * W * C) return;
+    const int c = (int)(k % C);
+    const long long p = k / C;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const long long n = p / ((long long)H * W);
+    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+    const long long q = (n * Hc + yy / LBM_SG_POOL) * Wc + xx / LBM_SG_POOL;
+    y[p * csy + c] = x[q * csx + c];
+}
+
+// gx[coarse] = sum of g over the 8x8 block
+__global__ void upsample_bwd_kernel(const float* __restrict__ g, int csg, float* __restrict__ gx, int csx, int N,
+                                    int H, int W, int C) {
+    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)N * Hc * Wc * C) return;
+    const int c = (int)(k % C);
+    const long long q = k / C;
+    const int xc = (int)(q % Wc), yc = (int)((q / Wc) % Hc);
+    const long long n = q / ((long long)Hc * Wc);
+    float s = 0.0f;
+    for (int i = 0; i < LBM_SG_POOL; ++i)
+        for (int j = 0; j < LBM_SG_POOL; ++j) {
+            const long long p = (n * H + yc * LBM_SG_POOL + i) * W + xc * LBM_SG_POOL + j;
+            s += g[p * csg + c];
+        }
+    gx[q * csx + c] = s;
+}
+
+// per-block partial sums of column c of g (rows = pixels), fixed order
+__global__ void colsum_partial_kernel(const float* __restrict__ g, int csg, long long npix, int C,
+                                      float* __restrict__ part) {
+    __shared__ float sh[kThreads];
+    const int c = blockIdx.y;
+    float s = 0.0f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x)
+        s += g[p * csg + c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void colsum_finish_kernel(const float* __restrict__ part, int nb, int C, float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.0f;
+    for (int b = 0; b < nb; ++b) s += part[(long long)c * nb + b];
+    out[c] = s;
+}
+
+// out = x + delta on the first C channels; g = 2 (out - t) / (npix C) (zero beyond C up to csd);
+// block partials of sum (out - t)^2 in FP64
+__global__ void mse_kernel(const float* __restrict__ x, int csx, const float* __restrict__ delta, int csd,
+                           const float* __restrict__ t, int cst, float* __restrict__ g, long long npix, int C,
+                           double* __restrict__ part) {
+    __shared__ double sh[kThreads];
+    double s = 0.0;
+    const double inv = 1.0 / ((double)npix * C);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < npix * csd;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long p = k / csd;
+        const int c = (int)(k - p * csd);
+        float gv = 0.0f;
+        if (c < C) {
+            const double e = (double)x[p * csx + c] + (double)delta[k] - (double)t[p * cst + c];
+            s += e * e;
+            gv = (float)(2.0 * e * inv);
+        }
+        g[k] = gv;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void mse_finish_kernel(const double* __restrict__ part, int nb, double inv_count, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    out[0] = s * inv_count;
+}
+
+// Adam on FP32 master values, with the bf16 copy used by the convolutions
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2, bf16* __restrict__ w16) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.0f - b1) * gk;
+    const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    const float wk = w[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    w[k] = wk;
+    if (w16) w16[k] = __float2bfloat16_rn(wk);
+}
+
+// LB fields (FP64, x fastest) -> normalised channels-last input: channel c = field c / scale c
+__global__ void pack_kernel(const double* __restrict__ f0, const double* __restrict__ f1, const double* __restrict__ f2,
+                            const double* __restrict__ f3, double s0, double s1, double s2, double s3,
+                            float* __restrict__ x32, int cs32, bf16* __restrict__ x16, int cs16, long long npix) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const float v[4] = {(float)(f0[p] / s0), (float)(f1[p] / s1), (float)(f2[p] / s2), (float)(f3[p] / s3)};
+    for (int c = 0; c < 4; ++c) x32[p * cs32 + c] = v[c];
+    for (int c = 0; c < cs16; ++c) x16[p * cs16 + c] = __float2bfloat16_rn(c < 4 ? v[c] : 0.0f);
+}
+
+// fields = (x + delta) * scale
+__global__ void unpack_kernel(const float* __restrict__ x32, int cs32, const float* __restrict__ delta, int csd,
+                              double* __restrict__ f0, double* __restrict__ f1, double* __restrict__ f2,
+                              double* __restrict__ f3, double s0, double s1, double s2, double s3, long long npix) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    double* f[4] = {f0, f1, f2, f3};
+    const double s[4] = {s0, s1, s2, s3};
+    for (int c = 0; c < 4; ++c) f[c][p] = ((double)x32[p * cs32 + c] + (double)delta[p * csd + c]) * s[c];
+}
+
+__global__ void shift_kernel(double* __restrict__ a, long long n, double s) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) a[k] += s;
+}
+
+bool conv_dims_ok(long long M, int Ci, int Co) { return M > 0 && M % 16 == 0 && Ci > 0 && Ci % 16 == 0 && Co > 0 && Co % 16 == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, float* y, int csy, int N, int H, int W,
+                   int Ci, int Co, void* stream) {
+    const long long M = (long long)N * H * W;
+    if (!x || !w || !y || N < 1 || H < 1 || W < 1 || !conv_dims_ok(M, Ci, Co) || csx < Ci || csx % 2 || csy < Co)
+        return LBM_EINVAL;
+    if (Co > 64) return LBM_EINVAL;
+    const long long warps = M / 16;
+    const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bf16* xb = (const bf16*)x;
+    const bf16* wb = (const bf16*)w;
+    switch (Co / 16) {
+        case 1: conv_fwd_kernel<2><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 2: conv_fwd_kernel<4><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 3: conv_fwd_kernel<6><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 4: conv_fwd_kernel<8><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        default: return LBM_EINVAL;
+    }
+    return check(cudaGetLastError());
+}
+
+long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co) {
+    const long long M = (long long)N * H * W;
+    return ((M + kChunk - 1) / kChunk) * (long long)Co * 9 * Ci;
+}
+
+int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float* gw, float* scratch,
+                         long long scratch_floats, int N, int H, int W, int Ci, int Co, void* stream) {
+    const long long M = (long long)N * H * W;
+    if (!x || !gy || !gw || !scratch || N < 1 || H < 1 || W < 1 || !conv_dims_ok(M, Ci, Co) || csx < Ci || csg < Co)
+        return LBM_EINVAL;
+    const long long need = lbm_sg_wgrad_scratch_floats(N, H, W, Ci, Co);
+    if (scratch_floats < need) return LBM_EINVAL;
+    const long long nchunks = (M + kChunk - 1) / kChunk;
+    const long long warps = nchunks * 9LL * (Co / 16) * (Ci / 8);
+    cudaStream_t s = (cudaStream_t)stream;
+    conv_wgrad_kernel<<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>((const bf16*)x, csx, (const bf16*)gy, csg,
+                                                                          scratch, M, H, W, Ci, Co);
+    const long long K = (long long)Co * 9 * Ci;
+    sum_chunks_kernel<<<blocks(K), kThreads, 0, s>>>(scratch, nchunks, K, gw);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_weight_flip(const void* w, void* wt, int Ci, int Co, void* stream) {
+    if (!w || !wt || Ci < 1 || Co < 1) return LBM_EINVAL;
+    weight_flip_kernel<<<blocks((long long)Co * 9 * Ci), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)w, (bf16*)wt,
+                                                                                              Ci, Co);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_bias_grad(const float* g, int csg, float* gb, float* scratch, long long npix, int C, void* stream) {
+    if (!g || !gb || !scratch || npix < 1 || C < 1 || csg < C) return LBM_EINVAL;
+    const int nb = (int)(npix < 64LL * kThreads ? (npix + kThreads - 1) / kThreads : 64);
+    cudaStream_t s = (cudaStream_t)stream;
+    colsum_partial_kernel<<<dim3(nb, C), kThreads, 0, s>>>(g, csg, npix, C, scratch);
+    colsum_finish_kernel<<<blocks(C), kThreads, 0, s>>>(scratch, nb, C, gb);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_relu(const float* a, int csa, void* y, int csy, long long npix, int C, void* stream) {
+    if (!a || !y || npix < 1 || C < 1 || csa < C || csy < C) return LBM_EINVAL;
+    relu_kernel<<<blocks(npix * C), kThreads, 0, (cudaStream_t)stream>>>(a, csa, (bf16*)y, csy, npix, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_relu_bwd(const float* g, int csg, const float* a, int csa, float* ga, void* ga16, long long npix, int C,
+                    void* stream) {
+    if (!g || !a || !ga || npix < 1 || C < 1 || csg < C || csa < C) return LBM_EINVAL;
+    relu_bwd_kernel<<<blocks(npix * C), kThreads, 0, (cudaStream_t)stream>>>(g, csg, a, csa, ga, (bf16*)ga16, npix, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_to_bf16(const float* a, int csa, void* y, int csy, long long npix, int C, void* stream) {
+    if (!a || !y || npix < 1 || C < 1 || csa < C || csy < C) return LBM_EINVAL;
+    to_bf16_kernel<<<blocks(npix * C), kThreads, 0, (cudaStream_t)stream>>>(a, csa, (bf16*)y, csy, npix, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_add(const float* a, int csa, const float* b, int csb, float* out, int cso, long long npix, int C,
+               void* stream) {
+    if (!a || !b || !out || npix < 1 || C < 1 || csa < C || csb < C || cso < C) return LBM_EINVAL;
+    add_kernel<<<blocks(npix * C), kThreads, 0, (cudaStream_t)stream>>>(a, csa, b, csb, out, cso, npix, C);
+    return check(cudaGetLastError());
+}
+
+static bool pool_dims_ok(int N, int H, int W, int C) {
+    return N >= 1 && H >= LBM_SG_POOL && W >= LBM_SG_POOL && H % LBM_SG_POOL == 0 && W % LBM_SG_POOL == 0 && C >= 1;
+}
+
+int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream) {
+    if (!x || !y || !pool_dims_ok(N, H, W, C) || csx < C || csy < C) return LBM_EINVAL;
+    const long long n = (long long)N * (H / LBM_SG_POOL) * (W / LBM_SG_POOL) * C;
+    pool_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)x, csx, (bf16*)y, csy, N, H, W, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream) {
+    if (!g || !gx || !pool_dims_ok(N, H, W, C) || csx < C || csg < C) return LBM_EINVAL;
+    pool_bwd_kernel<<<blocks((long long)N * H * W * C), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream) {
+    if (!x || !y || !pool_dims_ok(N, H, W, C) || csx < C || csy < C) return LBM_EINVAL;
+    upsample_kernel<<<blocks((long long)N * H * W * C), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)x, csx,
+                                                                                            (bf16*)y, csy, N, H, W, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream) {
+    if (!g || !gx || !pool_dims_ok(N, H, W, C) || csx < C || csg < C) return LBM_EINVAL;
+    const long long n = (long long)N * (H / LBM_SG_POOL) * (W / LBM_SG_POOL) * C;
+    upsample_bwd_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W, C);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_mse(const float* x, int csx, const float* delta, int csd, const float* target, int cst, float* g,
+               double* scratch, double* loss, long long npix, int C, void* stream) {
+    if (!x || !delta || !target || !g || !scratch || !loss || npix < 1 || C < 1 || csd < C || csx < C || cst < C)
+        return LBM_EINVAL;
+    const int nb = 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    mse_kernel<<<nb, kThreads, 0, s>>>(x, csx, delta, csd, target, cst, g, npix, C, scratch);
+    mse_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, 1.0 / ((double)npix * C), loss);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
+                int step, void* w16, void* stream) {
+    if (!w || !m || !v || !g || n < 1 || step < 1 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1))
+        return LBM_EINVAL;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    adam_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>(w, m, v, g, n, lr, b1, b2, eps, c1, c2, (bf16*)w16);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_pack(const double* phi, const double* ux, const double* uy, const double* P, const double scale[4],
+                float* x32, int cs32, void* x16, int cs16, long long npix, void* stream) {
+    if (!phi || !ux || !uy || !P || !scale || !x32 || !x16 || npix < 1 || cs32 < 4 || cs16 < 4) return LBM_EINVAL;
+    for (int c = 0; c < 4; ++c)
+        if (!(scale[c] > 0)) return LBM_EINVAL;
+    pack_kernel<<<blocks(npix), kThreads, 0, (cudaStream_t)stream>>>(phi, ux, uy, P, scale[0], scale[1], scale[2],
+                                                                      scale[3], x32, cs32, (bf16*)x16, cs16, npix);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
+                  double* P, const double scale[4], long long npix, void* stream) {
+    if (!x32 || !delta || !phi || !ux || !uy || !P || !scale || npix < 1 || cs32 < 4 || csd < 4) return LBM_EINVAL;
+    unpack_kernel<<<blocks(npix), kThreads, 0, (cudaStream_t)stream>>>(x32, cs32, delta, csd, phi, ux, uy, P, scale[0],
+                                                                        scale[1], scale[2], scale[3], npix);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_shift(double* a, long long n, double s, void* stream) {
+    if (!a || n < 1) return LBM_EINVAL;
+    shift_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>(a, n, s);
+    return check(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -84,6 +84,31 @@ SIGNATURES = [
     ("lbm_batch_plan", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.c_int, _IP,
                                       ctypes.c_int]),
     ("lbm_batch_destroy", None, [_VP]),
+    ("lbm_sg_conv3x3", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
+    ("lbm_sg_wgrad_scratch_floats", ctypes.c_longlong, [ctypes.c_int] * 5),
+    ("lbm_sg_conv3x3_wgrad", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_longlong]
+     + [ctypes.c_int] * 5 + [_VP]),
+    ("lbm_sg_weight_flip", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("lbm_sg_bias_grad", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_sg_relu", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_sg_relu_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_longlong,
+                                       ctypes.c_int, _VP]),
+    ("lbm_sg_to_bf16", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_sg_add", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
+                                  ctypes.c_int, _VP]),
+    ("lbm_sg_pool", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
+    ("lbm_sg_pool_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
+    ("lbm_sg_upsample", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
+    ("lbm_sg_upsample_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
+    ("lbm_sg_mse", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP,
+                                  ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_sg_adam", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_int, _VP, _VP]),
+    ("lbm_sg_pack", ctypes.c_int, [_VP, _VP, _VP, _VP, _DP, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
+                                   _VP]),
+    ("lbm_sg_unpack", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _DP,
+                                     ctypes.c_longlong, _VP]),
+    ("lbm_sg_shift", ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
