@@ -92,15 +92,22 @@ int lbm_sg_adam(float* w, float* m, float* v, const float* g, long long n, float
                 int step, void* w16, void* stream);
 
 /* Network input from one grid's fields (device FP64, x fastest, as
- * lbm_macro writes them, u as two component arrays): x32 (float, stride
- * cs32 >= 4) = (phi, ux, uy, P) / scale, x16 (bf16, stride cs16 >= 4) the
- * same rounded, zero in channels 4..cs16-1. */
-int lbm_sg_pack(const double* phi, const double* ux, const double* uy, const double* P, const double scale[4],
+ * lbm_macro writes them: phi, the two components of rho u, P): x32 (float,
+ * stride cs32 >= 4) = (phi, rho u_x, rho u_y, P) / scale, x16 (bf16, stride
+ * cs16 >= 4) the same rounded, zero in channels 4..cs16-1. */
+int lbm_sg_pack(const double* phi, const double* rux, const double* ruy, const double* P, const double scale[4],
                 float* x32, int cs32, void* x16, int cs16, long long npix, void* stream);
 
-/* Fields from the network output: (phi, ux, uy, P) = (x32 + delta) * scale. */
+/* Fields for lbm_init_fields from the network output: (phi, rho u, P) =
+ * (x32 + delta) * scale, written as phi, u = rho u / (rho_L + phi rho_dif)
+ * (the density of the paper's rho(phi)) and P. */
 int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
-                  double* P, const double scale[4], long long npix, void* stream);
+                  double* P, const double scale[4], double rho_L, double rho_dif, long long npix, void* stream);
+
+/* out (device, 2 doubles) = (sum (a - b)^2, sum a^2) over n values, FP64 in
+ * a fixed order; scratch: 512 doubles.  The convergence measure of the
+ * warm-start comparison: ||P(t) - P(t - k)|| / ||P(t)||. */
+int lbm_sg_residual(const double* a, const double* b, long long n, double* out, double* scratch, void* stream);
 
 /* a[k] += s (used to restore the exact total of phi after a prediction). */
 int lbm_sg_shift(double* a, long long n, double s, void* stream);

@@ -345,7 +345,7 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
     if (w16) w16[k] = __float2bfloat16_rn(wk);
 }
 
-// LB fields (FP64, x fastest) -> normalised channels-last input: channel c = field c / scale c
+// LB fields (FP64, x fastest: phi, rho u_x, rho u_y, P) -> normalised channels-last input: channel c = field c / scale c
 __global__ void pack_kernel(const double* __restrict__ f0, const double* __restrict__ f1, const double* __restrict__ f2,
                             const double* __restrict__ f3, double s0, double s1, double s2, double s3,
                             float* __restrict__ x32, int cs32, bf16* __restrict__ x16, int cs16, long long npix) {
@@ -356,20 +356,54 @@ __global__ void pack_kernel(const double* __restrict__ f0, const double* __restr
     for (int c = 0; c < cs16; ++c) x16[p * cs16 + c] = __float2bfloat16_rn(c < 4 ? v[c] : 0.0f);
 }
 
-// fields = (x + delta) * scale
+// (phi, rho u_x, rho u_y, P) = (x + delta) * scale, then u = rho u / rho(phi)
 __global__ void unpack_kernel(const float* __restrict__ x32, int cs32, const float* __restrict__ delta, int csd,
                               double* __restrict__ f0, double* __restrict__ f1, double* __restrict__ f2,
-                              double* __restrict__ f3, double s0, double s1, double s2, double s3, long long npix) {
+                              double* __restrict__ f3, double s0, double s1, double s2, double s3, double rho_L,
+                              double rho_dif, long long npix) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    double* f[4] = {f0, f1, f2, f3};
+    double v[4];
     const double s[4] = {s0, s1, s2, s3};
-    for (int c = 0; c < 4; ++c) f[c][p] = ((double)x32[p * cs32 + c] + (double)delta[p * csd + c]) * s[c];
+    for (int c = 0; c < 4; ++c) v[c] = ((double)x32[p * cs32 + c] + (double)delta[p * csd + c]) * s[c];
+    const double rho = rho_L + v[0] * rho_dif;
+    f0[p] = v[0];
+    f1[p] = v[1] / rho;
+    f2[p] = v[2] / rho;
+    f3[p] = v[3];
 }
 
 __global__ void shift_kernel(double* __restrict__ a, long long n, double s) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) a[k] += s;
+}
+
+// block partials of sum (a - b)^2 and sum a^2 (FP64, fixed order)
+__global__ void residual_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                        double* __restrict__ part) {
+    __shared__ double s0[kThreads], s1[kThreads];
+    double d2 = 0.0, a2 = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double d = a[k] - b[k];
+        d2 += d * d;
+        a2 += a[k] * a[k];
+    }
+    s0[threadIdx.x] = d2;
+    s1[threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
+}
+
+__global__ void residual_finish_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double d2 = 0.0, a2 = 0.0;
+    for (int k = 0; k < nb; ++k) { d2 += part[2 * k]; a2 += part[2 * k + 1]; }
+    out[0] = d2;
+    out[1] = a2;
 }
 
 bool conv_dims_ok(long long M, int Ci, int Co) { return M > 0 && M % 16 == 0 && Ci > 0 && Ci % 16 == 0 && Co > 0 && Co % 16 == 0; }
@@ -525,10 +559,21 @@ int lbm_sg_pack(const double* phi, const double* ux, const double* uy, const dou
 }
 
 int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
-                  double* P, const double scale[4], long long npix, void* stream) {
-    if (!x32 || !delta || !phi || !ux || !uy || !P || !scale || npix < 1 || cs32 < 4 || csd < 4) return LBM_EINVAL;
+                  double* P, const double scale[4], double rho_L, double rho_dif, long long npix, void* stream) {
+    if (!x32 || !delta || !phi || !ux || !uy || !P || !scale || npix < 1 || cs32 < 4 || csd < 4 || !(rho_L > 0))
+        return LBM_EINVAL;
     unpack_kernel<<<blocks(npix), kThreads, 0, (cudaStream_t)stream>>>(x32, cs32, delta, csd, phi, ux, uy, P, scale[0],
-                                                                        scale[1], scale[2], scale[3], npix);
+                                                                        scale[1], scale[2], scale[3], rho_L, rho_dif,
+                                                                        npix);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_residual(const double* a, const double* b, long long n, double* out, double* scratch, void* stream) {
+    if (!a || !b || !out || !scratch || n < 1) return LBM_EINVAL;
+    const int nb = 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    residual_partial_kernel<<<nb, kThreads, 0, s>>>(a, b, n, scratch);
+    residual_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
     return check(cudaGetLastError());
 }
 

@@ -95,3 +95,38 @@ def batch_cases(n_cases=512, L_min=32, L_max=512, seed=0):
         drop = bool(rng.integers(0, 2))
         cases.append(dict(L=L, R=R, rho_ratio=ratio, tau=tau, W=W, drop=drop))
     return cases
+
+
+def drops(L, seed, n_min=1, n_max=4, R_min=12.0, R_max=48.0, W=4.0, gap=None):
+    """(phi, u, P, drops) of 1-4 static drops (phi = 1 inside) in a periodic
+    L x L box, shape (1, L, L): radii uniform in [R_min, R_max], centres
+    uniform and off the nodes, drops at least `gap` (default 2 W) apart along
+    the periodic distance, phi the sum of the tanh profiles (clipped to 1).
+    A drop that finds no room after 200 tries is left out; the drop list
+    gives (x, y, R)."""
+    rng = np.random.default_rng([seed, 1812])
+    gap = 2.0 * W if gap is None else gap
+    n = int(rng.integers(n_min, n_max + 1))
+    placed = []
+    for _ in range(n):
+        for _attempt in range(200):
+            R = float(rng.uniform(R_min, min(R_max, L / 2.0 - W)))
+            c = rng.uniform(0.0, L, size=2) + 0.31
+            ok = True
+            for (px, py, pR) in placed:
+                d = np.abs(np.array([c[0] - px, c[1] - py]))
+                d = np.minimum(d, L - d)
+                if np.hypot(*d) < R + pR + gap:
+                    ok = False
+                    break
+            if ok:
+                placed.append((float(c[0]), float(c[1]), R))
+                break
+    if not placed:
+        placed.append((L / 2.0 + 0.31, L / 2.0 - 0.23, R_min))
+    phi = np.zeros((1, L, L))
+    for (cx, cy, R) in placed:
+        p, _, _ = sphere((1, L, L), (cx, cy, 0.0), R, W, drop=True)
+        phi += p
+    phi = np.minimum(phi, 1.0)
+    return phi, np.zeros((3, 1, L, L)), np.zeros((1, L, L)), placed

@@ -1,0 +1,175 @@
+"""Learned warm start of the phase-field LB solver, and time-to-tolerance.
+
+A static-drop state relaxes slowly from its initial fields: starting from
+u = 0, P = 0 the Laplace pressure jump builds up as acoustic waves that the
+viscosity damps over tens of thousands of steps.  The surrogate
+(paper_1812_00118_gb300.surrogate) is trained on pairs the solver itself
+generates -- the initial fields (phi0, 0, 0) and the state T steps later --
+and its prediction replaces the initial fields: populations are rebuilt from
+it as equilibria (lbm_init_fields), with the total of phi restored exactly
+(uniform shift of phi, FP64 sums).  The plain solver then continues and
+decides convergence, so the method stays the judge and the fallback.
+
+Convergence (time-to-tolerance): every `check_every` steps the pressure
+field P(t) is compared with P(t - check_every); the run has converged when
+||P(t) - P(t - k)|| / ||P(t)|| < tol for `consecutive` checks in a row
+(FP64 sums on the GPU, lbm_sg_residual).
+
+Everything that computes runs in the library's kernels; PyTorch allocates
+device memory and copies it.
+"""
+import ctypes
+
+import numpy as np
+
+from . import inputs as I
+from . import lbm as L
+from .surrogate import NC, _ck, _ptr
+
+# normalisation of (phi, rho u_x, rho u_y, P) for the network: spurious
+# currents are ~1e-5, Laplace jumps sigma / R ~ 4e-4 - 1e-3
+SCALE = (1.0, 1e-5, 1e-5, 2e-4)
+# the warm-start workload: drops at density ratio 1000, water-like viscosity
+# of the paper's shear and Galilean tests (nu = 1.7e-2)
+PHYS = dict(M=0.1, W=4.0, sigma=0.01, rho_L=1e-3, rho_H=1.0, nu_L=1.0 / 60.0, nu_H=1.0 / 60.0)
+RADII = (12.0, 28.0)
+
+
+def case_params(store=L.F32):
+    return L.make_params(store=store, g_scale=(1e3 if store == L.F16S else 0.0), **PHYS)
+
+
+def case_fields(Lsz, seed, R_min=RADII[0], R_max=RADII[1]):
+    phi, u, P, placed = I.drops(Lsz, seed, R_min=R_min, R_max=R_max, W=PHYS["W"])
+    return phi.reshape(-1).copy(), placed
+
+
+class DeviceFields:
+    """FP64 device fields of one grid (phi, P, rho u as lbm_macro writes them,
+    and u for lbm_init_fields)."""
+
+    def __init__(self, torch, n):
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+        self.n = n
+        self.phi, self.P, self.ru, self.u = z(n), z(n), z(2 * n), z(2 * n)
+
+
+def _scale_arr():
+    return (ctypes.c_double * 4)(*SCALE)
+
+
+def pack(lib, f, x32, x16, stream):
+    """x32/x16 (device addresses) <- (phi, rho u, P) of f."""
+    n = f.n
+    ru = f.ru.data_ptr()
+    _ck(lib.lbm_sg_pack(_ptr(f.phi), ctypes.c_void_p(ru), ctypes.c_void_p(ru + 8 * n), _ptr(f.P), _scale_arr(),
+                        ctypes.c_void_p(x32), NC, ctypes.c_void_p(x16), 16, n, stream), "lbm_sg_pack")
+
+
+def generate_pairs(torch, Lsz, seeds, T, store=L.F32):
+    """Training pairs from the batched solver: inputs (phi0, 0, 0) and the
+    state after T steps, normalised; returns (X, Y), each (n, L*L, 4)
+    float32 on the device."""
+    lib = L.load()
+    n, npix = len(seeds), Lsz * Lsz
+    prm = case_params(store)
+    batch = L.Batch([(Lsz, Lsz)] * n, prm)
+    X = torch.zeros(n, npix, NC, dtype=torch.float32, device="cuda")
+    Y = torch.zeros(n, npix, NC, dtype=torch.float32, device="cuda")
+    tmp16 = torch.zeros(npix, 16, dtype=torch.bfloat16, device="cuda")
+    f = DeviceFields(torch, npix)
+    stream = torch.cuda.current_stream().cuda_stream
+    for k, sd in enumerate(seeds):
+        phi0, _ = case_fields(Lsz, sd)
+        f.phi.copy_(torch.from_numpy(phi0))
+        for t in (f.P, f.ru, f.u):
+            t.zero_()
+        batch.grid(k).init_fields(f.phi, f.u, f.P)
+        pack(lib, f, X[k].data_ptr(), tmp16.data_ptr(), stream)
+    batch.step(T)
+    for k in range(n):
+        batch.grid(k).macro(f.phi, f.P, f.ru)
+        pack(lib, f, Y[k].data_ptr(), tmp16.data_ptr(), stream)
+    torch.cuda.synchronize()
+    batch.close()
+    return X, Y
+
+
+def train(torch, sg, X, Y, iters, lr=2e-3, seed=0, log_every=100, decay_at=0.7):
+    """Adam on random mini-batches of sg.N images (indices drawn on the host);
+    the learning rate drops tenfold after decay_at of the iterations.
+    Returns [(iteration, loss)]."""
+    rng = np.random.default_rng(seed)
+    n, npix = X.shape[0], X.shape[1]
+    xb = torch.zeros(sg.N * npix, NC, dtype=torch.float32, device="cuda")
+    yb = torch.zeros_like(xb)
+    hist = []
+    for it in range(iters):
+        idx = rng.choice(n, size=sg.N, replace=n < sg.N)
+        for j, k in enumerate(idx):   # gather the mini-batch (device copies)
+            xb[j * npix:(j + 1) * npix].copy_(X[int(k)])
+            yb[j * npix:(j + 1) * npix].copy_(Y[int(k)])
+        loss = sg.train_step(xb, yb, lr=lr if it < decay_at * iters else 0.1 * lr)
+        if it % log_every == 0 or it == iters - 1:
+            hist.append((it, float(loss.item())))
+    return hist
+
+
+def predict_into(torch, sg1, sim, phi0_host, prm):
+    """Warm start: predict the state of (phi0, 0, 0) with a one-image
+    surrogate, restore the exact total of phi, and initialise sim from it."""
+    lib = L.load()
+    n = sg1.M
+    stream = torch.cuda.current_stream().cuda_stream
+    f = DeviceFields(torch, n)
+    f.phi.copy_(torch.from_numpy(phi0_host))
+    tmp16 = torch.zeros(n, 16, dtype=torch.bfloat16, device="cuda")
+    x32 = torch.zeros(n, NC, dtype=torch.float32, device="cuda")
+    pack(lib, f, x32.data_ptr(), tmp16.data_ptr(), stream)
+    sg1.set_input(x32)
+    delta = sg1.forward()
+    u = f.u.data_ptr()
+    rho_dif = prm.rho_H - prm.rho_L
+    _ck(lib.lbm_sg_unpack(_ptr(sg1.x32), NC, _ptr(delta), 16, _ptr(f.phi), ctypes.c_void_p(u),
+                          ctypes.c_void_p(u + 8 * n), _ptr(f.P), _scale_arr(), prm.rho_L, rho_dif, n, stream),
+        "lbm_sg_unpack")
+    # total of phi restored exactly: FP64 sums on the GPU, uniform shift
+    sums = torch.zeros(4, dtype=torch.float64, device="cuda")
+    _ck(lib.lbm_field_sums_noalloc(_ptr(f.phi), _ptr(f.P), None, None, None, n, prm.rho_L, rho_dif, _ptr(sums),
+                                   ctypes.c_void_p(stream)), "lbm_field_sums_noalloc")
+    target = float(np.sum(phi0_host))
+    _ck(lib.lbm_sg_shift(_ptr(f.phi), n, (target - float(sums[0].item())) / n, stream), "lbm_sg_shift")
+    sim.init_fields(f.phi, f.u, f.P)
+
+
+def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max_steps=200000):
+    """Steps until ||P(t) - P(t - check_every)|| / ||P(t)|| < tol for
+    `consecutive` checks (None if not within max_steps); returns (steps,
+    device ms of the whole loop including the checks, last residual)."""
+    lib = L.load()
+    n = sim.N
+    stream = torch.cuda.current_stream().cuda_stream
+    P = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(2)]
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    scratch = torch.zeros(512, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.macro(phi, P[0], None)
+    steps, ok, r, cur, done = 0, 0, float("inf"), 0, None
+    while steps < max_steps:
+        sim.step(check_every)
+        steps += check_every
+        nxt = 1 - cur
+        sim.macro(phi, P[nxt], None)
+        _ck(lib.lbm_sg_residual(_ptr(P[nxt]), _ptr(P[cur]), n, _ptr(out), _ptr(scratch), stream), "lbm_sg_residual")
+        d2, a2 = out.tolist()
+        r = float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
+        cur = nxt
+        ok = ok + 1 if r < tol else 0
+        if ok >= consecutive:
+            done = steps
+            break
+    e1.record()
+    e1.synchronize()
+    return done, e0.elapsed_time(e1), r
