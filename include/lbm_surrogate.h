@@ -109,6 +109,11 @@ int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, doubl
  * warm-start comparison: ||P(t) - P(t - k)|| / ||P(t)||. */
 int lbm_sg_residual(const double* a, const double* b, long long n, double* out, double* scratch, void* stream);
 
+/* iters times two explicit diffusion passes a <- a + k lap(a) (five-point,
+ * periodic in each of N images of H x W, 0 <= k <= 1/4, tmp: N H W doubles):
+ * removes the block-scale roughness of a prediction before it seeds a run. */
+int lbm_sg_smooth(double* a, double* tmp, int N, int H, int W, int iters, double k, void* stream);
+
 /* a[k] += s (used to restore the exact total of phi after a prediction). */
 int lbm_sg_shift(double* a, long long n, double s, void* stream);
 

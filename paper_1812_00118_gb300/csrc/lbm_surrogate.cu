@@ -406,6 +406,20 @@ __global__ void residual_finish_kernel(const double* __restrict__ part, int nb, 
     out[1] = a2;
 }
 
+// b = a + k lap(a), five-point Laplacian, periodic in each H x W image
+__global__ void smooth_kernel(const double* __restrict__ a, double* __restrict__ b, int N, int H, int W, double k) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long long)N * H * W) return;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long long base = p - (long long)y * W - x;
+    const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
+    const double c = a[p];
+    const double lap = a[base + (long long)y * W + xm] + a[base + (long long)y * W + xp] + a[base + (long long)ym * W + x] +
+                       a[base + (long long)yp * W + x] - 4.0 * c;
+    b[p] = c + k * lap;
+}
+
 bool conv_dims_ok(long long M, int Ci, int Co) { return M > 0 && M % 16 == 0 && Ci > 0 && Ci % 16 == 0 && Co > 0 && Co % 16 == 0; }
 
 }  // namespace
@@ -574,6 +588,17 @@ int lbm_sg_residual(const double* a, const double* b, long long n, double* out, 
     cudaStream_t s = (cudaStream_t)stream;
     residual_partial_kernel<<<nb, kThreads, 0, s>>>(a, b, n, scratch);
     residual_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_smooth(double* a, double* tmp, int N, int H, int W, int iters, double k, void* stream) {
+    if (!a || !tmp || N < 1 || H < 1 || W < 1 || iters < 0 || !(k >= 0.0 && k <= 0.25)) return LBM_EINVAL;
+    const long long n = (long long)N * H * W;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int it = 0; it < iters; ++it) {
+        smooth_kernel<<<blocks(n), kThreads, 0, s>>>(a, tmp, N, H, W, k);
+        smooth_kernel<<<blocks(n), kThreads, 0, s>>>(tmp, a, N, H, W, k);
+    }
     return check(cudaGetLastError());
 }
 

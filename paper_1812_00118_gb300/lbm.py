@@ -109,6 +109,8 @@ SIGNATURES = [
     ("lbm_sg_unpack", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _DP, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_longlong, _VP]),
     ("lbm_sg_residual", ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP, _VP]),
+    ("lbm_sg_smooth", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     _VP]),
     ("lbm_sg_shift", ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),

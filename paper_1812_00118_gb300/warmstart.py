@@ -4,10 +4,10 @@ A static-drop state relaxes slowly from its initial fields: starting from
 u = 0, P = 0 the Laplace pressure jump builds up as acoustic waves that the
 viscosity damps over tens of thousands of steps.  The surrogate
 (paper_1812_00118_gb300.surrogate) is trained on pairs the solver itself
-generates -- the initial fields (phi0, 0, 0) and the state T steps later --
-and its prediction replaces the initial fields: populations are rebuilt from
-it as equilibria (lbm_init_fields), with the total of phi restored exactly
-(uniform shift of phi, FP64 sums).  The plain solver then continues and
+generates -- the initial fields (phi0, 0, 0) and the pressure field T steps
+later -- and its prediction replaces the initial pressure: populations are
+rebuilt as equilibria of (phi0, 0, P_predicted) (lbm_init_fields), so phi
+and its total are exactly those of the plain start.  The plain solver then continues and
 decides convergence, so the method stays the judge and the fallback.
 
 Convergence (time-to-tolerance): every `check_every` steps the pressure
@@ -40,7 +40,8 @@ def case_params(store=L.F32):
 
 
 def case_fields(Lsz, seed, R_min=RADII[0], R_max=RADII[1]):
-    phi, u, P, placed = I.drops(Lsz, seed, R_min=R_min, R_max=R_max, W=PHYS["W"])
+    # drops three interface widths apart: static, no coalescence
+    phi, u, P, placed = I.drops(Lsz, seed, R_min=R_min, R_max=R_max, W=PHYS["W"], gap=3.0 * PHYS["W"])
     return phi.reshape(-1).copy(), placed
 
 
@@ -66,10 +67,11 @@ def pack(lib, f, x32, x16, stream):
                         ctypes.c_void_p(x32), NC, ctypes.c_void_p(x16), 16, n, stream), "lbm_sg_pack")
 
 
-def generate_pairs(torch, Lsz, seeds, T, store=L.F32):
+def generate_pairs(torch, Lsz, seeds, T, store=L.F32, max_u=0.05):
     """Training pairs from the batched solver: inputs (phi0, 0, 0) and the
     state after T steps, normalised; returns (X, Y), each (n, L*L, 4)
-    float32 on the device."""
+    float32 on the device, and the number of cases left out because their
+    run did not stay bounded (non-finite fields or |u| > max_u)."""
     lib = L.load()
     n, npix = len(seeds), Lsz * Lsz
     prm = case_params(store)
@@ -87,12 +89,24 @@ def generate_pairs(torch, Lsz, seeds, T, store=L.F32):
         batch.grid(k).init_fields(f.phi, f.u, f.P)
         pack(lib, f, X[k].data_ptr(), tmp16.data_ptr(), stream)
     batch.step(T)
+    keep = []
     for k in range(n):
+        d = batch.grid(k).diagnostics(raise_on_divergence=False)
+        if d["nonfinite"] > 0 or not d["max_u"] < max_u:
+            continue
         batch.grid(k).macro(f.phi, f.P, f.ru)
         pack(lib, f, Y[k].data_ptr(), tmp16.data_ptr(), stream)
+        keep.append(k)
     torch.cuda.synchronize()
     batch.close()
-    return X, Y
+    idx = torch.tensor(keep, dtype=torch.long, device="cuda")
+    X, Y = X.index_select(0, idx), Y.index_select(0, idx)
+    # the network predicts the pressure only: phi and u of the warm start stay
+    # the initial ones (u = 0).  The residual flows of the relaxing state are
+    # not a function of the initial fields, and a wrong velocity field feeds
+    # instabilities of the restarted run.
+    Y[:, :, :3].copy_(X[:, :, :3])
+    return X, Y, n - len(keep)
 
 
 def train(torch, sg, X, Y, iters, lr=2e-3, seed=0, log_every=100, decay_at=0.7):
@@ -115,9 +129,13 @@ def train(torch, sg, X, Y, iters, lr=2e-3, seed=0, log_every=100, decay_at=0.7):
     return hist
 
 
-def predict_into(torch, sg1, sim, phi0_host, prm):
-    """Warm start: predict the state of (phi0, 0, 0) with a one-image
-    surrogate, restore the exact total of phi, and initialise sim from it."""
+def predict_into(torch, sg1, sim, phi0_host, prm, smooth=3):
+    """Warm start: predict the pressure of (phi0, 0, 0) with a one-image
+    surrogate, smooth it (2 `smooth` diffusion passes of the block-scale
+    roughness of the coarse path), and initialise sim from (phi0, 0, P).
+    phi is phi0 itself, so its total is exactly that of the plain start; the
+    network's phi and rho u channels are not used (a phi a little below 0
+    in the light phase would make rho(phi) negative)."""
     lib = L.load()
     n = sg1.M
     stream = torch.cuda.current_stream().cuda_stream
@@ -133,12 +151,11 @@ def predict_into(torch, sg1, sim, phi0_host, prm):
     _ck(lib.lbm_sg_unpack(_ptr(sg1.x32), NC, _ptr(delta), 16, _ptr(f.phi), ctypes.c_void_p(u),
                           ctypes.c_void_p(u + 8 * n), _ptr(f.P), _scale_arr(), prm.rho_L, rho_dif, n, stream),
         "lbm_sg_unpack")
-    # total of phi restored exactly: FP64 sums on the GPU, uniform shift
-    sums = torch.zeros(4, dtype=torch.float64, device="cuda")
-    _ck(lib.lbm_field_sums_noalloc(_ptr(f.phi), _ptr(f.P), None, None, None, n, prm.rho_L, rho_dif, _ptr(sums),
-                                   ctypes.c_void_p(stream)), "lbm_field_sums_noalloc")
-    target = float(np.sum(phi0_host))
-    _ck(lib.lbm_sg_shift(_ptr(f.phi), n, (target - float(sums[0].item())) / n, stream), "lbm_sg_shift")
+    if smooth > 0:
+        tmp = torch.zeros(n, dtype=torch.float64, device="cuda")
+        _ck(lib.lbm_sg_smooth(_ptr(f.P), _ptr(tmp), 1, sg1.H, sg1.W, int(smooth), 0.2, stream), "lbm_sg_smooth")
+    f.phi.copy_(torch.from_numpy(phi0_host))
+    f.u.zero_()
     sim.init_fields(f.phi, f.u, f.P)
 
 
@@ -166,6 +183,8 @@ def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max
         d2, a2 = out.tolist()
         r = float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
         cur = nxt
+        if not np.isfinite(r):   # the run diverged: no convergence
+            break
         ok = ok + 1 if r < tol else 0
         if ok >= consecutive:
             done = steps
