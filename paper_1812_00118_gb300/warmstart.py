@@ -192,3 +192,42 @@ def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max
     e1.record()
     e1.synchronize()
     return done, e0.elapsed_time(e1), r
+
+
+def batch_steps_to_tolerance(torch, batch, tol=1e-3, check_every=100, consecutive=3, max_steps=200000):
+    """steps_to_tolerance for every grid of a Batch stepped together: the
+    batch advances until each grid has met the criterion (or max_steps);
+    returns (per-grid steps or None, device ms of the whole loop)."""
+    lib = L.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    views = [batch.grid(k) for k in range(len(batch))]
+    P = [[torch.zeros(v.N, dtype=torch.float64, device="cuda") for _ in range(2)] for v in views]
+    phi = [torch.zeros(v.N, dtype=torch.float64, device="cuda") for v in views]
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    scratch = torch.zeros(512, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k, v in enumerate(views):
+        v.macro(phi[k], P[k][0], None)
+    done = [None] * len(views)
+    ok = [0] * len(views)
+    cur, steps = 0, 0
+    while steps < max_steps and any(d is None for d in done):
+        batch.step(check_every)
+        steps += check_every
+        nxt = 1 - cur
+        for k, v in enumerate(views):
+            v.macro(phi[k], P[k][nxt], None)
+            if done[k] is not None:
+                continue
+            _ck(lib.lbm_sg_residual(_ptr(P[k][nxt]), _ptr(P[k][cur]), v.N, _ptr(out), _ptr(scratch), stream),
+                "lbm_sg_residual")
+            d2, a2 = out.tolist()
+            r = float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
+            ok[k] = ok[k] + 1 if r < tol else 0
+            if ok[k] >= consecutive:
+                done[k] = steps
+        cur = nxt
+    e1.record()
+    e1.synchronize()
+    return done, e0.elapsed_time(e1)
