@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=list(BYTES_PER_LU), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tile", type=int, default=None, help="fixed step tile (skips the autotuner)")
+    ap.add_argument("--tile", type=int, default=None, help="fixed step tile (default: the library's, tile 1)")
     ap.add_argument("--lz", type=int, default=16, help="planes per CTA chunk with --tile")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every tile and chunk length first and keep the fastest (run-to-run noise of a "
+                         "few per cent can change the pick, and with it the kernel the ncu profile describes)")
     ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt"], default="bubble128",
                     help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
                          "stepped as one batch; ttt: time-to-tolerance of D2Q9 drop relaxation for plain FP32, "
@@ -249,11 +252,12 @@ def run_ours(args):
         sim = lbm.Simulation(lbm.D3Q19, SHAPE, prm, stream=stream.cuda_stream)
         sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
                         np.ascontiguousarray(P.reshape(-1)))
-        if args.tile is None:
+        if args.autotune:
             tile, lz, tune_ms = sim.autotune(10)
         else:
-            sim.set_tile(args.tile, args.lz)
-            tile, lz = args.tile, args.lz
+            tile = 1 if args.tile is None else args.tile
+            lz = args.lz
+            sim.set_tile(tile, lz)
         sim.step(args.warmup)
         stream.synchronize()
         # --- device-timed region
