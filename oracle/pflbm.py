@@ -70,6 +70,9 @@ class Params:
     hocorr: bool = True       # Eq. 13 on/off
     collision: str = "filtered"            # "filtered" (Eq. 10) or "bgk" (Eq. 5)
     bc: Sequence[str] = (PERIODIC, PERIODIC, PERIODIC)   # per axis x, y, z
+    # velocity of the wall at each end of each walled axis, wall_u[2 a + side]
+    # (side 0: below coordinate 0, side 1: above n_a - 1); R15
+    wall_u: Sequence[Sequence[float]] = ((0.0, 0.0, 0.0),) * 6
 
     @property
     def rho_dif(self):
@@ -114,11 +117,42 @@ def value_at_offset(f, c, bc):
     return out
 
 
-def stream(fstar, lat: Lattice, bc):
+def moving_wall_terms(lat: Lattice, p: Params, s, shape):
+    """R15 (reading; the paper assigns wall velocities in its Couette flow of
+    Section 3 without writing the boundary rule): a population f*_j that
+    leaves x towards a wall moving with u_w returns reduced by the momentum
+    the wall hands over, 2 w_j s (c_j . u_w) / T, where s is the density the
+    equilibrium carries velocity with (phi for h, rho for g) at x.  Returns
+    term[j] on the grid; where x + c_j crosses two walls (a corner) u_w is the
+    mean of theirs."""
+    nz, ny, nx = shape
+    coords = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    xyz = (coords[2], coords[1], coords[0])
+    n = (nx, ny, nz)
+    term = np.zeros((lat.Q,) + tuple(shape))
+    for j in range(lat.Q):
+        c = lat.c[j]
+        usum = np.zeros((3,) + tuple(shape))
+        count = np.zeros(shape)
+        for a in range(3):
+            if c[a] == 0 or p.bc[a] != WALL:
+                continue
+            t = xyz[a] + c[a]
+            for side, hit in ((0, t < 0), (1, t >= n[a])):
+                uw = np.asarray(p.wall_u[2 * a + side], dtype=float)
+                usum += hit[None] * uw[:, None, None, None]
+                count += hit
+        cu = np.einsum("a,axyz->xyz", c.astype(float), usum) / np.maximum(count, 1)
+        term[j] = 2.0 * lat.w[j] * s * cu / T
+    return term
+
+
+def stream(fstar, lat: Lattice, bc, wall_term=None):
     """Pull streaming, the left-hand sides of Eqs. 1 and 10:
     f_i(x, t+1) = f*_i(x - c_i, t).  If x - c_i lies behind a wall the
     population that left x towards the wall returns reversed (halfway
-    bounce-back, R9): f_i(x, t+1) = f*_opp(i)(x, t)."""
+    bounce-back, R9): f_i(x, t+1) = f*_opp(i)(x, t), less wall_term[opp(i)]
+    at x for a moving wall (R15)."""
     nz, ny, nx = fstar.shape[1:]
     coords = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     xyz = (coords[2], coords[1], coords[0])
@@ -135,7 +169,8 @@ def stream(fstar, lat: Lattice, bc):
             if bc[a] == WALL:
                 src = xyz[a] - c[a]
                 blocked |= (src < 0) | (src >= fstar.shape[1 + ax])
-        out[i] = np.where(blocked, fstar[lat.opp[i]], pulled)
+        back = fstar[lat.opp[i]] if wall_term is None else fstar[lat.opp[i]] - wall_term[lat.opp[i]]
+        out[i] = np.where(blocked, back, pulled)
     return out
 
 
@@ -350,7 +385,12 @@ def collide(h, g, lat: Lattice, p: Params, m=None):
 def step(h, g, lat: Lattice, p: Params):
     """One time step: collide at every node, then pull-stream."""
     hstar, gstar = collide(h, g, lat, p)
-    return stream(hstar, lat, p.bc), stream(gstar, lat, p.bc)
+    if not any(any(v != 0.0 for v in u) for u in p.wall_u):
+        return stream(hstar, lat, p.bc), stream(gstar, lat, p.bc)
+    phi = hstar.sum(axis=0)            # Eq. 1 conserves phi through the collision
+    shape = phi.shape
+    return (stream(hstar, lat, p.bc, moving_wall_terms(lat, p, phi, shape)),
+            stream(gstar, lat, p.bc, moving_wall_terms(lat, p, density(phi, p), shape)))
 
 
 def run(h, g, lat: Lattice, p: Params, n):
