@@ -166,6 +166,18 @@ long long lbm_launch_count(const lbm_ctx* ctx);
 /* The CUDA stream of the context (as given to lbm_create). */
 void* lbm_stream(const lbm_ctx* ctx);
 
+/* Velocity u (user axes; u[2] ignored for D2Q9) of the wall at end `side`
+ * (0: below coordinate 0, 1: above n - 1) of walled user axis `axis`; all
+ * walls start at rest.  A sliding wall only: the component normal to the wall
+ * must be 0.  Halfway bounce-back less the momentum the wall hands over: a
+ * population f*_j leaving a node towards the wall returns as
+ * f*_j - 2 w_j s (c_j . u) / T, s = phi for h and rho(phi) for g at that node
+ * (the paper's Couette flow of Section 3 assigns wall velocities without
+ * writing the rule; this is the library's reading).  Takes effect at the next
+ * step.  Errors: LBM_EINVAL (bad axis or side, axis not walled, normal
+ * component, non-finite). */
+int lbm_set_wall_velocity(lbm_ctx* ctx, int axis, int side, const double u[3]);
+
 /* Step kernel configuration.  `tile` indexes the compiled step kernels of
  * the lattice:
  *   0-3   per-thread loads, grid = tile columns x chunks of `lz` planes.

@@ -650,6 +650,26 @@ long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
 
 void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
+int lbm_set_wall_velocity(lbm_ctx* c, int axis, int side, const double u[3]) {
+    if (!c || !u || side < 0 || side > 1) return LBM_EINVAL;
+    if (axis < 0 || axis >= c->dim) return LBM_EINVAL;
+    if (c->grid.bc[axis] != LBM_WALL) return LBM_EINVAL;       // only walls move
+    if (u[axis] != 0.0) return LBM_EINVAL;                      // sliding: no normal component
+    for (int d = 0; d < c->dim; ++d)
+        if (!std::isfinite(u[d])) return LBM_EINVAL;
+    const int ia = internal_axis(c, axis);
+    double ui[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < c->dim; ++d) ui[internal_axis(c, d)] = u[d];
+    for (int k = 0; k < 3; ++k) c->P.uw[ia][side][k] = ui[k];
+    int moving = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            for (int k = 0; k < 3; ++k) moving |= c->P.uw[a][sd][k] != 0.0;
+    c->P.moving = moving;
+    c->pversion += 1;
+    return LBM_OK;
+}
+
 // Step tile shape and z-chunk length (used by the tuner and the tests).
 int lbm_set_tile(lbm_ctx* c, int tile, int lz) {
     if (!c || tile < 0 || tile >= c->K->n_tiles || lz < 1 || c->owner) return LBM_EINVAL;

@@ -27,6 +27,7 @@ struct lbm_batch {
     const KernelTable* K = nullptr;
     std::vector<lbm_ctx*> views;
     std::vector<double> rho_bar_up;      // rho_bar of each grid as uploaded
+    std::vector<int> pversion_up;        // parameter version of each grid as uploaded
     long long NP = 0;                    // padded cells of all grids
     void* h[2] = {nullptr, nullptr};
     void* g[2] = {nullptr, nullptr};
@@ -99,10 +100,12 @@ int set_items(lbm_batch* b) {
 }
 
 // Grid parameters into device memory; again whenever a grid's rho_bar (set by
-// its initialisation under force_mode 1) has changed since the last upload.
+// its initialisation under force_mode 1) or its wall velocities have changed
+// since the last upload.
 int upload_cases(lbm_batch* b, bool force) {
     bool dirty = force;
-    for (int c = 0; c < b->n && !dirty; ++c) dirty = b->views[c]->P.rho_bar != b->rho_bar_up[c];
+    for (int c = 0; c < b->n && !dirty; ++c)
+        dirty = b->views[c]->P.rho_bar != b->rho_bar_up[c] || b->views[c]->pversion != b->pversion_up[c];
     if (!dirty) return LBM_OK;
     std::vector<Geom> G(b->n);
     std::vector<Phys> P(b->n);
@@ -110,6 +113,7 @@ int upload_cases(lbm_batch* b, bool force) {
         G[c] = b->views[c]->G;
         P[c] = b->views[c]->P;
         b->rho_bar_up[c] = P[c].rho_bar;
+        b->pversion_up[c] = b->views[c]->pversion;
     }
     return check(b->K->batch_upload(G.data(), P.data(), b->n, b->d_cases, b->stream));
 }
@@ -236,6 +240,7 @@ int lbm_batch_create(int n, const lbm_grid* grids, const lbm_params* params, voi
     if (!b->K->batch_step) { free_batch(b); return LBM_ENOTSUP; }
     b->NP = base;
     b->rho_bar_up.assign(n, 0.0);
+    b->pversion_up.assign(n, 0);
     const size_t bytes = b->elem * 9 * (size_t)b->NP;
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {

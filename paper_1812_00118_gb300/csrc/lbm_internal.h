@@ -115,6 +115,7 @@ struct lbm_ctx {
     double* partial = nullptr;   // scratch: reduction partials
     int n_partial_blocks = 0;
     long long launches = 0;
+    int pversion = 0;            // bumped whenever P changes after creation
     lbm_batch* owner = nullptr;  // set for the view of one grid of a batch: the
                                  // buffers and scratch belong to the batch,
                                  // which alone steps them

@@ -59,6 +59,8 @@ struct Phys {
     double rho_bar;
     double eps;            // n = grad phi / (|grad phi| + eps)
     int hocorr;            // Eq. 13 and the corrected velocity definition
+    double uw[3][2][3];    // wall velocity of each end (side 0: below 0, 1: above n - 1) of each walled axis
+    int moving;            // any wall velocity nonzero
     double h_shift;        // 16-bit storage keeps h_i - w_i h_shift
     double g_shift;        // ... and (g_i - w_i g_shift) * g_scale
     double g_scale, g_inv_scale;
@@ -72,6 +74,8 @@ struct PhysT {
     R g[3];
     R rho_bar, eps;
     R h_shift, g_shift, g_scale, g_inv_scale;
+    R uw[3][2][3];
+    int moving;
     int force_mode, hocorr;
 };
 
@@ -87,6 +91,10 @@ inline PhysT<R> phys_as(const Phys& p) {
     q.h_shift = (R)p.h_shift; q.g_shift = (R)p.g_shift;
     q.g_scale = (R)p.g_scale; q.g_inv_scale = (R)p.g_inv_scale;
     q.force_mode = p.force_mode; q.hocorr = p.hocorr;
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            for (int k = 0; k < 3; ++k) q.uw[a][sd][k] = (R)p.uw[a][sd][k];
+    q.moving = p.moving;
     return q;
 }
 
@@ -293,6 +301,39 @@ __device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, i
                                     wrap1(tz, G.NZ, G.wall[2]))] = v;
         }
     }
+}
+
+// Moving walls (halfway bounce-back less the momentum the wall hands over):
+// when x + c_J crosses a wall, the value write_dir stored for the bounce-back
+// pull of opp(J) becomes v - 2 w_J s (c_J . u_w) / T, with s the density the
+// equilibrium carries velocity with (phi for h, rho for g) at x and u_w the
+// crossed wall's velocity (the mean of two at a corner).  `store` converts to
+// the storage type.
+template <int LAT, int J, typename S, typename R, typename Store>
+__device__ __forceinline__ void moving_wall_write(S* const* arr, const Geom& G, int x, int y, int z, R v, R s,
+                                                  const PhysT<R>& p, Store store) {
+    using L = Lattice<LAT>;
+    constexpr int CX = L::cx[J], CY = L::cy[J], CZ = L::cz[J];
+    const int t[3] = {x + CX, y + CY, z + CZ};
+    const int n[3] = {G.NX, G.NY, G.NZ};
+    const int c[3] = {CX, CY, CZ};
+    R u0 = (R)0, u1 = (R)0, u2 = (R)0;
+    int cnt = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0 || !G.wall[a]) continue;
+        const int side = t[a] < 0 ? 0 : (t[a] >= n[a] ? 1 : -1);
+        if (side < 0) continue;
+        u0 += p.uw[a][side][0];
+        u1 += p.uw[a][side][1];
+        u2 += p.uw[a][side][2];
+        ++cnt;
+    }
+    if (cnt == 0) return;
+    const R cu = ((R)CX * u0 + (R)CY * u1 + (R)CZ * u2) / (R)cnt;
+    const R corr = (R)6 * (R)L::w[J] * s * cu;
+    arr[L::opp(J)][pidx(G, wrap1(t[0], G.NX, G.wall[0]), wrap1(t[1], G.NY, G.wall[1]), wrap1(t[2], G.NZ, G.wall[2]))] =
+        store(v - corr);
 }
 
 // Reciprocal: correctly rounded, through the hardware reciprocal for FP32.
@@ -657,6 +698,16 @@ __device__ __forceinline__ void collide_node(const DirPtrs<typename Storage<ST>:
                 write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.y, hsh, (R)1));
                 write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.x, gsh, p.g_scale));
                 write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.y, gsh, p.g_scale));
+                if constexpr (WALLS) {
+                    if (p.moving && nw.wall_adj) {
+                        auto sh = [&](R v) { return St::store(v, hsh, (R)1); };
+                        auto sg = [&](R v) { return St::store(v, gsh, p.g_scale); };
+                        moving_wall_write<LAT, i>(D.hout, G, x, y, z, hs.x, s.phi, p, sh);
+                        moving_wall_write<LAT, o>(D.hout, G, x, y, z, hs.y, s.phi, p, sh);
+                        moving_wall_write<LAT, i>(D.gout, G, x, y, z, gs.x, s.rho, p, sg);
+                        moving_wall_write<LAT, o>(D.gout, G, x, y, z, gs.y, s.rho, p, sg);
+                    }
+                }
             }
         });
         hsum = hsum2.x + hsum2.y;
@@ -669,6 +720,14 @@ __device__ __forceinline__ void collide_node(const DirPtrs<typename Storage<ST>:
             hsum += hs;
             write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
             write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
+            if constexpr (WALLS) {
+                if (p.moving && nw.wall_adj) {
+                    moving_wall_write<LAT, i>(D.hout, G, x, y, z, hs, s.phi, p,
+                                              [&](R v) { return St::store(v, (R)W * p.h_shift, (R)1); });
+                    moving_wall_write<LAT, i>(D.gout, G, x, y, z, gs, s.rho, p,
+                                              [&](R v) { return St::store(v, (R)W * p.g_shift, p.g_scale); });
+                }
+            }
         });
     }
     {

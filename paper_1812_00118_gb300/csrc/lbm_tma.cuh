@@ -305,6 +305,14 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
                     hsum += hs;
                     write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs, (R)W * p.h_shift, (R)1));
                     write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W * p.g_shift, p.g_scale));
+                    if constexpr (WALLS) {
+                        if (p.moving && nw.wall_adj) {
+                            moving_wall_write<LAT, i>(D.hout, G, x, y, z, hs, s.phi, p,
+                                                      [&](R v) { return St::store(v, (R)W * p.h_shift, (R)1); });
+                            moving_wall_write<LAT, i>(D.gout, G, x, y, z, gs, s.rho, p,
+                                                      [&](R v) { return St::store(v, (R)W * p.g_shift, p.g_scale); });
+                        }
+                    }
                 });
                 {
                     constexpr double W0 = L::w[0];

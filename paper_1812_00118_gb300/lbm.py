@@ -66,6 +66,7 @@ SIGNATURES = [
     ("lbm_lattice_info", ctypes.c_int, [ctypes.c_int, _IP, _IP, _DP]),
     ("lbm_launch_count", ctypes.c_longlong, [_VP]),
     ("lbm_stream", _VP, [_VP]),
+    ("lbm_set_wall_velocity", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
@@ -305,6 +306,11 @@ class Simulation:
 
     def launch_count(self):
         return load().lbm_launch_count(self._ctx)
+
+    def set_wall_velocity(self, axis, side, u):
+        """Velocity of the wall at end `side` (0 low, 1 high) of walled axis `axis`."""
+        v = (ctypes.c_double * 3)(*[float(a) for a in (list(u) + [0.0, 0.0, 0.0])[:3]])
+        _check(load().lbm_set_wall_velocity(self._ctx, int(axis), int(side), v), "lbm_set_wall_velocity")
 
     def set_tile(self, tile, lz):
         _check(load().lbm_set_tile(self._ctx, tile, lz), "lbm_set_tile")
