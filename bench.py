@@ -569,8 +569,11 @@ def run_ttt(args):
     plain_P, plain_steps = [], []
     for sd in eval_seeds:
         phi0, placed = WS.case_fields(Lsz, sd)
-        for name, store in (("plain_f32", lbm.F32), ("plain_f16s", lbm.F16S), ("plain_bf16s", lbm.BF16S)):
+        for name, store, fix in (("plain_f32", lbm.F32, 0), ("plain_f16s", lbm.F16S, 0),
+                                 ("plain_f16s_phifix", lbm.F16S, 100), ("plain_bf16s", lbm.BF16S, 0),
+                                 ("plain_bf16s_phifix", lbm.BF16S, 100)):
             sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), WS.case_params(store))
+            sim.set_phi_correction(fix)
             sim.init_fields(phi0, zeros2, zeros1)
             cap = 200000 if name == "plain_f32" else 2 * plain_steps[-1]
             st, ms, r = WS.steps_to_tolerance(torch, sim, max_steps=cap)
@@ -620,6 +623,8 @@ def run_ttt(args):
                                                 else float(max(v for v in rec["P_vs_plain"] if v is not None))),
                          "laplace_err_single_drop_cases": [v for v in rec["laplace_err"] if v is not None]}
     summary["batch_f32"]["note"] = "all 8 grids in one persistent launch per step; mean_ms = total / 8"
+    for k in ("plain_f16s_phifix", "plain_bf16s_phifix"):
+        summary[k]["note"] = "total of phi re-imposed every 100 steps (lbm_set_phi_correction)"
     summary["warm_f32"]["mean_inference_ms"] = float(np.mean(forms["warm_f32"]["inference_ms"]))
     warm = summary["warm_f32"]["mean_ms"]
     line = {

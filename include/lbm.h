@@ -166,6 +166,19 @@ long long lbm_launch_count(const lbm_ctx* ctx);
 /* The CUDA stream of the context (as given to lbm_create). */
 void* lbm_stream(const lbm_ctx* ctx);
 
+/* Re-impose the total of phi every `every` steps (0, the default: never).
+ * 16-bit population storage rounds the stored h every step, and the rounding
+ * does not sum to zero: over tens of thousands of steps the total of phi
+ * drifts (a third of it in FP16 drop relaxations).  The correction sums phi
+ * in FP64 on the GPU, compares it with the total the last lbm_init_fields
+ * or lbm_set_populations gave, and adds the difference / N to the rest
+ * population h_0 of every node (a uniform shift of phi; the paper's Eq. 1
+ * conserves phi exactly, so this only undoes storage rounding).  Four
+ * stream-ordered launches per correction, no host synchronisation.  Not for
+ * the grids of a batch.  Errors: LBM_EINVAL (every < 0, a batch grid),
+ * LBM_ENOMEM. */
+int lbm_set_phi_correction(lbm_ctx* ctx, int every);
+
 /* Velocity u (user axes; u[2] ignored for D2Q9) of the wall at end `side`
  * (0: below coordinate 0, 1: above n - 1) of walled user axis `axis`; all
  * walls start at rest.  A sliding wall only: the component normal to the wall

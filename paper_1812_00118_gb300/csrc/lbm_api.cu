@@ -199,6 +199,32 @@ __global__ void laplace_partial_kernel(const double* __restrict__ P, Geom G, dou
     }
 }
 
+// Re-imposition of the total of phi: block partials of sum a (fixed order),
+// then delta = (target - sum) / N in one thread.
+constexpr int kFixBlocks = 1024;
+
+__global__ void sum_partial_kernel(const double* __restrict__ a, long long n, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        s += a[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void phi_delta_kernel(const double* __restrict__ part, int nb, double target, long long n,
+                                 double* __restrict__ delta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *delta = (target - s) / (double)n;
+}
+
 // rho u = rho(phi) u
 __global__ void rho_times_u_kernel(const double* __restrict__ phi, const double* __restrict__ u, long long N,
                                    double rho_L, double rho_dif, double* out) {
@@ -222,6 +248,20 @@ int reduce_diag(lbm_ctx* c, double out[4]) {
     if (check_cuda(cudaGetLastError())) return LBM_ECUDA;
     if (check_cuda(cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream))) return LBM_ECUDA;
     return check_cuda(cudaStreamSynchronize(c->stream));
+}
+
+// Total of phi restored to phi_target (FP64 sums on the GPU, uniform shift of
+// the rest population); stream-ordered, no host synchronisation.
+int phi_fix(lbm_ctx* c) {
+    if (check_cuda(c->K->phi(c->h[c->cur], c->G, c->P, f_phi(c), c->stream))) return LBM_ECUDA;
+    long long nb = (c->G.N + kRedThreads - 1) / kRedThreads;
+    if (nb > kFixBlocks) nb = kFixBlocks;
+    sum_partial_kernel<<<(unsigned)nb, kRedThreads, 0, c->stream>>>(f_phi(c), c->G.N, c->d_fix);
+    phi_delta_kernel<<<1, 32, 0, c->stream>>>(c->d_fix, (int)nb, c->phi_target, c->G.N, c->d_fix + kFixBlocks);
+    if (check_cuda(cudaGetLastError())) return LBM_ECUDA;
+    if (check_cuda(c->K->shift_rest(c->h[c->cur], c->G, c->P, c->d_fix + kFixBlocks, c->stream))) return LBM_ECUDA;
+    c->launches += 4;
+    return LBM_OK;
 }
 
 int copy_field(lbm_ctx* c, double* dst, const double* src, size_t n, int on_device) {
@@ -375,6 +415,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->fields) cudaFreeAsync(c->fields, c->stream);
     if (c->d_err) cudaFreeAsync(c->d_err, c->stream);
     if (c->partial) cudaFreeAsync(c->partial, c->stream);
+    if (c->d_fix) cudaFreeAsync(c->d_fix, c->stream);
     cudaStreamSynchronize(c->stream);
     delete c;
 }
@@ -392,12 +433,14 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
     for (int d = 0; d < c->dim; ++d)
         if (check_cuda(cudaMemcpyAsync(f_u(c, internal_axis(c, d)), u + d * N, N * sizeof(double), kind, c->stream)))
             return LBM_ECUDA;
-    if (c->P.force_mode == 1) {   // rho_bar from the given phi
+    {   // total of phi (kept for the re-imposition) and rho_bar from the given phi
         double d[4];
         rc = reduce_diag(c, d);
         if (rc) return rc;
-        c->P.rho_bar = c->P.rho_L + c->P.rho_dif * d[0] / (double)N;
+        c->phi_target = d[0];
+        if (c->P.force_mode == 1) c->P.rho_bar = c->P.rho_L + c->P.rho_dif * d[0] / (double)N;
     }
+    c->phi_fix_count = 0;
     // the state is written into the current buffer (for a grid of a batch,
     // the buffer all its grids hold the state in)
     const int b = c->cur;
@@ -471,6 +514,10 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
             c->launches += 1;
         }
         c->cur = o;
+        if (c->phi_fix_every > 0 && ++c->phi_fix_count >= c->phi_fix_every) {
+            if (phi_fix(c)) return LBM_ECUDA;
+            c->phi_fix_count = 0;
+        }
     }
     return LBM_OK;
 }
@@ -546,9 +593,15 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
     c->ghosts[b] = true;
     c->launches += 1;
     if (th) { cudaFreeAsync(th, c->stream); cudaFreeAsync(tg, c->stream); }
-    if (!rc && c->P.force_mode == 1) {
+    if (!rc) {
         rc = compute_fields(c);
-        if (!rc) rc = update_rho_bar(c);
+        double d[4];
+        if (!rc) rc = reduce_diag(c, d);
+        if (!rc) {
+            c->phi_target = d[0];
+            c->phi_fix_count = 0;
+            if (c->P.force_mode == 1) c->P.rho_bar = c->P.rho_L + c->P.rho_dif * d[0] / (double)c->G.N;
+        }
     }
     int rs = check_cuda(cudaStreamSynchronize(c->stream));
     return rc ? rc : rs;
@@ -649,6 +702,22 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
 long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
 
 void* lbm_stream(const lbm_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int lbm_set_phi_correction(lbm_ctx* c, int every) {
+    if (!c || every < 0 || c->owner) return LBM_EINVAL;
+    if (every > 0) {
+        int rc = ensure_scratch(c);
+        if (rc) return rc;
+        if (!c->d_fix && cudaMallocAsync((void**)&c->d_fix, sizeof(double) * (kFixBlocks + 1), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_fix = nullptr;
+            return LBM_ENOMEM;
+        }
+    }
+    c->phi_fix_every = every;
+    c->phi_fix_count = 0;
+    return LBM_OK;
+}
 
 int lbm_set_wall_velocity(lbm_ctx* c, int axis, int side, const double u[3]) {
     if (!c || !u || side < 0 || side > 1) return LBM_EINVAL;

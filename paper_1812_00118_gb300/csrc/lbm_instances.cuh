@@ -241,6 +241,11 @@ struct Launchers {
         halo_kernel<LAT, ST><<<blocks_for(n, 256), 256, 0, s>>>(dir_ptrs<S, Q>(hout, gout, hout, gout, G.NP), G);
         return cudaGetLastError();
     }
+    static cudaError_t shift_rest(void* h, const Geom& G, const Phys& p, const double* delta, cudaStream_t s) {
+        shift_rest_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>((S*)h, G, phys_as<typename Storage<ST>::R>(p),
+                                                                         delta);
+        return cudaGetLastError();
+    }
     static cudaError_t set(void* hout, void* gout, const Geom& G, const Phys& p, const double* h,
                            const double* g, cudaStream_t s) {
         set_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>(

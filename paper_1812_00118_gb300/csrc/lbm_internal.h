@@ -63,6 +63,8 @@ struct KernelTable {
                        const double* g, cudaStream_t s);
     // periodic images of the ghost band of a freshly written buffer pair
     cudaError_t (*halo)(void* hout, void* gout, const Geom& G, cudaStream_t s);
+    // h_0 += *delta (device double) at every node of buffer h
+    cudaError_t (*shift_rest)(void* h, const Geom& G, const Phys& p, const double* delta, cudaStream_t s);
     int n_tiles;            // number of compiled step tile shapes
     int tile_tx[kMaxTiles], tile_ty[kMaxTiles];
     int tile_tma[kMaxTiles];   // 1: bulk tensor copy pipeline, 0: per-thread loads
@@ -116,6 +118,10 @@ struct lbm_ctx {
     int n_partial_blocks = 0;
     long long launches = 0;
     int pversion = 0;            // bumped whenever P changes after creation
+    int phi_fix_every = 0;       // re-impose the total of phi every k steps (0: never)
+    int phi_fix_count = 0;       // steps since the last re-imposition
+    double phi_target = 0.0;     // total of phi at the last initialisation
+    double* d_fix = nullptr;     // device scratch of the re-imposition: partials, delta
     lbm_batch* owner = nullptr;  // set for the view of one grid of a batch: the
                                  // buffers and scratch belong to the batch,
                                  // which alone steps them

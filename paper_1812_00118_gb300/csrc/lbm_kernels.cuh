@@ -1051,6 +1051,22 @@ __device__ __forceinline__ void node_coords(const Geom& G, long long n, int* x, 
     *z = (int)(n / ((long long)G.NX * G.NY));
 }
 
+// h_0 += *delta at every node (the rest population pulls from its own cell,
+// so phi of every node rises by *delta): the uniform re-imposition of the
+// total of phi after 16-bit rounding has moved it.
+template <int LAT, int ST>
+__global__ void shift_rest_kernel(typename Storage<ST>::S* __restrict__ h0, Geom G, PhysT<typename Storage<ST>::R> p,
+                                  const double* __restrict__ delta) {
+    using St = Storage<ST>;
+    using R = typename St::R;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = (int)(n % G.NX), y = (int)((n / G.NX) % G.NY), z = (int)(n / ((long long)G.NX * G.NY));
+    const int k = pidx(G, x, y, z);
+    const R sh = (R)Lattice<LAT>::w[0] * p.h_shift;
+    h0[k] = St::store(St::load(h0[k], sh, (R)1) + (R)*delta, sh, (R)1);
+}
+
 // phi = sum_i of the pulled h at every node (double output, node order).
 template <int LAT, int ST>
 __global__ void phi_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p, double* phi) {

@@ -135,7 +135,8 @@ cudaError_t batch_dispatch(const BatchArgs& a) {
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
                             Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
-                            Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo, kMaxTiles,
+                            Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo,
+                            Launchers<LBM_LAT, LBM_ST>::shift_rest, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
                             {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS};
 

@@ -67,6 +67,7 @@ SIGNATURES = [
     ("lbm_launch_count", ctypes.c_longlong, [_VP]),
     ("lbm_stream", _VP, [_VP]),
     ("lbm_set_wall_velocity", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
+    ("lbm_set_phi_correction", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
@@ -306,6 +307,10 @@ class Simulation:
 
     def launch_count(self):
         return load().lbm_launch_count(self._ctx)
+
+    def set_phi_correction(self, every):
+        """Re-impose the total of phi every `every` steps (0: never)."""
+        _check(load().lbm_set_phi_correction(self._ctx, int(every)), "lbm_set_phi_correction")
 
     def set_wall_velocity(self, axis, side, u):
         """Velocity of the wall at end `side` (0 low, 1 high) of walled axis `axis`."""
