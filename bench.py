@@ -43,6 +43,7 @@ METRIC = "D3Q19 two-population phase-field LB throughput (GLUPS), 128^3 static b
 WORKLOAD = ("D3Q19 static bubble 128^3 periodic, R=24, W=5, rho ratio 1000, nu=1e-3, sigma=1e-3, "
             "M=0.1 (lattice units), fused collide + pull-stream step")
 PROFILE = os.path.join(ROOT, "profiles", "step_d3q19_f32_128cube.md")
+BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_step_d2q9_f32_64grids.md")
 KERNEL_SOURCES = ["lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_instances.cuh", "lbm_tables.cu"]
 
 
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="fixed step tile (default: the library's, tile 1)")
     ap.add_argument("--lz", type=int, default=16, help="planes per CTA chunk with --tile")
+    ap.add_argument("--batch-grids", type=int, default=512,
+                    help="batch512: use the first N grids of the workload (profiling on a smaller device footprint)")
     ap.add_argument("--autotune", action="store_true",
                     help="time every tile and chunk length first and keep the fastest (run-to-run noise of a "
                          "few per cent can change the pick, and with it the kernel the ncu profile describes)")
@@ -74,20 +77,21 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(path=PROFILE, key="dram_bytes_per_launch"):
+    """DRAM bytes (per launch, or per lattice update with key
+    dram_bytes_per_lu) from a committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(PROFILE):
-        if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "kernel_source_sha")):
+    for line in open(path):
+        if ":" in line and line.strip().startswith((key, "kernel_source_sha")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -339,9 +343,9 @@ BATCH_WORKLOAD = ("512 independent periodic D2Q9 grids, side L uniform in [32, 5
                   "W in {3, 4, 5}, sigma = 0.01, M = 0.1; one persistent launch per step over all grids")
 
 
-def batch_inputs(lbm, store):
+def batch_inputs(lbm, store, n=512):
     from paper_1812_00118_gb300 import inputs as I
-    cases = I.batch_cases(512)
+    cases = I.batch_cases(512)[:n]
     shapes, params, fields = [], [], []
     for c in cases:
         L = c["L"]
@@ -388,7 +392,7 @@ def run_batch(args):
         dist.barrier()
     lbm.load()
     store = {"f64": lbm.F64, "f32": lbm.F32, "f16s": lbm.F16S, "bf16s": lbm.BF16S}[args.store]
-    cases, shapes, params, fields = batch_inputs(lbm, store)
+    cases, shapes, params, fields = batch_inputs(lbm, store, args.batch_grids)
     N = sum(a * b for a, b in shapes)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -396,11 +400,13 @@ def run_batch(args):
         for k, (phi, u, P) in enumerate(fields):
             b.grid(k).init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u[:2].reshape(-1)),
                                   np.ascontiguousarray(P.reshape(-1)))
-        if args.tile is None:
+        if args.autotune:
             tile, lz, _ = b.autotune(5)
         else:
-            b.set_tile(args.tile, args.lz)
-            tile, lz = args.tile, args.lz
+            # 32-wide CTAs, 16 planes: the tuner's pick on this workload
+            tile = 2 if args.tile is None else args.tile
+            lz = args.lz
+            b.set_tile(tile, lz)
         b.set_graph(10)
         b.step(args.warmup)
         stream.synchronize()
@@ -456,7 +462,9 @@ def run_batch(args):
                    "graph_steps": 10,
                    "l2": "inputs larger than L2 (%.1f GB of populations move per step)" % (alg_bytes / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "persistent batch step kernel (D2Q9)",
+                     "traffic": (None if args.store != "f32" or profiled_traffic(BATCH_PROFILE, "dram_bytes_per_lu") is None
+                                 else profiled_traffic(BATCH_PROFILE, "dram_bytes_per_lu") * N),
+                     "peak_kind": peak_kind, "kernel": "persistent batch step kernel (D2Q9)",
                      "alg_bytes_per_launch": alg_bytes, "mean_launch_ms": per_launch_ms},
         "sequential": {"value": float(N) / (seq_ms * 1e-3) / 1e9, "unit": "GLUPS", "ms_per_step": seq_ms,
                        "launches_per_step": len(shapes),

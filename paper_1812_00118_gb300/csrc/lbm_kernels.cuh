@@ -319,14 +319,16 @@ __device__ __forceinline__ void moving_wall_write(S* const* arr, const Geom& G, 
     const int c[3] = {CX, CY, CZ};
     R u0 = (R)0, u1 = (R)0, u2 = (R)0;
     int cnt = 0;
+    // selects, not a runtime index into p.uw: an indexed parameter block
+    // would be copied to local memory
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (c[a] == 0 || !G.wall[a]) continue;
-        const int side = t[a] < 0 ? 0 : (t[a] >= n[a] ? 1 : -1);
-        if (side < 0) continue;
-        u0 += p.uw[a][side][0];
-        u1 += p.uw[a][side][1];
-        u2 += p.uw[a][side][2];
+        const bool lo = t[a] < 0, hi = t[a] >= n[a];
+        if (!lo && !hi) continue;
+        u0 += hi ? p.uw[a][1][0] : p.uw[a][0][0];
+        u1 += hi ? p.uw[a][1][1] : p.uw[a][0][1];
+        u2 += hi ? p.uw[a][1][2] : p.uw[a][0][2];
         ++cnt;
     }
     if (cnt == 0) return;
