@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=list(BYTES_PER_LU), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tile", type=int, default=None, help="fixed step tile (default: the library's, tile 1)")
+    ap.add_argument("--tile", type=int, default=None, help="fixed step tile (default: the library's choice for the lattice)")
     ap.add_argument("--lz", type=int, default=16, help="planes per CTA chunk with --tile")
     ap.add_argument("--batch-grids", type=int, default=512,
                     help="batch512: use the first N grids of the workload (profiling on a smaller device footprint)")
@@ -259,9 +259,9 @@ def run_ours(args):
         if args.autotune:
             tile, lz, tune_ms = sim.autotune(10)
         else:
-            tile = 1 if args.tile is None else args.tile
-            lz = args.lz
-            sim.set_tile(tile, lz)
+            if args.tile is not None:
+                sim.set_tile(args.tile, args.lz)
+            tile, lz = sim.get_tile()[:2]
         sim.step(args.warmup)
         stream.synchronize()
         # --- device-timed region

@@ -203,12 +203,16 @@ int lbm_set_wall_velocity(lbm_ctx* ctx, int axis, int side, const double u[3]);
  *   8-11  tiles 0-3 launched as one wave: every column split into the same
  *         number of chunks, as many as the resident CTAs allow, each at
  *         least `lz` planes long.
+ *   12-13 loads issued one plane ahead as asynchronous copies into shared
+ *         memory (FP32 storage only; D3Q19: 32x4, 32x2; D2Q9: 128, 256).
+ *   14-15 tile 1 at 7 CTAs per SM (72 registers), and the same as a one-wave
+ *         launch.
  * `lz` >= 1 is the number of planes along the march axis (z in 3-D, y in
  * 2-D) as above.  Every tile computes the same arithmetic.  lbm_create picks
- * tile 1 with lz = 16; lbm_get_tile reports the current choice and its CTA
- * shape.
+ * tile 14 (D3Q19) or tile 1 (D2Q9) with lz = 16; lbm_get_tile reports the
+ * current choice and its CTA shape.
  * Errors: LBM_EINVAL for an unknown tile or lz < 1, LBM_ENOTSUP for a
- * bulk-copy tile this grid or storage type cannot use. */
+ * bulk-copy or asynchronous-copy tile this grid or storage type cannot use. */
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
 int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
 

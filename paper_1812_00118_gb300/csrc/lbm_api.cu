@@ -331,9 +331,9 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
     }
     c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
     if (!c->K || c->G.NP >= (1LL << 31)) return LBM_EINVAL;
-    // default: per-thread loads in phases, 8 CTAs per SM (the fastest tile on
-    // the measured grids; lbm_autotune picks per grid)
-    c->tile = 1;
+    // default: per-thread loads in phases (the fastest tiles on the measured
+    // grids; lbm_autotune picks per grid): D3Q19 at 7 CTAs per SM, D2Q9 at 8
+    c->tile = lattice == LBM_D2Q9 ? 1 : 14;
     return LBM_OK;
 }
 

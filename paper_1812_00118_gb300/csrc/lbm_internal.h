@@ -11,7 +11,7 @@ namespace lbm {
 
 struct TmaMaps;
 
-constexpr int kMaxTiles = 14;   // step kernel variants per (lattice, storage)
+constexpr int kMaxTiles = 16;   // step kernel variants per (lattice, storage)
 
 // Everything one step launch needs.
 struct StepArgs {

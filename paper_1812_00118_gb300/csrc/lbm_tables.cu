@@ -16,7 +16,10 @@ namespace {
 #if LBM_LAT == 1
 // D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
 // the bulk tensor copy pipeline, 8-11 are tiles 0-3 as a one-wave launch,
-// 12-13 load through cp.async ahead of use (FP32 storage only).
+// 12-13 load through cp.async ahead of use (FP32 storage only), 14-15 are
+// tile 1 and its one-wave form at 7 CTAs per SM (72 registers instead of 64:
+// a grid of up to 7 CTAs per SM runs in one wave either way, and the wider
+// budget holds the march's loop invariants).
 #define LBM_TILES(X)         \
     X(0, hoist, 32, 4, 4)    \
     X(1, split, 32, 4, 8)    \
@@ -31,7 +34,9 @@ namespace {
     X(10, splitbal, 32, 8, 4) \
     X(11, splitbal, 32, 4, 6) \
     X(12, async, 32, 4, 4)    \
-    X(13, async, 32, 2, 8)
+    X(13, async, 32, 2, 8)    \
+    X(14, split, 32, 4, 7)    \
+    X(15, splitbal, 32, 4, 7)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 #define LBM_TILES(X)           \
@@ -48,7 +53,9 @@ namespace {
     X(10, splitbal, 256, 1, 4) \
     X(11, splitbal, 64, 1, 16) \
     X(12, async, 128, 1, 8)    \
-    X(13, async, 256, 1, 4)
+    X(13, async, 256, 1, 4)    \
+    X(14, split, 128, 1, 7)    \
+    X(15, splitbal, 128, 1, 7)
 #endif
 
 #define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false>(a)

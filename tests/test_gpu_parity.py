@@ -236,17 +236,20 @@ def test_config1_static_droplet_f64(lbm):
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_tile_shapes_agree(lbm, lat_id, shape, bc):
     """Every compiled CTA shape (per-thread loads, tiles 0-3; bulk tensor
-    copies, tiles 4-7; balanced persistent launches of tiles 0-3, tiles 8-11)
-    and z-chunk length computes the same arithmetic: FP64 results agree to
-    rounding (the compiler may contract a*b+c differently per instantiation)."""
+    copies, tiles 4-7; balanced persistent launches of tiles 0-3, tiles 8-11;
+    tile 1 at 7 CTAs per SM and its one-wave form, tiles 14-15) and z-chunk
+    length computes the same arithmetic: FP64 results agree to rounding (the
+    compiler may contract a*b+c differently per instantiation)."""
     ref = None
     for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (5, 1), (6, 1), (7, 1),
-                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100), (12, 4)):
+                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100), (12, 4), (14, 16), (14, 1), (15, 3),
+                     (15, 100)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            assert e.code == lbm.ENOTSUP and 4 <= tile <= 7 or tile >= 12
+            # bulk copies (4-7) and asynchronous copies (12-13) may not apply
+            assert e.code == lbm.ENOTSUP and (4 <= tile <= 7 or tile in (12, 13)), tile
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
@@ -258,20 +261,20 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_async_tiles_agree_f32(lbm, lat_id, shape, bc):
-    """The cp.async tiles (12: every load, 13: the g loads; FP32 storage only)
-    against the per-thread-load tile 1 and the oracle: the same FP32
+    """The cp.async tiles (12-13; FP32 storage only) and the 7-CTA tiles
+    (14-15) against the per-thread-load tile 1 and the oracle: the same FP32
     arithmetic, so agreement to a few FP32 roundings after 7 steps."""
     ref, _, _, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
     ref.set_tile(1, 16)
     ref.step(7)
     hr, gr = ref.get_populations()
-    for tile, lz in ((12, 16), (12, 1), (12, 5), (13, 3), (13, 100), (13, 1)):
+    for tile, lz in ((12, 16), (12, 1), (12, 5), (13, 3), (13, 100), (13, 1), (14, 16), (14, 1), (15, 5)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, lz)
         sim.step(7)
         hg, gg = sim.get_populations()
         assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz)
-    for tile in (12, 13):
+    for tile in (12, 13, 14, 15):
         sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, 16)
         sim.step(1)

@@ -49,10 +49,15 @@ def test_correction_is_inert_without_rounding(lbm):
     f0, P0, d0 = drop_run(lbm, lbm.F64, 0, 300, n=48)
     f1, P1, d1 = drop_run(lbm, lbm.F64, 1, 300, n=48)
     assert d1 < 1e-13
-    # each shift is ~1e-17; near the drop centre |grad phi| ~ 1e-9 makes the
-    # interface normal amplify round-off (the sensitivity of Eq. 2), so the
-    # runs agree pointwise to ~1e-9, far below the 1e-4 shifts FP16 needs
-    assert np.abs(f1 - f0).max() < 1e-8
+    # each shift is ~1e-17; near the drop centre, where |grad phi| is small,
+    # the interface normal n = grad phi / (|grad phi| + eps) of Eq. 2
+    # amplifies round-off-sized changes: in the FP64 oracle itself, shifts of
+    # 1e-17 in the rest population grow to 2.4e-8 in phi there after 300
+    # steps (1.8e-9 normwise), and how far depends on the rounding of every
+    # operation.  The bounds leave that room and stay far below the 1e-4
+    # shifts FP16 needs.
+    assert np.abs(f1 - f0).max() < 1e-6
+    assert np.linalg.norm(f1 - f0) < 1e-7 * np.linalg.norm(f0)
     assert np.abs(P1 - P0).max() < 1e-6 * np.abs(P0).max()
 
 
