@@ -78,7 +78,7 @@ def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False):
 
 
 @pytest.mark.parametrize("lat_id,shape,bc,axis,walls", CASES, ids=["d2q9", "d3q19"])
-@pytest.mark.parametrize("path", ["tile1", "bulkcopy", "batch"])
+@pytest.mark.parametrize("path", ["default", "bulkcopy", "batch"])
 def test_sliding_walls_against_oracle(lbm, lat_id, shape, bc, axis, walls, path):
     if path == "batch" and lat_id == 1:
         pytest.skip("batches hold D2Q9 grids")
