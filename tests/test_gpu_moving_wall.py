@@ -3,9 +3,9 @@
 rho(phi) for g).
 
 * FP64 populations after tens of steps, D2Q9 and D3Q19, both ends of the
-  walled axis sliding with different velocities, through the per-thread-load
-  tile, a bulk-copy tile and a grid of a batch: 1e-10 normwise (operation
-  order only);
+  walled axis sliding with different velocities, through the default
+  per-thread-load tile (14 for D3Q19, 1 for D2Q9), a bulk-copy tile and a
+  grid of a batch: 1e-10 normwise (operation order only);
 * the layered Couette flow of Section 3 in FP32 against the quadrature of
   (eta u')' = 0: within 3 % of the wall speed, as the oracle;
 * argument errors."""
