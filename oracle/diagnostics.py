@@ -42,3 +42,14 @@ def effective_radius(phi, dim, drop=True):
 def totals(phi, rho):
     """Global sum of phi and of mass (conserved under periodic boundaries)."""
     return float(phi.sum()), float(rho.sum())
+
+
+def rt_fronts(phi, nx, ny):
+    """Rayleigh-Taylor fronts (Section 4) in units of the width L = nx,
+    measured from the initial interface height ny / 2: the lowest row
+    holding heavy fluid (phi > 1/2, the spike tip, negative) and the highest
+    row holding light fluid (the bubble tip, positive)."""
+    heavy = np.asarray(phi).reshape(ny, nx) > 0.5
+    spike = np.where(heavy.any(axis=1))[0].min()
+    bubble = np.where((~heavy).any(axis=1))[0].max()
+    return (spike - ny / 2) / nx, (bubble - ny / 2) / nx

@@ -130,3 +130,13 @@ def drops(L, seed, n_min=1, n_max=4, R_min=12.0, R_max=48.0, W=4.0, gap=None):
         phi += p
     phi = np.minimum(phi, 1.0)
     return phi, np.zeros((3, 1, L, L)), np.zeros((1, L, L)), placed
+
+
+def perturbed_interface(nx, ny, W, amplitude=0.1):
+    """(ny, nx) phi of a flat horizontal interface at ny / 2 with a cosine
+    perturbation of one wavelength nx and amplitude `amplitude` * nx, heavy
+    fluid (phi = 1) above: the Rayleigh-Taylor start of Section 4 (the paper
+    gives no perturbation; this one is a reading)."""
+    Y, X = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    y0 = ny / 2 + amplitude * nx * np.cos(2 * np.pi * (X + 0.5) / nx)
+    return 0.5 + 0.5 * np.tanh(2 * (Y - y0) / W)

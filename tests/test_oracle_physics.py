@@ -284,3 +284,14 @@ def test_layered_couette():
     err_w, dphi = _couette(100.0, False, "water")
     assert err_w > 0.2 and dphi < 1e-9
     assert _couette(100.0, False, "air")[0] < 0.035
+
+
+@pytest.mark.parametrize("nx,ny,W,amp", [(150, 600, 2.5, 0.1), (64, 256, 4.0, 0.2), (150, 600, 2.5, 0.0)])
+def test_rt_fronts_of_the_initial_interface(nx, ny, W, amp):
+    """The Rayleigh-Taylor front diagnostic on the unevolved start: a cosine
+    of amplitude amp L puts the spike tip amp L below and the bubble tip
+    amp L above the mean interface, to within one row (fronts are whole rows
+    where phi crosses 1/2)."""
+    s, b = D.rt_fronts(I.perturbed_interface(nx, ny, W, amplitude=amp), nx, ny)
+    assert abs(s * nx + amp * nx) <= 1.0 and abs(b * nx - amp * nx) <= 1.0
+    assert s <= b + 1.0 / nx
