@@ -40,6 +40,9 @@ R8  phi is clipped to [0, 1] inside 1/tau_mix only.
 R9  Walls: halfway bounce-back for h and g; the phi value at a ghost node
     behind a wall is the adjacent fluid node's (zero normal gradient).
 R10 Initialisation: h = h^eq, g = g^eq of the given (phi, u, P).
+R17 A buoyancy-driven start at rest takes the hydrostatic pressure,
+    grad P = F (``hydrostatic_pressure``); the paper gives no initial
+    pressure for its Rayleigh-Taylor cases.
 """
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
@@ -402,6 +405,24 @@ def run(h, g, lat: Lattice, p: Params, n):
 def mean_density(phi, p: Params):
     """rho_bar of reading R7 from the (conserved) order parameter."""
     return p.rho_L + p.rho_dif * float(phi.mean())
+
+
+def hydrostatic_pressure(phi, p: Params):
+    """Reading R17, a start at rest for buoyancy-driven cases: the pressure
+    in balance with the body force, grad P = F (force_mode 1: F = (rho -
+    rho_bar) g), integrated along the one axis g points along by the
+    trapezoid rule and shifted to zero mean.  phi is (nz, ny, nx).  With P = 0
+    instead the unbalanced force launches pressure waves; at density ratio
+    1000 they wreck the Rayleigh-Taylor case of Section 4 before t* = 0.25."""
+    comps = [a for a in range(3) if p.g[a] != 0.0]
+    if len(comps) != 1 or p.force_mode != 1:
+        raise ValueError("hydrostatic start: force_mode 1 with g along one axis")
+    a = comps[0]
+    axis = 2 - a                       # array axes are (z, y, x)
+    rho_bar = p.rho_bar if p.rho_bar is not None else mean_density(phi, p)
+    F = (density(phi, p) - rho_bar) * p.g[a]
+    P = np.cumsum(F, axis=axis) - 0.5 * F - 0.5 * np.take(F, [0], axis=axis)
+    return P - P.mean()
 
 
 def init_populations(phi, u, P, lat: Lattice, p: Params):

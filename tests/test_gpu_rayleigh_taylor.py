@@ -95,3 +95,42 @@ def test_rayleigh_taylor_fronts_f32(lbm):
     ref = np.loadtxt(GOLDEN)
     for (s, b), (ts, _, s_o, b_o) in zip(pos, ref):
         assert abs(s - s_o) <= 0.03 and abs(b - b_o) <= 0.03, (ts, s, s_o, b, b_o)
+
+
+GOLDEN_1000 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rt_ratio1000_fronts.txt")
+
+
+def test_rayleigh_taylor_ratio1000_f32(lbm):
+    """The paper's density-ratio-1000 case (256 x 1000, sigma 4.7e-1 in its
+    units = 4.7e-4 with the heavy density 1, W 5, M 1.3e-2, nu_water 4.1e-3,
+    dynamic viscosity ratio 100), started at rest in hydrostatic balance
+    (oracle reading R17; from P = 0 the pressure waves wreck the run) with
+    the 0.1 L cosine perturbation: FP32 stays finite, keeps the total of phi,
+    the fronts grow, and they agree with the FP64 oracle's
+    (tests/golden/rt_ratio1000_fronts.txt) within 0.03 L."""
+    nx, ny, ratio, W1, M1, nuw, mur = 256, 1000, 1000.0, 5.0, 1.3e-2, 4.1e-3, 100.0
+    sigma = 4.7e-1 / ratio
+    prm = lbm.make_params(M=M1, W=W1, sigma=sigma, rho_L=1.0 / ratio, rho_H=1.0, nu_L=nuw * ratio / mur, nu_H=nuw,
+                          g=(0.0, -G), force_mode=1, store=lbm.F32)
+    p = O.Params(M=M1, W=W1, sigma=sigma, rho_L=1.0 / ratio, rho_H=1.0, nu_L=nuw * ratio / mur, nu_H=nuw,
+                 g=(0.0, -G, 0.0), force_mode=1, bc=("periodic", "wall", "periodic"))
+    phi = I.perturbed_interface(nx, ny, W1)
+    P0 = O.hydrostatic_pressure(phi.reshape(1, ny, nx), p)
+    sim = lbm.Simulation(lbm.D2Q9, (nx, ny), prm, bc=(lbm.PERIODIC, lbm.WALL))
+    sim.init_fields(phi.reshape(-1).copy(), np.zeros(2 * nx * ny), np.ascontiguousarray(P0.reshape(-1)))
+    t_unit = 1.0 / np.sqrt(G / nx)
+    ref = np.loadtxt(GOLDEN_1000)
+    pos, done = [], 0
+    for ts, n, s_o, b_o in ref:
+        sim.step(int(n) - done)
+        done = int(n)
+        assert int(n) == int(round(ts * t_unit))
+        f, P, ru = sim.macro()
+        assert np.isfinite(f).all() and np.isfinite(P).all()
+        assert abs(f.sum() - phi.sum()) < 1e-5 * phi.sum()
+        s, b = D.rt_fronts(f, nx, ny)
+        pos.append((s, b))
+        assert abs(s - s_o) <= 0.03 and abs(b - b_o) <= 0.03, (ts, s, s_o, b, b_o)
+    print("ratio 1000 spike / bubble fronts (L):", pos)
+    (s1, b1), (s2, b2) = pos
+    assert s1 < -0.12 and b1 > 0.12 and s2 < s1 and b2 > b1

@@ -295,3 +295,26 @@ def test_rt_fronts_of_the_initial_interface(nx, ny, W, amp):
     s, b = D.rt_fronts(I.perturbed_interface(nx, ny, W, amplitude=amp), nx, ny)
     assert abs(s * nx + amp * nx) <= 1.0 and abs(b * nx - amp * nx) <= 1.0
     assert s <= b + 1.0 / nx
+
+
+def test_hydrostatic_start_balances_the_body_force():
+    """Reading R17: the hydrostatic start's pressure differences along g are
+    the trapezoid means of F = (rho - rho_bar) g, its mean is zero, and a
+    stable flat layering (heavy below) started from it stays at rest far
+    better than one started from P = 0 (a wrong sign or axis would not)."""
+    nx, ny, G = 8, 64, 1e-4
+    p = O.Params(M=0.05, W=4.0, sigma=1e-3, rho_L=1e-2, rho_H=1.0, nu_L=0.1, nu_H=0.02,
+                 g=(0.0, -G, 0.0), force_mode=1, bc=("periodic", "wall", "periodic"))
+    phi, _, _ = I.layers((1, ny, nx), axis=1, split=ny / 2 - 0.5, W=4.0)
+    P = O.hydrostatic_pressure(phi, p)
+    rho = p.rho_L + phi * p.rho_dif
+    F = (rho - O.mean_density(phi, p)) * (-G)
+    np.testing.assert_allclose(np.diff(P, axis=1), 0.5 * (F[:, 1:] + F[:, :-1]), rtol=0, atol=1e-15)
+    assert abs(P.mean()) < 1e-15
+    umax = {}
+    for name, P0 in (("hydrostatic", P), ("zero", np.zeros_like(P))):
+        q = O.Params(**{**p.__dict__, "rho_bar": None})
+        h, g = O.init_populations(phi, np.zeros((3,) + phi.shape), P0, L.D2Q9, q)
+        h, g = O.run(h, g, L.D2Q9, q, 200)
+        umax[name] = np.abs(O.macroscopic(h, g, L.D2Q9, q)["u"]).max()
+    assert umax["hydrostatic"] < 0.05 * umax["zero"], umax
