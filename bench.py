@@ -32,6 +32,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -62,10 +64,13 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="time every tile and chunk length first and keep the fastest (run-to-run noise of a "
                          "few per cent can change the pick, and with it the kernel the ncu profile describes)")
-    ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt"], default="bubble128",
+    ap.add_argument("--rising-ref-steps", type=int, default=2000,
+                    help="rising: FP64 reference steps at full size (errors of the other forms are taken there)")
+    ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt", "rising"], default="bubble128",
                     help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
                          "stepped as one batch; ttt: time-to-tolerance of D2Q9 drop relaxation for plain FP32, "
-                         "16-bit storage, the batch and the learned warm start")
+                         "16-bit storage, the batch and the learned warm start; rising: the 256x256x512 rising "
+                         "bubble in FP32 and 16-bit storage against an FP64 reference (--steps per form)")
     return ap.parse_args()
 
 
@@ -516,6 +521,136 @@ def run_batch_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- rising
+RISING_METRIC = "D3Q19 rising bubble throughput (GLUPS), 256x256x512, populations FP32 / FP16-shifted / BF16-shifted"
+RISING_WORKLOAD = ("air bubble R = 32 started at z = 64 in water, 256 x 256 x 512 D3Q19, walls at the z ends, "
+                   "periodic x and y, density ratio 1000, dynamic viscosity ratio 100 (nu_water 0.01, nu_air 0.1), "
+                   "gravity 1e-6 on rho - rho_bar along -z, W = 4, sigma = 5e-4, M = 0.1, u = 0, P = 0 at start")
+
+
+def rising_setup(lbm, scale, store, phi_fix):
+    """The rising-bubble case at `scale` (1: 256 x 256 x 512, R = 32, z0 = 64)."""
+    from paper_1812_00118_gb300 import inputs as I
+    nx, ny, nz = int(256 * scale), int(256 * scale), int(512 * scale)
+    R, z0 = 32.0 * scale, 64.0 * scale
+    phi, u, P = I.sphere((nz, ny, nx), ((nx - 1) / 2, (ny - 1) / 2, z0), R, 4.0, drop=False, periodic=False)
+    prm = lbm.make_params(M=0.1, W=4.0, sigma=5e-4, rho_L=1e-3, rho_H=1.0, nu_L=0.1, nu_H=0.01,
+                          g=(0.0, 0.0, -1e-6), force_mode=1, store=store, g_scale=1e3 if store == lbm.F16S else 0.0)
+    sim = lbm.Simulation(lbm.D3Q19, (nx, ny, nz), prm, bc=(lbm.PERIODIC, lbm.PERIODIC, lbm.WALL))
+    if phi_fix:
+        sim.set_phi_correction(phi_fix)
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
+                    np.ascontiguousarray(P.reshape(-1)))
+    return sim, (nx, ny, nz), prm
+
+
+def rising_fields(torch, sim, N):
+    f = torch.empty(N, dtype=torch.float64, device="cuda")
+    Pd = torch.empty_like(f)
+    ru = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    sim.macro(f, Pd, ru)
+    return f, Pd, ru
+
+
+def rising_centroid(torch, f, shape):
+    """z of the bubble's centroid: the (1 - phi)-weighted mean height."""
+    nx, ny, nz = shape
+    a = (1.0 - f).clamp(min=0.0).view(nz, ny * nx).sum(dim=1)
+    z = torch.arange(nz, dtype=torch.float64, device=f.device)
+    return float((a * z).sum() / a.sum())
+
+
+def rising_run(torch, lbm, scale, store, steps, every, ref=None, ref_at=None, phi_fix=0):
+    """Run `steps` steps; centroid every `every` steps; timed with CUDA events
+    around the step launches only.  With ref = (phi, u) of another run at
+    step ref_at, also the normwise phi and u errors there."""
+    sim, shape, prm = rising_setup(lbm, scale, store, phi_fix)
+    N = shape[0] * shape[1] * shape[2]
+    rho = lambda f: prm.rho_L + f * (prm.rho_H - prm.rho_L)
+    zs, ms, errs, fields_at = [], 0.0, None, None
+    f, _, _ = rising_fields(torch, sim, N)
+    zs.append((0, rising_centroid(torch, f, shape)))
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        if ref_at is not None and done < ref_at < done + k:
+            k = ref_at - done
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(k)
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        done += k
+        f, Pd, ru = rising_fields(torch, sim, N)
+        if done % every == 0 or done == steps:
+            zs.append((done, rising_centroid(torch, f, shape)))
+        if ref_at is not None and done == ref_at:
+            u = ru.view(3, N) / rho(f)
+            if ref is not None:
+                rf, ru_ref = ref
+                errs = {"phi": float((f - rf).abs().max() / rf.abs().max()),
+                        "u": float((u - ru_ref).abs().max() / ru_ref.abs().max())}
+            else:
+                fields_at = (f.clone(), u.clone())
+    d = sim.diagnostics(raise_on_divergence=False)
+    sim.close()
+    # rise velocity: least-squares slope of the centroid over the second half
+    pts = [(t, z) for t, z in zs if t >= steps // 2]
+    vel = None
+    if len(pts) >= 2:
+        t = np.array([p[0] for p in pts], dtype=float)
+        z = np.array([p[1] for p in pts])
+        vel = float(np.polyfit(t, z, 1)[0])
+    return {"glups": N * steps / (ms * 1e-3) / 1e9, "ms": ms, "centroid": zs, "rise_velocity": vel,
+            "errors_vs_f64": errs, "nonfinite": d["nonfinite"], "sum_phi": d["sum_phi"]}, fields_at, N
+
+
+def run_rising(args):
+    import torch
+
+    from paper_1812_00118_gb300 import build, lbm
+    torch.cuda.set_device(0)
+    build.build()
+    lbm.load()
+    peak, peak_kind = measured_peak()
+    full_steps, ref_steps, every = args.steps, args.rising_ref_steps, 1000
+    stores = (("f32", lbm.F32, 0), ("f16s", lbm.F16S, 100), ("bf16s", lbm.BF16S, 100))
+    out = {"full": {}, "half": {}}
+    clocks = ClockSampler(0)
+    time.sleep(0.3)
+    # full size: FP64 reference for ref_steps, the storage forms for full_steps
+    r64, ref, N = rising_run(torch, lbm, 1.0, lbm.F64, ref_steps, every, ref_at=ref_steps)
+    out["full"]["f64"] = r64
+    for name, st, fix in stores:
+        r, _, _ = rising_run(torch, lbm, 1.0, st, full_steps, every, ref=ref, ref_at=ref_steps, phi_fix=fix)
+        r["roofline_frac"] = BYTES_PER_LU[name] * r["glups"] / peak
+        out["full"][name] = r
+    del ref
+    # half size, every form to full length: terminal velocity against FP64
+    h64, _, Nh = rising_run(torch, lbm, 0.5, lbm.F64, full_steps, every)
+    out["half"]["f64"] = h64
+    for name, st, fix in stores:
+        r, _, _ = rising_run(torch, lbm, 0.5, st, full_steps, every, phi_fix=fix)
+        if r["rise_velocity"] is not None and h64["rise_velocity"]:
+            r["rise_velocity_error_vs_f64"] = abs(r["rise_velocity"] - h64["rise_velocity"]) / abs(h64["rise_velocity"])
+        out["half"][name] = r
+    clk = clocks.stop()
+    f32 = out["full"]["f32"]
+    line = {
+        "metric": RISING_METRIC, "value": f32["glups"], "unit": "GLUPS", "n_gpus": 1, "steps": full_steps,
+        "warmup": 0, "ms_per_step": f32["ms"] / full_steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": RISING_WORKLOAD, "nodes": N, "half_scale_nodes": Nh,
+                   "value_is": "FP32 GLUPS at full size; 16-bit forms re-impose the phi total every 100 steps",
+                   "reference": f"GPU FP64 run, {ref_steps} steps at full size and {full_steps} at half size"},
+        "roofline": {"bound": "hbm", "achieved": BYTES_PER_LU["f32"] * f32["glups"], "peak": peak, "unit": "GB/s",
+                     "frac": f32["roofline_frac"], "traffic": None, "peak_kind": peak_kind},
+        "forms": out, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- ttt
 TTT_METRIC = "D2Q9 drop relaxation time-to-tolerance (ms), 8 held-out 128^2 cases, mean"
 TTT_WORKLOAD = ("1-4 static drops in a periodic 128^2 box (radii 12-28, density ratio 1000, sigma 0.01, W 4, "
@@ -658,6 +793,15 @@ def main():
                                              "oracle is timed on the bubble128 and batch512 workloads"}), flush=True)
         else:
             run_ttt(args)
+        return
+    if args.workload == "rising":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "metric": RISING_METRIC,
+                              "unavailable": "33.5 M nodes per step: the numpy oracle needs hours per step sample "
+                                             "of this size; it is timed on the bubble128 and batch512 workloads"}),
+                  flush=True)
+        else:
+            run_rising(args)
         return
     if args.workload == "batch512":
         (run_batch_reference if args.impl == "reference" else run_batch)(args)

@@ -86,6 +86,15 @@ typedef struct {
  *   store   an lbm_store value
  *   P_ref, g_scale  shift and scale of the 16-bit storage types (ignored
  *           otherwise; g_scale = 0 means 1)
+ *   C_dtheta  constant C of the diffusion correction of Eq. 14 (Section 3):
+ *           theta of Eq. 4 becomes theta + delta theta with
+ *           delta theta = C (M/T) F |grad phi|.  The paper leaves F open and
+ *           asks only that it vanish on ordinary drops and bubbles; the
+ *           library takes F = -W^2 max(0, (2 phi - 1) lap phi), which is 0 on
+ *           the tanh interface profile and negative in a dense bubble (a dip
+ *           of phi inside the heavy phase) or a rarefied droplet (a bump
+ *           inside the light phase), where C > 0 then adds diffusion.
+ *           0 (the default) is the model of Section 2; must be finite.
  */
 typedef struct {
     double M, W, sigma, rho_L, rho_H, nu_L, nu_H;
@@ -95,6 +104,7 @@ typedef struct {
     int hocorr;
     int store;
     double P_ref, g_scale;
+    double C_dtheta;
 } lbm_params;
 
 /* Create a context: validates the grid and parameters, allocates the A/B
@@ -117,10 +127,14 @@ int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const doub
                     int on_device);
 
 /* Advance n >= 0 time steps: each step is one launch of the fused
- * collide-and-pull-stream kernel (Eqs. 1-13) and a buffer swap; the
- * bulk-copy tiles (see lbm_set_tile) add one launch of a small kernel that
- * writes the periodic images into the ghost layer of the buffer just written.
- * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails. */
+ * collide-and-pull-stream kernel (Eqs. 1-14) and a buffer swap; the
+ * bulk-copy tile (see lbm_set_tile) adds one launch of a small kernel that
+ * writes the periodic images into the ghost layer of the buffer just written,
+ * and so does a node-pair tile once after a state another tile wrote.
+ * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails,
+ * and LBM_EDIVERGED without launching anything if the last lbm_diagnostics
+ * found the state diverged (until lbm_init_fields or lbm_set_populations
+ * replace it). */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* lbm_step with CUDA events recorded on the context stream around every
@@ -216,6 +230,18 @@ int lbm_set_wall_velocity(lbm_ctx* ctx, int axis, int side, const double u[3]);
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
 int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
 
+/* Poll limit of the bounded waits of the bulk-copy step pipeline (tile 4;
+ * the other step kernels do not wait).  A wait whose copies have not landed
+ * after `polls` tries gives up: the kernel raises the context's error flag,
+ * lets the copies it has in flight land (a separate bounded wait) and
+ * returns, so the GPU context stays usable, lbm_diagnostics returns
+ * LBM_ETIMEOUT and the state of that step is invalid until the next
+ * lbm_init_fields / lbm_set_populations (which also clear the flag).
+ * Default 4194304; 0 makes every pipeline wait give up at once (a host-side
+ * way to exercise the failure path without any fault).  Errors: LBM_EINVAL
+ * (polls < 0). */
+int lbm_set_wait_limit(lbm_ctx* ctx, long long polls);
+
 /* Autotuner: times every compiled tile (those the grid supports) with lz in
  * {4, 8, 16, 32} for `steps` steps each on the current state, keeps the
  * fastest configuration, and restores the state it started from (the state
@@ -228,11 +254,10 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
 /* Field diagnostics without any allocation.  The paper has no counterpart:
  * this is a service of the library, not a step of the method.
  *
- * For callers that cannot call cudaMalloc -- code running while a stream is
- * captured into a CUDA graph with allocation forbidden, a host framework whose
- * allocator owns all device memory, a loop that must not enter the allocator
- * -- this computes the same FP64 sums as lbm_diagnostics, in a fixed order,
- * from field arrays the caller provides, and allocates nothing: its scratch
+ * For callers that cannot call cudaMalloc -- a host framework whose allocator
+ * owns all device memory, a loop that must not enter the allocator -- this
+ * computes the same FP64 sums as lbm_diagnostics, in a fixed order, from
+ * field arrays the caller provides, and allocates nothing: its scratch
  * (per-block partial sums) is a static device array of 256 KB inside the
  * library, held by every GPU that loads the library until the process exits.
  *
@@ -246,12 +271,14 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
  *   cuda_stream the stream to launch on (NULL: default stream)
  *
  * Asynchronous: out is valid once the stream reaches the call.  The first
- * call on a device looks up the scratch array's device address (with that
- * device current); make that first call before any stream capture.  Every
+ * call on a device (and the first after its context was replaced, e.g. by
+ * cudaDeviceReset) looks up the scratch array's device address with that
+ * device current; make that first call before any stream capture.  Every
  * call on a device shares the one scratch array, so calls whose launches
  * overlap on the GPU (different streams, no ordering) race: order them on
  * one stream.  Errors: LBM_EINVAL (NULL phi, P or out, n < 0 or
- * n > LBM_NOALLOC_MAX_NODES), LBM_ECUDA (launch failed). */
+ * n > LBM_NOALLOC_MAX_NODES), LBM_ECUDA (an error was pending before the
+ * call -- it is left for its owner to read -- or a launch failed). */
 #define LBM_NOALLOC_MAX_NODES 33554432
 int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
                            const double* v2, long long n, double rho_L, double rho_dif, double* out,

@@ -13,13 +13,15 @@ tables and no helpers.
 Modules
 -------
 lattice      D2Q9 / D3Q19 velocity sets and weights, lattice temperature T.
-pflbm        the per-time-step update (Eqs. 1-13) on whole fields, FP64.
+pflbm        the per-time-step update (Eqs. 1-14) on whole fields, FP64.
 diagnostics  Laplace-law measurement and global sums used by validation.
 
 Every function cites the section / equation it follows.  Readings of
 places where the paper is silent or garbled are stated at the function
 that takes them.  Parity status: every function here is pinned by
-``tests/test_oracle_*.py`` except the optional diffusion correction
-``delta_theta`` (Eq. 14), whose function F the paper leaves open:
-parity unpinned.
+``tests/test_oracle_*.py``.  The diffusion correction ``delta_theta``
+(Eq. 14) is pinned against what the mathematics fixes (it vanishes on the
+tanh profile, leaves sum_i h^eq_i = phi, enters the first moment as
+delta theta T n, and adds diffusion to a dense bubble); its function F is
+this package's reading (R18 in ``pflbm``), since the paper leaves F open.
 """

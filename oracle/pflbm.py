@@ -43,6 +43,17 @@ R10 Initialisation: h = h^eq, g = g^eq of the given (phi, u, P).
 R17 A buoyancy-driven start at rest takes the hydrostatic pressure,
     grad P = F (``hydrostatic_pressure``); the paper gives no initial
     pressure for its Rayleigh-Taylor cases.
+R18 The diffusion correction of Eq. 14 (Section 3) leaves the constant C and
+    the function F open, asking only that F vanish on "decent" drops and
+    bubbles.  Reading: F(phi, lap phi) = -W^2 max(0, (2 phi - 1) lap phi).
+    On the tanh profile phi'' = (16/W^2) phi (1 - phi) (1 - 2 phi), so
+    (2 phi - 1) phi'' <= 0 everywhere and F = 0; a dense bubble (a dip of phi
+    inside the heavy phase, phi > 1/2, lap phi > 0) or a rarefied droplet (a
+    bump inside the light phase, phi < 1/2, lap phi < 0) gives F < 0.  With
+    theta + delta theta in h^eq the interface flux becomes
+    M (1 - C F) grad phi - theta T n: for C > 0 the correction adds
+    diffusion exactly where such structures sit.  C = 0 (the default) is the
+    model of Section 2.
 """
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
@@ -76,6 +87,7 @@ class Params:
     # velocity of the wall at each end of each walled axis, wall_u[2 a + side]
     # (side 0: below coordinate 0, side 1: above n_a - 1); R15
     wall_u: Sequence[Sequence[float]] = ((0.0, 0.0, 0.0),) * 6
+    C_dtheta: float = 0.0     # constant C of the diffusion correction (Eq. 14, R18)
 
     @property
     def rho_dif(self):
@@ -236,6 +248,14 @@ def theta(phi, p: Params):
     return (p.M / T) * (1.0 - 4.0 * (phi - 0.5) ** 2) / p.W
 
 
+def delta_theta(phi, grad, lap, p: Params):
+    """Eq. 14: delta theta = C (M/T) F(phi, lap phi) |grad phi|, with F of
+    reading R18, F = -W^2 max(0, (2 phi - 1) lap phi)."""
+    F = -(p.W ** 2) * np.maximum(0.0, (2.0 * phi - 1.0) * lap)
+    mag = np.sqrt((grad ** 2).sum(axis=0))
+    return p.C_dtheta * (p.M / T) * F * mag
+
+
 def normal(grad, p: Params):
     """n = grad phi / (|grad phi| + eps) (Section 2, after Eq. 4)."""
     mag = np.sqrt((grad ** 2).sum(axis=0))
@@ -290,12 +310,15 @@ def macroscopic(h, g, lat: Lattice, p: Params):
 # --------------------------------------------------------------------------
 # equilibria and forcing
 # --------------------------------------------------------------------------
-def h_equilibrium(phi, u, grad, lat: Lattice, p: Params, G=None):
-    """Eq. 2: h^eq_i = phi Gamma_i + theta w_i (c_i . n)."""
+def h_equilibrium(phi, u, grad, lat: Lattice, p: Params, G=None, lap=None):
+    """Eq. 2: h^eq_i = phi Gamma_i + theta w_i (c_i . n), with theta corrected
+    by delta theta of Eq. 14 when C != 0 (R18; lap = lap phi is then needed)."""
     if G is None:
         G = gamma(u, lat)
     n = normal(grad, p)
     th = theta(phi, p)
+    if p.C_dtheta != 0.0:
+        th = th + delta_theta(phi, grad, lap, p)
     heq = np.empty_like(G)
     for i in range(lat.Q):
         cn = sum(lat.c[i][a] * n[a] for a in range(3))
@@ -371,7 +394,7 @@ def collide(h, g, lat: Lattice, p: Params, m=None):
         m = macroscopic(h, g, lat, p)
     G = gamma(m["u"], lat)
     # h: Eq. 1 with Eq. 2
-    heq = h_equilibrium(m["phi"], m["u"], m["grad"], lat, p, G)
+    heq = h_equilibrium(m["phi"], m["u"], m["grad"], lat, p, G, m["lap"])
     hstar = h - (h - heq) / p.tau_phi
     # g: Eqs. 6, 7, 13, then Eq. 10 (filtered) or Eq. 5 (BGK)
     K = forcing(m["u"], m["grad"], m["mu"], m["F"], lat, p, G)
@@ -436,7 +459,7 @@ def init_populations(phi, u, P, lat: Lattice, p: Params):
     mu = chemical_potential(phi, lap, p)
     F = external_force(rho, p)
     G = gamma(u, lat)
-    h = h_equilibrium(phi, u, grad, lat, p, G)
+    h = h_equilibrium(phi, u, grad, lat, p, G, lap)
     K = forcing(u, grad, mu, F, lat, p, G)
     g = g_equilibrium(rho, u, P, K, lap, lat, p, G)
     return h, g

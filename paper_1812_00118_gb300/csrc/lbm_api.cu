@@ -57,6 +57,7 @@ int derive(const lbm_params& u, int lattice, Phys* out) {
         !(u.nu_L > 0) || !(u.nu_H > 0) || !(u.eps > 0))
         return LBM_EINVAL;
     if (u.force_mode != 0 && u.force_mode != 1) return LBM_EINVAL;
+    if (!std::isfinite(u.C_dtheta)) return LBM_EINVAL;
     if (elem_size(u.store) == 0) return LBM_EINVAL;
     Phys p{};
     p.inv_tau_phi = 1.0 / (u.M / kT + 0.5);
@@ -82,17 +83,30 @@ int derive(const lbm_params& u, int lattice, Phys* out) {
     p.g_shift = shifted ? u.P_ref / kT : 0.0;
     p.g_scale = shifted && u.g_scale > 0 ? u.g_scale : 1.0;
     p.g_inv_scale = 1.0 / p.g_scale;
+    p.dtheta_coef = u.C_dtheta * (u.M / kT) * u.W * u.W;   // Eq. 14, F of the header
     *out = p;
     return LBM_OK;
 }
 
 int ensure_scratch(lbm_ctx* c) {
-    if (c->fields) return LBM_OK;
-    cudaError_t e = cudaMallocAsync((void**)&c->fields, sizeof(double) * 5 * (size_t)c->G.N, c->stream);
-    if (e != cudaSuccess) { c->fields = nullptr; return LBM_ENOMEM; }
+    if (c->fields && c->partial) return LBM_OK;
+    if (!c->fields) {
+        cudaError_t e = cudaMallocAsync((void**)&c->fields, sizeof(double) * 5 * (size_t)c->G.N, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->fields = nullptr;
+            return LBM_ENOMEM;
+        }
+    }
     c->n_partial_blocks = 1024;
-    e = cudaMallocAsync((void**)&c->partial, sizeof(double) * 8 * c->n_partial_blocks, c->stream);
-    if (e != cudaSuccess) { c->partial = nullptr; return LBM_ENOMEM; }
+    cudaError_t e = cudaMallocAsync((void**)&c->partial, sizeof(double) * 8 * c->n_partial_blocks, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(c->fields, c->stream);
+        c->fields = nullptr;
+        c->partial = nullptr;
+        return LBM_ENOMEM;
+    }
     return LBM_OK;
 }
 
@@ -333,7 +347,7 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
     if (!c->K || c->G.NP >= (1LL << 31)) return LBM_EINVAL;
     // default: per-thread loads in phases (the fastest tiles on the measured
     // grids; lbm_autotune picks per grid): D3Q19 at 7 CTAs per SM, D2Q9 at 8
-    c->tile = lattice == LBM_D2Q9 ? 1 : 14;
+    c->tile = lattice == LBM_D2Q9 ? 1 : 8;
     return LBM_OK;
 }
 
@@ -384,7 +398,8 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
     int rc = ctx_setup(c, grid, lattice, params, cuda_stream);
     if (rc) { delete c; return rc; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
-    const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
+    // the node-pair kernels read (never use) up to a warp strip past the last row
+    const size_t bytes = c->elem * ((size_t)Q * (size_t)c->G.NP + kPairTail);
     for (int b = 0; b < 2; ++b) {
         if (cudaMallocAsync(&c->h[b], bytes, c->stream) != cudaSuccess ||
             cudaMallocAsync(&c->g[b], bytes, c->stream) != cudaSuccess) {
@@ -447,7 +462,9 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
     if (check_cuda(c->K->init(c->h[b], c->g[b], c->G, c->P, f_phi(c), f_u(c, 0), f_u(c, 1), f_u(c, 2), f_P(c),
                               c->stream)))
         return LBM_ECUDA;
-    c->ghosts[b] = true;   // the initialisation writes the periodic images too
+    c->ghosts[b] = c->xghosts[b] = true;   // the initialisation writes the periodic images too
+    c->diverged = false;
+    if (check_cuda(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream))) return LBM_ECUDA;
     c->launches += 1;
     return check_cuda(cudaStreamSynchronize(c->stream));
 }
@@ -479,7 +496,9 @@ int lbm_step_profiled(lbm_ctx* c, int n, double* kernel_ms) {
 
 static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
     if (!c || n < 0 || c->owner) return LBM_EINVAL;
+    if (c->diverged) return LBM_EDIVERGED;
     const bool tma = c->K->tile_tma[c->tile] != 0;
+    const bool pair = c->K->tile_pair[c->tile] != 0;
     if (tma && c->maps_tile != c->tile) {
         for (int b = 0; b < 2; ++b)
             if (check_cuda(c->K->make_maps(c->tile, &c->maps[b], c->h[b], c->g[b], c->G))) return LBM_ECUDA;
@@ -492,15 +511,18 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
     a.lz = c->lz;
     a.stream = c->stream;
     a.error_flag = c->d_err;
+    a.wait_polls = c->wait_polls;
     for (int s = 0; s < n; ++s) {
         const int i = c->cur, o = 1 - c->cur;
         a.hin = c->h[i]; a.gin = c->g[i]; a.hout = c->h[o]; a.gout = c->g[o];
         a.maps = &c->maps[i];
         // bulk-copy tiles read the ghost band unwrapped: it must hold the
         // periodic images (per-thread-load tiles wrap their pulls instead)
-        if (tma && !c->ghosts[i]) {
+        // the node-pair tiles pull x from the ghost columns: after a state
+        // written by a one-node tile they need the periodic images first
+        if ((tma && !c->ghosts[i]) || (pair && !c->ghosts[i] && !c->xghosts[i])) {
             if (check_cuda(c->K->halo(c->h[i], c->g[i], c->G, c->stream))) return LBM_ECUDA;
-            c->ghosts[i] = true;
+            c->ghosts[i] = c->xghosts[i] = true;
             c->launches += 1;
         }
         if (ev) cudaEventRecord(ev[2 * s], c->stream);
@@ -508,9 +530,10 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
         if (ev) cudaEventRecord(ev[2 * s + 1], c->stream);
         c->launches += 1;
         c->ghosts[o] = false;
+        c->xghosts[o] = pair;   // a pair step writes the x images it pulls next
         if (tma) {
             if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
-            c->ghosts[o] = true;
+            c->ghosts[o] = c->xghosts[o] = true;
             c->launches += 1;
         }
         c->cur = o;
@@ -590,7 +613,9 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
     }
     const int b = c->cur;
     int rc = check_cuda(c->K->set(c->h[b], c->g[b], c->G, c->P, dh, dg, c->stream));
-    c->ghosts[b] = true;
+    c->ghosts[b] = c->xghosts[b] = true;
+    c->diverged = false;
+    if (!rc) rc = check_cuda(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->launches += 1;
     if (th) { cudaFreeAsync(th, c->stream); cudaFreeAsync(tg, c->stream); }
     if (!rc) {
@@ -616,7 +641,12 @@ int lbm_diagnostics(lbm_ctx* c, double out[4]) {
     int err = 0;
     if (check_cuda(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost))) return LBM_ECUDA;
     if (err) return LBM_ETIMEOUT;
-    if (out[3] > 0 || out[2] > 0.3) return LBM_EDIVERGED;
+    if (out[3] > 0 || out[2] > 0.3) {
+        // sticky: lbm_step refuses to advance a diverged state until it is
+        // replaced (lbm_init_fields, lbm_set_populations)
+        c->diverged = true;
+        return LBM_EDIVERGED;
+    }
     return LBM_OK;
 }
 
@@ -653,7 +683,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         cudaFreeAsync(save_h, c->stream);
         return LBM_ENOMEM;
     }
-    const bool saved_ghosts = c->ghosts[c->cur];
+    const bool saved_ghosts = c->ghosts[c->cur], saved_xghosts = c->xghosts[c->cur];
     int rc = check_cuda(cudaMemcpyAsync(save_h, c->h[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     if (!rc) rc = check_cuda(cudaMemcpyAsync(save_g, c->g[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t e0, e1;
@@ -686,7 +716,8 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         if (!rc) rc = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
         c->cur = 0;
         c->ghosts[0] = saved_ghosts;
-        c->ghosts[1] = false;
+        c->xghosts[0] = saved_xghosts;
+        c->ghosts[1] = c->xghosts[1] = false;
     }
     cudaFreeAsync(save_h, c->stream);
     cudaFreeAsync(save_g, c->stream);
@@ -736,6 +767,12 @@ int lbm_set_wall_velocity(lbm_ctx* c, int axis, int side, const double u[3]) {
             for (int k = 0; k < 3; ++k) moving |= c->P.uw[a][sd][k] != 0.0;
     c->P.moving = moving;
     c->pversion += 1;
+    return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_ctx* c, long long polls) {
+    if (!c || polls < 0) return LBM_EINVAL;
+    c->wait_polls = (long)polls;
     return LBM_OK;
 }
 

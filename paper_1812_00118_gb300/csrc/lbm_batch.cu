@@ -241,7 +241,8 @@ int lbm_batch_create(int n, const lbm_grid* grids, const lbm_params* params, voi
     b->NP = base;
     b->rho_bar_up.assign(n, 0.0);
     b->pversion_up.assign(n, 0);
-    const size_t bytes = b->elem * 9 * (size_t)b->NP;
+    // tail: the node-pair kernels read (never use) up to a warp strip past the last row
+    const size_t bytes = b->elem * (9 * (size_t)b->NP + kPairTail);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
         ok = cudaMallocAsync(&b->h[k], bytes, b->stream) == cudaSuccess &&
@@ -315,6 +316,7 @@ int lbm_batch_step_sequential(lbm_batch* b, int n) {
             a.stream = b->stream;
             a.maps = nullptr;
             a.error_flag = b->d_err;
+            a.wait_polls = 1L << 22;
             rc = check(b->K->step(a));
             b->launches += 1;
         }

@@ -1,15 +1,54 @@
-// Kernel launchers for one lattice, all storage types.  Included by exactly
-// one translation unit per lattice (lbm_d2q9.cu, lbm_d3q19.cu) so that the
-// two lattices compile in parallel.
+// Kernel launchers of one (lattice, storage) pair.  Included by
+// lbm_tables.cu, which the build compiles once per pair (LBM_LAT, LBM_ST) so
+// that the eight pairs compile in parallel.
 #pragma once
 #include <cudaTypedefs.h>
 
 #include <new>
 
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
+
+// Values a launcher computes once per device and kernel variant (resident
+// CTAs, function attributes): kept per device ordinal, since two devices of
+// one process may differ.  Slot value 0 means "not computed yet".
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+    int v[kMaxDevices][2] = {};
+};
+
+template <typename F>
+cudaError_t per_device(PerDevice& cache, int variant, F compute, int* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return compute(out);
+    int& c = cache.v[dev][variant];
+    if (c == 0) {
+        int val = 0;
+        e = compute(&val);
+        if (e != cudaSuccess) return e;
+        c = val + 1;
+    }
+    *out = c - 1;
+    return cudaSuccess;
+}
+
+// Resident-slot count of a kernel on the current device: SMs x occupancy.
+template <typename K>
+cudaError_t resident_slots(K kern, int threads, size_t smem, int* out) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    *out = sms * occ;
+    return cudaSuccess;
+}
 
 // Grid = tile columns x chunks along z.  Chunks of lz planes, or with BAL
 // (one-wave launch) as many equal chunks as the resident slots (occupancy x
@@ -25,17 +64,11 @@ cudaError_t launch_step_tile(const StepArgs& a) {
     dim3 block(TX, TY);
     dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
     if (BAL) {
-        static int slots_v[2] = {-1, -1};
-        int& slots = slots_v[walls ? 1 : 0];
-        if (slots < 0) {
-            int dev = 0, sms = 0, occ = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX * TY, 0);
-            if (e != cudaSuccess) return e;
-            if (occ < 1) return cudaErrorInvalidConfiguration;
-            slots = sms * occ;
-        }
+        static PerDevice slots_cache;
+        int slots = 0;
+        cudaError_t e = per_device(slots_cache, walls ? 1 : 0,
+                                   [&](int* v) { return resident_slots(kern, TX * TY, 0, v); }, &slots);
+        if (e != cudaSuccess) return e;
         long long nzc = slots / ((long long)grid.x * grid.y);
         const long long by_lz = (G.NZ + a.lz - 1) / a.lz;
         if (nzc > by_lz) nzc = by_lz;
@@ -66,12 +99,13 @@ cudaError_t launch_async_tile(const StepArgs& a) {
         const bool walls = G.wall[0] || G.wall[1] || G.wall[2];
         auto kern = walls ? step_async_kernel<LAT, TX, TY, MINB, true> : step_async_kernel<LAT, TX, TY, MINB, false>;
         constexpr size_t bytes = async_smem_bytes<LAT, TX, TY>();
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[walls ? 1 : 0]) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-            if (e != cudaSuccess) return e;
-            attr_set[walls ? 1 : 0] = true;
-        }
+        static PerDevice attr_cache;
+        int done = 0;
+        cudaError_t e = per_device(attr_cache, walls ? 1 : 0, [&](int* v) {
+            *v = 1;
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        }, &done);
+        if (e != cudaSuccess) return e;
         dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
         kern<<<grid, dim3(TX, TY), bytes, a.stream>>>(dir_ptrs<float, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP),
                                                       G, phys_as<float>(a.p), a.lz);
@@ -87,16 +121,10 @@ cudaError_t launch_batch_tile(const BatchArgs& a) {
     using S = typename Storage<ST>::S;
     using R = typename Storage<ST>::R;
     auto kern = batch_step_kernel<LAT, ST, TX, MINB, HOIST>;
-    static int slots = -1;
-    if (slots < 0) {
-        int dev = 0, sms = 0, occ = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
-        slots = sms * occ;
-    }
+    static PerDevice slots_cache;
+    int slots = 0;
+    cudaError_t e = per_device(slots_cache, 0, [&](int* v) { return resident_slots(kern, TX, 0, v); }, &slots);
+    if (e != cudaSuccess) return e;
     if (a.n_items < 1) return cudaSuccess;
     const int nb = a.n_items < slots ? a.n_items : slots;
     kern<<<nb, TX, 0, a.stream>>>(dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, a.NP),
@@ -178,29 +206,58 @@ cudaError_t launch_tma_tile(const StepArgs& a) {
     using C = TmaCfg<LAT, ST, TX, TY>;
     const bool walls = a.G.wall[0] || a.G.wall[1] || a.G.wall[2];
     auto kern = walls ? step_tma_kernel<LAT, ST, TX, TY, MINB, true> : step_tma_kernel<LAT, ST, TX, TY, MINB, false>;
-    static int grid_per_sm_v[2] = {-1, -1};
-    static int num_sms = 0;
-    int& grid_per_sm = grid_per_sm_v[walls ? 1 : 0];
-    if (grid_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX * TY, C::smem_bytes);
-        if (e != cudaSuccess || occ < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
-        grid_per_sm = occ;
-    }
+    static PerDevice slots_cache;
+    int slots = 0;
+    cudaError_t e = per_device(slots_cache, walls ? 1 : 0, [&](int* v) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+        return r != cudaSuccess ? r : resident_slots(kern, TX * TY, C::smem_bytes, v);
+    }, &slots);
+    if (e != cudaSuccess) return e;
     const Geom& G = a.G;
     const int chunk = a.lz > 0 ? a.lz : 8;
     const long long work = (long long)((G.NX + TX - 1) / TX) * ((G.NY + TY - 1) / TY) * ((G.NZ + chunk - 1) / chunk);
-    long long grid = (long long)num_sms * grid_per_sm;
+    long long grid = slots;
     if (grid > work) grid = work;
     kern<<<(unsigned)grid, dim3(TX, TY), C::smem_bytes, a.stream>>>(
         *a.maps, dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP), G,
-        phys_as<typename Storage<ST>::R>(a.p), chunk, a.error_flag);
+        phys_as<typename Storage<ST>::R>(a.p), chunk, a.error_flag, a.wait_polls);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- node-pair tiles (FP32 arithmetic)
+template <int LAT, int ST, int TX, int TY>
+bool pair_tile_ok(const Geom&) {
+    return ST != ST_F64 && sizeof(PairSmem<LAT, ST, TX, TY>) <= 227 * 1024;
+}
+
+template <int LAT, int ST, int TX, int TY, int MINB, bool GFIRST, bool SRING, bool HG>
+cudaError_t launch_pair_tile(const StepArgs& a) {
+    if constexpr (ST == ST_F64) {
+        return cudaErrorNotSupported;
+    } else {
+        using S = typename Storage<ST>::S;
+        const Geom& G = a.G;
+        const bool walls = G.wall[0] || G.wall[1] || G.wall[2];
+        auto kern = walls ? step_pair_kernel<LAT, ST, TX, TY, MINB, true, GFIRST, SRING, HG>
+                          : step_pair_kernel<LAT, ST, TX, TY, MINB, false, GFIRST, SRING, HG>;
+        constexpr size_t bytes = sizeof(PairSmem<LAT, ST, TX, TY>);
+        static PerDevice attr_cache;
+        int done = 0;
+        cudaError_t e = per_device(attr_cache, walls ? 1 : 0, [&](int* v) {
+            *v = 1;
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            // MINB CTAs of `bytes` each must fit the shared-memory carveout
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+            return r;
+        }, &done);
+        if (e != cudaSuccess) return e;
+        dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
+        kern<<<grid, TX / 2 * TY, bytes, a.stream>>>(dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP),
+                                                     G, phys_as<float>(a.p), a.lz);
+        return cudaGetLastError();
+    }
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }

@@ -25,6 +25,7 @@ struct StepArgs {
     cudaStream_t stream;
     const TmaMaps* maps;   // tensor maps of (hin, gin) for a bulk-copy tile
     int* error_flag;       // raised by a bounded wait that gave up
+    long wait_polls;       // polls of a bulk-copy pipeline wait before it gives up
 };
 
 // Everything one batch step launch needs (see batch_step_kernel).
@@ -68,6 +69,7 @@ struct KernelTable {
     int n_tiles;            // number of compiled step tile shapes
     int tile_tx[kMaxTiles], tile_ty[kMaxTiles];
     int tile_tma[kMaxTiles];   // 1: bulk tensor copy pipeline, 0: per-thread loads
+    int tile_pair[kMaxTiles];  // 1: node-pair kernel (pulls x from the ghost columns)
     // batches of grids (D2Q9; null and 0 for D3Q19)
     cudaError_t (*batch_step)(const BatchArgs& a);
     // BatchCase<R> of n grids from their geometries and parameters into d_cases
@@ -112,7 +114,11 @@ struct lbm_ctx {
     lbm::TmaMaps maps[2];  // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
     int maps_tile = -1;    // tile the maps were made for
     bool ghosts[2] = {false, false};   // ghost band of buffer b holds the periodic images
+    bool xghosts[2] = {false, false};  // ghost columns x = -1, NX of buffer b hold what the
+                                       // node-pair kernel pulls (x images, unwrapped wall ghosts)
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
+    bool diverged = false; // the last lbm_diagnostics found the state diverged
+    long wait_polls = 1L << 22;   // bulk-copy pipeline wait limit (lbm_set_wait_limit)
     double* fields = nullptr;    // scratch: phi, P, ux, uy, uz (5 N doubles)
     double* partial = nullptr;   // scratch: reduction partials
     int n_partial_blocks = 0;

@@ -31,6 +31,10 @@ namespace lbm {
 
 // ---------------------------------------------------------------- geometry
 constexpr int kRep = 2;   // periodic replication depth in x and y
+// Elements allocated after the last population array of a buffer: a warp
+// strip of the node-pair kernels (lbm_pair.cuh) that overhangs the last row
+// of a grid reads, but never uses, up to one strip width past the row end.
+constexpr int kPairTail = 1024;
 
 struct Geom {
     int NX, NY, NZ;   // nodes (internal axes)
@@ -64,6 +68,7 @@ struct Phys {
     double h_shift;        // 16-bit storage keeps h_i - w_i h_shift
     double g_shift;        // ... and (g_i - w_i g_shift) * g_scale
     double g_scale, g_inv_scale;
+    double dtheta_coef;    // C (M/T) W^2 of the diffusion correction (Eq. 14), 0: off
 };
 
 // The same parameters in the arithmetic type of a kernel, converted once on
@@ -75,6 +80,7 @@ struct PhysT {
     R rho_bar, eps;
     R h_shift, g_shift, g_scale, g_inv_scale;
     R uw[3][2][3];
+    R dtheta_coef;
     int moving;
     int force_mode, hocorr;
 };
@@ -95,6 +101,7 @@ inline PhysT<R> phys_as(const Phys& p) {
         for (int sd = 0; sd < 2; ++sd)
             for (int k = 0; k < 3; ++k) q.uw[a][sd][k] = (R)p.uw[a][sd][k];
     q.moving = p.moving;
+    q.dtheta_coef = (R)p.dtheta_coef;
     return q;
 }
 
@@ -478,6 +485,13 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     s.nz = s.gz * inv;
     const R d = s.phi - (R)0.5;
     s.theta = (R)p.theta_coef * ((R)1 - (R)4 * d * d);
+    // diffusion correction of Eq. 14: delta theta = C (M/T) F |grad phi| with
+    // F = -W^2 max(0, (2 phi - 1) lap phi), zero on the tanh profile (dtheta_coef
+    // = C (M/T) W^2; 0 leaves theta untouched)
+    if (p.dtheta_coef != (R)0) {
+        const R t = ((R)2 * s.phi - (R)1) * s.lap;
+        s.theta -= (R)p.dtheta_coef * (t > (R)0 ? t : (R)0) * gmag;
+    }
 }
 
 // Post-collision g*_i (Eq. 10 with G^eq = g^eq + K, Eqs. 6, 7, 11, 13):
@@ -1242,6 +1256,10 @@ __global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
     s.nx = s.gx / (gmag + p.eps); s.ny = s.gy / (gmag + p.eps); s.nz = s.gz / (gmag + p.eps);
     const double d = s.phi - 0.5;
     s.theta = p.theta_coef * (1 - 4 * d * d);
+    if (p.dtheta_coef != 0.0) {   // Eq. 14, as in node_state
+        const double t = (2 * s.phi - 1) * s.lap;
+        s.theta -= p.dtheta_coef * (t > 0 ? t : 0.0) * gmag;
+    }
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];

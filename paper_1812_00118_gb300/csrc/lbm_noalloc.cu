@@ -4,10 +4,9 @@
 // a fixed order, then one block sums the partials in a fixed order), but its
 // scratch -- the per-block partials -- lives in a file-scope device array
 // instead of memory obtained from cudaMalloc.  It serves callers that must
-// not allocate device memory: code running while a CUDA stream is being
-// captured into a graph with allocation forbidden, a host framework whose
-// allocator owns all device memory, or a real-time loop that may not touch
-// the allocator.
+// not allocate device memory: a host framework whose allocator owns all
+// device memory, or a real-time loop that may not touch the allocator.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -79,10 +78,29 @@ __global__ void finish_kernel(const double* __restrict__ part, int nb, double* _
     out[k] = r;
 }
 
-// Device address of g_partials, looked up once per device (host code may not
-// use the symbol's name as a device pointer).
+// Device address of g_partials, looked up at set-up once per device and
+// context (host code may not use the symbol's name as a device pointer).  The
+// context is part of the key: after cudaDeviceReset the device gets a new
+// context, and the array a new address.
 constexpr int kMaxDevices = 64;
-double* g_addr[kMaxDevices] = {nullptr};
+struct Scratch {
+    CUcontext ctx = nullptr;
+    double* addr = nullptr;
+};
+Scratch g_scratch[kMaxDevices];
+
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+CtxGetCurrent ctx_get_current() {
+    static CtxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrent)f;
+    }
+    return fn;
+}
 
 }  // namespace
 
@@ -91,18 +109,29 @@ extern "C" int lbm_field_sums_noalloc(const double* phi, const double* P, const 
                                       void* cuda_stream) {
     if (!phi || !P || !out || n < 0) return LBM_EINVAL;
     if (n > (long long)LBM_NOALLOC_MAX_NODES) return LBM_EINVAL;
+    // an error left by earlier, unrelated work is reported, not cleared
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
-    if (!g_addr[dev]) {
+    // set-up: look the array up on the first call on this device, and again
+    // whenever the current context is not the one of the last lookup (the
+    // lookup also creates the device's primary context if none is current)
+    CtxGetCurrent get = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    Scratch& sc = g_scratch[dev];
+    if (!sc.addr || !ctx || sc.ctx != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess) return LBM_ECUDA;
-        g_addr[dev] = (double*)p;
+        if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+        sc.addr = (double*)p;
+        sc.ctx = ctx;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nb = (int)((n + kChunk - 1) / kChunk);
     if (nb > 0)
-        partial_kernel<<<nb, kThreads, 0, s>>>(phi, P, v0, v1, v2, n, rho_L, rho_dif, g_addr[dev]);
+        partial_kernel<<<nb, kThreads, 0, s>>>(phi, P, v0, v1, v2, n, rho_L, rho_dif, sc.addr);
     // every partial the finish reads was written above: nothing to clear first
-    finish_kernel<<<1, 32, 0, s>>>(g_addr[dev], nb, out);
+    finish_kernel<<<1, 32, 0, s>>>(sc.addr, nb, out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

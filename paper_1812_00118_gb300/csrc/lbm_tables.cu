@@ -14,29 +14,29 @@ namespace lbm {
 namespace {
 
 #if LBM_LAT == 1
-// D3Q19: CTA shapes in the x-y plane.  Tiles 0-3 use per-thread loads, 4-7
-// the bulk tensor copy pipeline, 8-11 are tiles 0-3 as a one-wave launch,
-// 12-13 load through cp.async ahead of use (FP32 storage only), 14-15 are
-// tile 1 and its one-wave form at 7 CTAs per SM (72 registers instead of 64:
-// a grid of up to 7 CTAs per SM runs in one wave either way, and the wider
-// budget holds the march's loop invariants).
+// D3Q19: CTA shapes in the x-y plane (nodes).  Tiles 0-3 use per-thread
+// loads, 4 the bulk tensor copy pipeline, 5-6 are tiles 0-1 as a one-wave
+// launch, 7 loads through cp.async ahead of use (FP32 storage only), 8-9 are
+// tile 1 and its one-wave form at 7 CTAs per SM (72 registers instead of 64),
+// 10-13 the node-pair kernel (two nodes per thread, paired FP32 arithmetic;
+// FP32 and 16-bit storage), 64 nodes per warp along x.
 #define LBM_TILES(X)         \
     X(0, hoist, 32, 4, 4)    \
     X(1, split, 32, 4, 8)    \
     X(2, split, 32, 8, 4)    \
     X(3, split, 32, 4, 6)    \
     X(4, tma, 32, 4, 2)      \
-    X(5, tma, 32, 8, 1)      \
-    X(6, tma, 64, 4, 1)      \
-    X(7, tma, 32, 2, 3)      \
-    X(8, hoistbal, 32, 4, 4) \
-    X(9, splitbal, 32, 4, 8) \
-    X(10, splitbal, 32, 8, 4) \
-    X(11, splitbal, 32, 4, 6) \
-    X(12, async, 32, 4, 4)    \
-    X(13, async, 32, 2, 8)    \
-    X(14, split, 32, 4, 7)    \
-    X(15, splitbal, 32, 4, 7)
+    X(5, hoistbal, 32, 4, 4) \
+    X(6, splitbal, 32, 4, 8) \
+    X(7, async, 32, 4, 4)    \
+    X(8, split, 32, 4, 7)    \
+    X(9, splitbal, 32, 4, 7) \
+    X(10, pair, 64, 4, 4)    \
+    X(11, pairg, 64, 4, 4)   \
+    X(12, pairs, 64, 8, 2)   \
+    X(13, pairgs, 64, 8, 2)  \
+    X(14, pair, 64, 4, 5)    \
+    X(15, pairh, 64, 4, 4)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 #define LBM_TILES(X)           \
@@ -45,17 +45,17 @@ namespace {
     X(2, split, 256, 1, 4)     \
     X(3, split, 64, 1, 16)     \
     X(4, tma, 128, 1, 2)       \
-    X(5, tma, 64, 1, 4)        \
-    X(6, tma, 192, 1, 1)       \
-    X(7, tma, 32, 1, 6)        \
-    X(8, hoistbal, 128, 1, 4)  \
-    X(9, splitbal, 128, 1, 8)  \
-    X(10, splitbal, 256, 1, 4) \
-    X(11, splitbal, 64, 1, 16) \
-    X(12, async, 128, 1, 8)    \
-    X(13, async, 256, 1, 4)    \
-    X(14, split, 128, 1, 7)    \
-    X(15, splitbal, 128, 1, 7)
+    X(5, hoistbal, 128, 1, 4)  \
+    X(6, splitbal, 128, 1, 8)  \
+    X(7, async, 128, 1, 8)     \
+    X(8, split, 128, 1, 7)     \
+    X(9, splitbal, 128, 1, 7)  \
+    X(10, pair, 128, 1, 8)     \
+    X(11, pairg, 128, 1, 8)    \
+    X(12, pairs, 256, 1, 4)    \
+    X(13, pairgs, 256, 1, 4)   \
+    X(14, pair, 128, 1, 10)    \
+    X(15, pairh, 128, 1, 8)
 #endif
 
 #define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false>(a)
@@ -64,6 +64,11 @@ namespace {
 #define LBM_LAUNCH_splitbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true>(a)
 #define LBM_LAUNCH_async(TX, TY, MB) launch_async_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
+#define LBM_LAUNCH_pair(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false, false>(a)
+#define LBM_LAUNCH_pairg(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false, false>(a)
+#define LBM_LAUNCH_pairs(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true, false>(a)
+#define LBM_LAUNCH_pairgs(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, true, false>(a)
+#define LBM_LAUNCH_pairh(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false, true>(a)
 #define LBM_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
 
@@ -80,6 +85,11 @@ cudaError_t step_dispatch(const StepArgs& a) {
 #define LBM_MAPS_splitbal(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_async(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
+#define LBM_MAPS_pair(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_pairg(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_pairs(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_pairgs(TX, TY) cudaErrorInvalidValue
+#define LBM_MAPS_pairh(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_MAPS_##KIND(TX, TY);
 
@@ -96,6 +106,11 @@ cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, 
 #define LBM_OK_splitbal(TX, TY) true
 #define LBM_OK_async(TX, TY) async_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_pair(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_pairg(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_pairs(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_pairgs(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
+#define LBM_OK_pairh(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_OK_##KIND(TX, TY);
 
@@ -137,7 +152,24 @@ cudaError_t batch_dispatch(const BatchArgs& a) {
 #define LBM_ISTMA_splitbal 0
 #define LBM_ISTMA_async 0
 #define LBM_ISTMA_tma 1
+#define LBM_ISTMA_pair 0
+#define LBM_ISTMA_pairg 0
+#define LBM_ISTMA_pairs 0
+#define LBM_ISTMA_pairgs 0
+#define LBM_ISTMA_pairh 0
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
+#define LBM_ISPAIR_hoist 0
+#define LBM_ISPAIR_split 0
+#define LBM_ISPAIR_hoistbal 0
+#define LBM_ISPAIR_splitbal 0
+#define LBM_ISPAIR_async 0
+#define LBM_ISPAIR_tma 0
+#define LBM_ISPAIR_pair 1
+#define LBM_ISPAIR_pairg 1
+#define LBM_ISPAIR_pairs 1
+#define LBM_ISPAIR_pairgs 1
+#define LBM_ISPAIR_pairh 1
+#define LBM_PAIR(ID, KIND, TX, TY, MB) LBM_ISPAIR_##KIND,
 
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
@@ -145,7 +177,7 @@ const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo,
                             Launchers<LBM_LAT, LBM_ST>::shift_rest, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
-                            {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS};
+                            {LBM_TILES(LBM_TMA)}, {LBM_TILES(LBM_PAIR)}, LBM_BATCH_FIELDS};
 
 }  // namespace
 

@@ -50,12 +50,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Bounded wait: false if the phase did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long it = 0; it < (1L << 22); ++it)
+// Bounded wait: false if the phase did not complete within `polls` tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long polls) {
+    for (long it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// Polls of the wait that drains the copies a failed CTA still has in flight:
+// far more than a bulk copy of a few tens of kilobytes takes to land.
+constexpr long kDrainPolls = 1L << 22;
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -125,7 +128,7 @@ struct TmaCfg {
 template <int LAT, int ST, int TX, int TY, int MINB, bool WALLS>
 __global__ void __launch_bounds__(TX * TY, MINB)
 step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D,
-                Geom G, PhysT<typename Storage<ST>::R> p, int chunk, int* error_flag) {
+                Geom G, PhysT<typename Storage<ST>::R> p, int chunk, int* error_flag, long wait_polls) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using S = typename St::S;
@@ -155,6 +158,10 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
     const int nchunks = (G.NZ + chunk - 1) / chunk;
     const long long items = (long long)ntiles * nchunks;   // (chunk, tile), tile fastest
     uint32_t hcount = 0, gcount = 0;                          // ring uses so far (parity = use & 1)
+    // uses issued so far (CTA-uniform: every thread follows the issue
+    // decisions of thread 0); all but the last use of a slot have been waited
+    // for when a wait gives up
+    uint32_t hiss = 0, giss = 0;
     bool failed = false;
 
     // issue the h box set of fill plane zf (unwrapped) into h slot s
@@ -234,9 +241,11 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
             for (int q = 0; q < 3 && q <= LZ + 1; ++q) issue_h(x0, y0, z0 - 1 + q, (hb0 + q) % 3);
             issue_g(x0, y0, z0, gb0 % 2);
         }
-        bool ok = mbar_wait(&hbar[hb0 % 3], ((hb0) / 3) & 1);
+        hiss = hb0 + (uint32_t)min(3, LZ + 2);
+        giss = gb0 + 1;
+        bool ok = mbar_wait(&hbar[hb0 % 3], ((hb0) / 3) & 1, wait_polls);
         fill(hb0 % 3, 0, x0, y0);
-        ok = ok && mbar_wait(&hbar[(hb0 + 1) % 3], ((hb0 + 1) / 3) & 1);
+        ok = ok && mbar_wait(&hbar[(hb0 + 1) % 3], ((hb0 + 1) / 3) & 1, wait_polls);
         fill((hb0 + 1) % 3, 1, x0, y0);
         if (__syncthreads_or(!ok)) { failed = true; break; }
         for (int j = 0; j < LZ; ++j) {
@@ -247,10 +256,12 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
                 if (j + 3 <= LZ + 1) issue_h(x0, y0, z0 - 1 + j + 3, (hb0 + j + 3) % 3);
                 if (j + 1 < LZ) issue_g(x0, y0, z + 1, (gb0 + j + 1) % 2);
             }
+            if (j + 3 <= LZ + 1) hiss = hb0 + (uint32_t)(j + 4);
+            if (j + 1 < LZ) giss = gb0 + (uint32_t)(j + 2);
             const uint32_t qh = hb0 + j + 2, qg = gb0 + j;
-            ok = mbar_wait(&hbar[qh % 3], (qh / 3) & 1);
+            ok = mbar_wait(&hbar[qh % 3], (qh / 3) & 1, wait_polls);
             fill(qh % 3, (j + 2) & 3, x0, y0);
-            ok = ok && mbar_wait(&gbar[qg % 2], (qg / 2) & 1);
+            ok = ok && mbar_wait(&gbar[qg % 2], (qg / 2) & 1, wait_polls);
             if (__syncthreads_or(!ok)) { failed = true; break; }
             if (active) {
                 const S* hs_ = reinterpret_cast<const S*>(smem + C::off_h + ((hb0 + j + 1) % 3) * C::HL::bytes);
@@ -330,16 +341,19 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
     if (failed) {
         if (tid == 0) atomicExch(error_flag, 1);
         // let copies already in flight land before the CTA's shared memory is
-        // released: the pending phase of every slot is the one after its last
-        // completed use (bounded waits; the counters are CTA-uniform)
-        for (uint32_t s = 0; s < (uint32_t)C::NHS; ++s) {
-            for (long it = 0; it < (1L << 16); ++it)
-                if (mbar_try_wait(&hbar[s], 0) && mbar_try_wait(&hbar[s], 1)) break;
-        }
-        for (uint32_t s = 0; s < (uint32_t)C::NGS; ++s) {
-            for (long it = 0; it < (1L << 16); ++it)
-                if (mbar_try_wait(&gbar[s], 0) && mbar_try_wait(&gbar[s], 1)) break;
-        }
+        // released.  Every use of a slot but its last issued one was waited for
+        // successfully, so the only phase that can be pending is that of the
+        // last issued use u (the (u / slots)-th use of the slot): wait for it,
+        // bounded; slots with no use issued have nothing in flight.
+        auto drain = [&](uint64_t* bars, uint32_t nslots, uint32_t issued) {
+            for (uint32_t s = 0; s < nslots; ++s) {
+                if (issued <= s) continue;
+                const uint32_t last = issued - 1 - ((issued - 1 - s) % nslots);   // last use of slot s
+                mbar_wait(&bars[s], (last / nslots) & 1, kDrainPolls);
+            }
+        };
+        drain(hbar, (uint32_t)C::NHS, hiss);
+        drain(gbar, (uint32_t)C::NGS, giss);
     }
 }
 

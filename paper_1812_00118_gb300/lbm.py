@@ -45,7 +45,8 @@ class lbm_params(ctypes.Structure):
                 ("nu_L", ctypes.c_double), ("nu_H", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("force_mode", ctypes.c_int),
                 ("eps", ctypes.c_double), ("hocorr", ctypes.c_int), ("store", ctypes.c_int),
-                ("P_ref", ctypes.c_double), ("g_scale", ctypes.c_double)]
+                ("P_ref", ctypes.c_double), ("g_scale", ctypes.c_double),
+                ("C_dtheta", ctypes.c_double)]
 
 
 _lib = None
@@ -68,6 +69,7 @@ SIGNATURES = [
     ("lbm_stream", _VP, [_VP]),
     ("lbm_set_wall_velocity", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     ("lbm_set_phi_correction", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_set_wait_limit", ctypes.c_int, [_VP, ctypes.c_longlong]),
     ("lbm_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_get_tile", ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
@@ -157,13 +159,15 @@ def lattice_info(lattice):
 
 
 def make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1 / 6, nu_H=0.1 / 6,
-                g=(0.0, 0.0, 0.0), force_mode=0, eps=1e-10, hocorr=1, store=F32, P_ref=0.0, g_scale=0.0):
+                g=(0.0, 0.0, 0.0), force_mode=0, eps=1e-10, hocorr=1, store=F32, P_ref=0.0, g_scale=0.0,
+                C_dtheta=0.0):
     p = lbm_params()
     p.M, p.W, p.sigma, p.rho_L, p.rho_H, p.nu_L, p.nu_H = M, W, sigma, rho_L, rho_H, nu_L, nu_H
     for a in range(3):
         p.g[a] = g[a] if a < len(g) else 0.0
     p.force_mode, p.eps, p.hocorr, p.store = force_mode, eps, int(hocorr), store
     p.P_ref, p.g_scale = P_ref, g_scale
+    p.C_dtheta = C_dtheta
     return p
 
 
@@ -184,16 +188,46 @@ def _ptr(a, writable=False):
 NOALLOC_MAX_NODES = 33554432
 
 
+def _noalloc_arg(name, t, n_min, n_exact=None):
+    """A contiguous float64 CUDA tensor on the current device with the stated
+    number of elements, else ValueError (checked before anything is launched:
+    a bad pointer or a short array would reach the kernel unchecked)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: float64 required, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if n_exact is not None and t.numel() != n_exact:
+        raise ValueError(f"{name}: {n_exact} elements required, got {t.numel()}")
+    if t.numel() < n_min:
+        raise ValueError(f"{name}: at least {n_min} elements required, got {t.numel()}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, current device is cuda:{torch.cuda.current_device()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def field_sums_noalloc(phi, P, v, rho_L, rho_dif, out, stream=None):
     """lbm_field_sums_noalloc on device tensors: phi, P (n,), v a sequence of up
-    to 3 component tensors (or None), out a (4,) float64 CUDA tensor."""
-    comps = list(v or [])[:3] + [None] * (3 - len(list(v or [])[:3]))
-    ptrs = [None if c is None else _ptr(c)[0] for c in comps]
+    to 3 component tensors of n elements (or None), out a float64 CUDA tensor
+    of at least 4 elements; all contiguous float64 on the current device."""
+    comps = list(v or [])
+    if len(comps) > 3:
+        raise ValueError("v: at most 3 components")
+    p_phi = _noalloc_arg("phi", phi, 0)
+    n = phi.numel()
+    p_P = _noalloc_arg("P", P, 0, n)
+    ptrs = [None if c is None else _noalloc_arg(f"v[{k}]", c, 0, n) for k, c in enumerate(comps)]
+    ptrs += [None] * (3 - len(ptrs))
+    p_out = _noalloc_arg("out", out, 4)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
-    _check(load().lbm_field_sums_noalloc(_ptr(phi)[0], _ptr(P)[0], ptrs[0], ptrs[1], ptrs[2], int(phi.numel()),
-                                         float(rho_L), float(rho_dif), _ptr(out, True)[0], ctypes.c_void_p(stream)),
+    _check(load().lbm_field_sums_noalloc(p_phi, p_P, ptrs[0], ptrs[1], ptrs[2], int(n), float(rho_L),
+                                         float(rho_dif), p_out, ctypes.c_void_p(stream)),
            "lbm_field_sums_noalloc")
 
 
@@ -319,6 +353,10 @@ class Simulation:
 
     def set_tile(self, tile, lz):
         _check(load().lbm_set_tile(self._ctx, tile, lz), "lbm_set_tile")
+
+    def set_wait_limit(self, polls):
+        """Poll limit of the bulk-copy pipeline waits (0: give up at once)."""
+        _check(load().lbm_set_wait_limit(self._ctx, int(polls)), "lbm_set_wait_limit")
 
     def get_tile(self):
         t, lz, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -20,7 +20,7 @@ def oracle_params(prm, bc_user, lat_id):
     return O.Params(M=prm.M, W=prm.W, sigma=prm.sigma, rho_L=prm.rho_L, rho_H=prm.rho_H,
                     nu_L=prm.nu_L, nu_H=prm.nu_H, g=(prm.g[0], prm.g[1], prm.g[2] if lat_id == 1 else 0.0),
                     force_mode=prm.force_mode, eps=prm.eps, hocorr=bool(prm.hocorr),
-                    modified_velocity=bool(prm.hocorr), bc=tuple(bc))
+                    modified_velocity=bool(prm.hocorr), bc=tuple(bc), C_dtheta=prm.C_dtheta)
 
 
 def order_map(lat_id):

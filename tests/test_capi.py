@@ -67,3 +67,29 @@ def test_missing_library_fails_loudly(tmp_path):
             lbm.load(str(tmp_path / "nope.so"))
     finally:
         lbm._lib = saved
+
+
+def test_noalloc_binding_rejects_bad_arguments_before_launch():
+    """The binding of lbm_field_sums_noalloc checks every argument before it
+    reaches the library: a numpy array, a wrong dtype, a non-contiguous
+    tensor, a P or vector component shorter than phi, an output of fewer than
+    4 elements, or a tensor not on the current CUDA device is a ValueError
+    (on this CPU-only machine every tensor fails the device check last)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_1812_00118_gb300 import lbm
+    f = torch.zeros(10, dtype=torch.float64)
+    out = torch.zeros(4, dtype=torch.float64)
+    bad = [
+        (np.zeros(10), f, None, out),                               # not a tensor
+        (f.float(), f, None, out),                                  # dtype
+        (torch.zeros(10, 2, dtype=torch.float64)[:, 0], f, None, out),   # not contiguous
+        (f, torch.zeros(9, dtype=torch.float64), None, out),        # P shorter than phi
+        (f, f, [f, torch.zeros(3, dtype=torch.float64)], out),      # component shorter
+        (f, f, [f, f, f, f], out),                                  # four components
+        (f, f, None, torch.zeros(3, dtype=torch.float64)),          # out too short
+        (f, f, None, out),                                          # host tensors
+    ]
+    for phi, P, v, o in bad:
+        with pytest.raises(ValueError):
+            lbm.field_sums_noalloc(phi, P, v, 0.0, 1.0, o, stream=0)

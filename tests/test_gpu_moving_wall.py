@@ -3,9 +3,10 @@
 rho(phi) for g).
 
 * FP64 populations after tens of steps, D2Q9 and D3Q19, both ends of the
-  walled axis sliding with different velocities, through the default
-  per-thread-load tile (14 for D3Q19, 1 for D2Q9), a bulk-copy tile and a
-  grid of a batch: 1e-10 normwise (operation order only);
+  walled axis sliding with different velocities, through the library's FP64
+  tile (one-node kernel: 8 for D3Q19, 1 for D2Q9), the bulk-copy tile and
+  (D2Q9) a grid of a batch: 1e-10 normwise (operation order only);
+* the same in FP32 through the node-pair tile (10): 1e-5 normwise;
 * the layered Couette flow of Section 3 in FP32 against the quadrature of
   (eta u')' = 0: within 3 % of the wall speed, as the oracle;
 * argument errors."""
@@ -47,10 +48,11 @@ CASES = [
 ]
 
 
-def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False):
+def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False, store=None):
     nz, ny, nx = shape
     phi, u, P = I.smooth_random(shape, 41, dim=2 if lat_id == 0 else 3)
-    prm = L.make_params(M=0.1, W=3.0, sigma=0.01, rho_L=0.01, rho_H=1.0, nu_L=0.1, nu_H=0.05, store=L.F64)
+    prm = L.make_params(M=0.1, W=3.0, sigma=0.01, rho_L=0.01, rho_H=1.0, nu_L=0.1, nu_H=0.05,
+                        store=L.F64 if store is None else store)
     user = (nx, ny) if lat_id == 0 else (nx, ny, nz)
     if batch:
         b = L.Batch([user], prm, bcs=[bc])
@@ -77,15 +79,19 @@ def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False):
     return out, oracle_macro_flat(h, g, lat, p, lat_id), b
 
 
-@pytest.mark.parametrize("lat_id,shape,bc,axis,walls", CASES, ids=["d2q9", "d3q19"])
-@pytest.mark.parametrize("path", ["default", "bulkcopy", "batch"])
-def test_sliding_walls_against_oracle(lbm, lat_id, shape, bc, axis, walls, path):
-    if path == "batch" and lat_id == 1:
-        pytest.skip("batches hold D2Q9 grids")
-    tile = (4, 3) if path == "bulkcopy" else None
+PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy", "batch", "pair")
+         if not (path == "batch" and CASES[c][0] == 1)]   # batches hold D2Q9 grids
+
+
+@pytest.mark.parametrize("case,path", PATHS, ids=[f"{('d2q9', 'd3q19')[CASES[c][0]]}-{p}" for c, p in PATHS])
+def test_sliding_walls_against_oracle(lbm, case, path):
+    lat_id, shape, bc, axis, walls = CASES[case]
+    tile = {"bulkcopy": (4, 3), "pair": (10, 5)}.get(path)
+    store = lbm.F32 if path == "pair" else lbm.F64
     (f, Pg, ru), (fo, Po, ruo), _ = run_case(lbm, lat_id, shape, bc, axis, walls, 40, tile=tile,
-                                             batch=path == "batch")
-    assert normwise(f, fo) < 1e-10 and normwise(Pg, Po) < 1e-10 and normwise(ru, ruo) < 1e-10
+                                             batch=path == "batch", store=store)
+    tol = 1e-5 if path == "pair" else 1e-10
+    assert normwise(f, fo) < tol and normwise(Pg, Po) < tol and normwise(ru, ruo) < tol
 
 
 def test_layered_couette_f32(lbm):

@@ -235,21 +235,22 @@ def test_config1_static_droplet_f64(lbm):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_tile_shapes_agree(lbm, lat_id, shape, bc):
-    """Every compiled CTA shape (per-thread loads, tiles 0-3; bulk tensor
-    copies, tiles 4-7; balanced persistent launches of tiles 0-3, tiles 8-11;
-    tile 1 at 7 CTAs per SM and its one-wave form, tiles 14-15) and z-chunk
-    length computes the same arithmetic: FP64 results agree to rounding (the
-    compiler may contract a*b+c differently per instantiation)."""
+    """Every compiled one-node tile that runs FP64 (per-thread loads, tiles
+    0-3; the bulk tensor copy pipeline, tile 4; one-wave launches, tiles 5-6
+    and 9; 7 CTAs per SM, tile 8) and z-chunk length computes the same
+    arithmetic: FP64 results agree to rounding (the compiler may contract
+    a*b+c differently per instantiation).  The cp.async tile (7) and the
+    node-pair tiles (10-13) compute in FP32 only."""
     ref = None
-    for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (5, 1), (6, 1), (7, 1),
-                     (8, 5), (9, 1), (10, 2), (11, 1), (9, 100), (12, 4), (14, 16), (14, 1), (15, 3),
-                     (15, 100)):
+    for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (4, 7), (5, 5), (6, 1), (6, 100),
+                     (7, 4), (8, 16), (8, 1), (9, 3), (9, 100), (10, 16)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            # bulk copies (4-7) and asynchronous copies (12-13) may not apply
-            assert e.code == lbm.ENOTSUP and (4 <= tile <= 7 or tile in (12, 13)), tile
+            # bulk copies (4) may not apply to a grid; cp.async (7) and the
+            # node-pair tiles (10-15) have no FP64 form
+            assert e.code == lbm.ENOTSUP and tile in (4, 7, 10, 11, 12, 13, 14, 15), tile
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
@@ -259,22 +260,43 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
             assert normwise(hg, ref[0]) < 1e-14 and normwise(gg, ref[1]) < 1e-13, (tile, lz)
 
 
+SAME_ARITH_TILES = ((7, 16), (7, 1), (7, 5), (8, 16), (8, 1), (9, 5))
+PAIR_TILES = ((10, 16), (10, 1), (10, 5), (11, 3), (11, 100), (12, 7), (12, 1), (13, 16), (13, 2), (14, 4),
+              (15, 16), (15, 3))
+
+
+def oracle_pops_after(lbm, lat_id, shape, bc, steps):
+    _, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    return O.run(h, g, lat, p, steps)
+
+
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
-def test_async_tiles_agree_f32(lbm, lat_id, shape, bc):
-    """The cp.async tiles (12-13; FP32 storage only) and the 7-CTA tiles
-    (14-15) against the per-thread-load tile 1 and the oracle: the same FP32
-    arithmetic, so agreement to a few FP32 roundings after 7 steps."""
+def test_f32_tiles_agree(lbm, lat_id, shape, bc):
+    """The FP32 tiles against the FP64 oracle after 7 steps (populations,
+    1e-5 normwise) and after one step (phi, P, rho u, 1e-5).  The tiles that
+    share the one-node kernel's arithmetic -- cp.async (7), 7 CTAs per SM
+    (8-9) -- also equal tile 1 to a few FP32 roundings (1e-6).  The node-pair
+    tiles (10-13: two nodes per thread on paired FP32 instructions, x pulled
+    from the ghost columns) group the same sums differently; near nodes where
+    grad phi nearly vanishes the interface normal of Eq. 2 amplifies such
+    rounding differences, so they are held to the oracle, not to tile 1."""
     ref, _, _, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
     ref.set_tile(1, 16)
     ref.step(7)
     hr, gr = ref.get_populations()
-    for tile, lz in ((12, 16), (12, 1), (12, 5), (13, 3), (13, 100), (13, 1), (14, 16), (14, 1), (15, 5)):
+    ho, go = oracle_pops_after(lbm, lat_id, shape, bc, 7)
+    hof, gof = oracle_to_lib_pops(ho, lat_id), oracle_to_lib_pops(go, lat_id)
+    assert normwise(hr, hof) < 1e-5 and normwise(gr, gof) < 1e-5
+    for tile, lz in SAME_ARITH_TILES + PAIR_TILES:
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, lz)
         sim.step(7)
         hg, gg = sim.get_populations()
-        assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz)
-    for tile in (12, 13, 14, 15):
+        eh, eg = normwise(hg, hof), normwise(gg, gof)
+        assert eh < 1e-5 and eg < 1e-5, (tile, lz, eh, eg)
+        if (tile, lz) in SAME_ARITH_TILES:
+            assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz, normwise(hg, hr), normwise(gg, gr))
+    for tile in (7, 8, 9, 10, 11, 12, 13, 14, 15):
         sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, 16)
         sim.step(1)
@@ -282,6 +304,28 @@ def test_async_tiles_agree_f32(lbm, lat_id, shape, bc):
         f, Pg, ru = sim.macro()
         fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
         assert normwise(f, fo) < 1e-5 and normwise(Pg, Po) < 1e-5 and normwise(ru, ruo) < 1e-5, tile
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
+def test_tile_switching_f32(lbm, lat_id, shape, bc):
+    """Changing tiles between steps: the node-pair tiles pull x from ghost
+    columns that a one-node tile does not write (the library first fills
+    them), and a one-node tile after a pair step finds the bounce-back
+    values where it wraps x.  A run that switches tiles every few steps stays
+    within 1e-5 (normwise, populations) of the FP64 oracle after 7 steps, as
+    a run on one tile does."""
+    ho, go = oracle_pops_after(lbm, lat_id, shape, bc, 7)
+    hof, gof = oracle_to_lib_pops(ho, lat_id), oracle_to_lib_pops(go, lat_id)
+    sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    for tile, n in ((8, 1), (10, 2), (8, 1), (4, 1), (11, 1), (12, 1)):
+        try:
+            sim.set_tile(tile, 5)
+        except lbm.LbmError as e:
+            assert e.code == lbm.ENOTSUP and tile == 4, tile
+            sim.set_tile(8, 5)
+        sim.step(n)
+    hg, gg = sim.get_populations()
+    assert normwise(hg, hof) < 1e-5 and normwise(gg, gof) < 1e-5, (normwise(hg, hof), normwise(gg, gof))
 
 
 @pytest.mark.parametrize("store", ["F64", "F32"])
@@ -340,3 +384,42 @@ def test_invalid_arguments(lbm):
     assert e.value.code == lbm.EINVAL
     with pytest.raises(lbm.LbmError):
         lbm.Simulation(lbm.D2Q9, (0, 8), lbm.make_params())
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[3]], ids=[IDS[0], IDS[1], IDS[3]])
+def test_delta_theta_against_oracle(lbm, lat_id, shape, bc):
+    """The diffusion correction of Eq. 14 (C = 2, F of the oracle's reading
+    R18) on smooth random fields, where (2 phi - 1) lap phi > 0 in places:
+    FP64 populations after one step to 1e-13, after 100 steps 1e-10
+    normwise; FP32 through the one-node (8) and node-pair (10) tiles after
+    one step 1e-5 normwise."""
+    sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F64, C_dtheta=2.0)
+    assert p.C_dtheta == 2.0
+    rng = np.random.default_rng(8)
+    h = h + rng.normal(scale=1e-3, size=h.shape)
+    sim.set_populations(oracle_to_lib_pops(h, lat_id), oracle_to_lib_pops(g, lat_id))
+    sim.step(1)
+    hg, gg = sim.get_populations()
+    h1, g1 = O.step(h, g, lat, p)
+    np.testing.assert_allclose(lib_to_oracle_pops(hg, lat_id, shape), h1, atol=1e-13, rtol=0)
+    np.testing.assert_allclose(lib_to_oracle_pops(gg, lat_id, shape), g1, atol=1e-13, rtol=0)
+    sim.step(99)
+    h2, g2 = O.run(h1, g1, lat, p, 99)
+    f, Pg, ru = sim.macro()
+    fo, Po, ruo = oracle_macro_flat(h2, g2, lat, p, lat_id)
+    assert normwise(f, fo) < 1e-10 and normwise(Pg, Po) < 1e-10 and normwise(ru, ruo) < 1e-10
+    # the case exercises the correction: without it the oracle differs
+    # from the corrected run far beyond the 1e-10 agreement above
+    p.C_dtheta = 0.0
+    h3, g3 = O.run(h, g, lat, p, 100)
+    f3, _, _ = oracle_macro_flat(h3, g3, lat, p, lat_id)
+    p.C_dtheta = 2.0
+    assert normwise(f3, fo) > 1e-8
+    for tile in (8, 10):
+        s32, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32, C_dtheta=2.0)
+        s32.set_tile(tile, 16)
+        s32.step(1)
+        h, g = O.step(h, g, lat, p)
+        f, Pg, ru = s32.macro()
+        fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
+        assert normwise(f, fo) < 1e-5 and normwise(Pg, Po) < 1e-5 and normwise(ru, ruo) < 1e-5, tile

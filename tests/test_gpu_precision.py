@@ -28,13 +28,15 @@ def lbm():
     return L
 
 
-def run_drop(L, store, steps, g_scale=0.0):
+def run_drop(L, store, steps, g_scale=0.0, tile=None):
     shape = (20, 22, 24)
     nz, ny, nx = shape
     phi, u, P = I.sphere(shape, (nx / 2 + 0.31, ny / 2 - 0.23, nz / 2 + 0.17), 7.0, 4.0, drop=True)
     prm = L.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1, nu_H=0.1, store=store,
                         g_scale=g_scale)
     sim = L.Simulation(L.D3Q19, (nx, ny, nz), prm)
+    if tile is not None:
+        sim.set_tile(tile, 16)
     sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), np.ascontiguousarray(u.reshape(-1)),
                     np.ascontiguousarray(P.reshape(-1)))
     sim.step(steps)
@@ -52,17 +54,20 @@ def oracle_200(lbm):
     return oracle_macro_flat(h, g, lat, p, 1), float(phi.sum())
 
 
+@pytest.mark.parametrize("tile", [8, 10], ids=["one-node", "pair"])
 @pytest.mark.parametrize("store,g_scale,bounds", [
     ("F32", 0.0, (1e-6, 1e-5, 1e-5)),
     ("F16S", 1e3, (1.2e-2, 2e-2, 8e-2)),
     ("BF16S", 0.0, (5e-2, 8e-2, 6e-1)),
 ], ids=["f32", "f16s", "bf16s"])
-def test_16bit_storage_error(lbm, oracle_200, store, g_scale, bounds):
+def test_16bit_storage_error(lbm, oracle_200, store, g_scale, bounds, tile):
+    """Every storage type through the one-node kernel (tile 8) and the
+    node-pair kernel (tile 10)."""
     (fo, Po, ruo), sum0 = oracle_200
-    (f, Pg, ru), d, _ = run_drop(lbm, getattr(lbm, store), 200, g_scale)
+    (f, Pg, ru), d, _ = run_drop(lbm, getattr(lbm, store), 200, g_scale, tile)
     errs = (normwise(f, fo), normwise(Pg, Po), normwise(ru, ruo))
     drift = abs(d["sum_phi"] - sum0) / sum0
-    print(f"{store} vs FP64 oracle after 200 steps: phi {errs[0]:.2e}  P {errs[1]:.2e}  rho_u {errs[2]:.2e}"
+    print(f"{store} tile {tile} vs FP64 oracle after 200 steps: phi {errs[0]:.2e}  P {errs[1]:.2e}  rho_u {errs[2]:.2e}"
           f"  sum(phi) drift {drift:.2e}")
     assert d["nonfinite"] == 0
     # 16-bit rounding of the stored h breaks exact conservation of sum(phi)

@@ -1,8 +1,8 @@
 """The allocation-free diagnostics entry point against lbm_diagnostics.
 
 lbm_field_sums_noalloc serves callers that cannot allocate device memory
-(stream capture with allocation forbidden, a host framework owning all
-device memory): its scratch is a static device array inside the library.
+(a host framework owning all device memory, a loop that must not enter the
+allocator): its scratch is a static device array inside the library.
 This file is collected last so that, if it fails, every other test has
 already run; it passes alone in a fresh process and after the others.
 """
