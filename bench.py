@@ -66,6 +66,11 @@ def parse():
                          "few per cent can change the pick, and with it the kernel the ncu profile describes)")
     ap.add_argument("--rising-ref-steps", type=int, default=2000,
                     help="rising: FP64 reference steps at full size (errors of the other forms are taken there)")
+    ap.add_argument("--ttt-cases", type=int, default=1000,
+                    help="ttt: training cases (each gives 20 snapshot pairs 2000 steps apart)")
+    ap.add_argument("--ttt-iters", type=int, default=4000, help="ttt: Adam iterations (mini-batch 8)")
+    ap.add_argument("--ttt-apply", type=int, default=20,
+                    help="ttt: surrogate applications at inference (each jumps 2000 steps)")
     ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt", "rising"], default="bubble128",
                     help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
                          "stepped as one batch; ttt: time-to-tolerance of D2Q9 drop relaxation for plain FP32, "
@@ -188,53 +193,129 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def oracle_glups(n_edge, steps, warmup=0):
-    """The FP64 numpy oracle as it stands on the host: `steps` time steps on a
-    periodic n_edge^3 crop of the workload fields around the bubble interface.
-    Returns (GLUPS, seconds, nodes)."""
-    import numpy as np
+# ---------------------------------------------------------------- oracle on all host cores
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    from oracle import lattice as OL
-    from oracle import pflbm as O
-    phi, u, P = workload_fields()
-    nx, ny, nz = SHAPE
-    if n_edge >= nx:
-        sl = (slice(None),) * 3
-    else:
-        c = (nz // 2, ny // 2, nx // 2 + int(BUBBLE_R))
-        sl = tuple(slice(ci - n_edge // 2, ci - n_edge // 2 + n_edge) for ci in c)
-    phi_s, P_s = np.ascontiguousarray(phi[sl]), np.ascontiguousarray(P[sl])
-    u_s = np.ascontiguousarray(u[(slice(None),) + sl])
-    p = O.Params(**PHYS)
-    h, g = O.init_populations(phi_s, u_s, P_s, OL.D3Q19, p)
-    for _ in range(warmup):
-        h, g = O.step(h, g, OL.D3Q19, p)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        h, g = O.step(h, g, OL.D3Q19, p)
-    dt = time.perf_counter() - t0
-    nodes = phi_s.size
-    return nodes * steps / dt / 1e9, dt, nodes
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_sample(kind, spec, steps, warmup, barrier, queue):
+    """One worker of the parallel oracle timing (a spawned process): builds its
+    sample of the workload, takes `warmup` steps, waits for every worker, then
+    times `steps` oracle steps.  Puts (lattice updates, seconds) on the queue."""
+    try:
+        from oracle import lattice as OL
+        from oracle import pflbm as O
+        from paper_1812_00118_gb300 import inputs as I
+        runs = []
+        if kind == "bubble":
+            n_edge, k = spec
+            phi, u, P = workload_fields()
+            nx, ny, nz = SHAPE
+            # crops centred on the bubble's interface, one per worker around its equator
+            ang = 2 * np.pi * k / 16.0
+            c = (nz // 2, ny // 2 + int(BUBBLE_R * np.sin(ang)), nx // 2 + int(BUBBLE_R * np.cos(ang)))
+            sl = tuple(slice(ci - n_edge // 2, ci - n_edge // 2 + n_edge) for ci in c) if n_edge < nx else \
+                (slice(None),) * 3
+            phi_s, P_s = np.ascontiguousarray(phi[sl]), np.ascontiguousarray(P[sl])
+            u_s = np.ascontiguousarray(u[(slice(None),) + sl])
+            p = O.Params(**PHYS)
+            runs.append((O.init_populations(phi_s, u_s, P_s, OL.D3Q19, p), OL.D3Q19, p, phi_s.size))
+        else:
+            cases = I.batch_cases(512)
+            for idx in spec:
+                c = cases[idx]
+                L = c["L"]
+                nu = (c["tau"] - 0.5) / 3.0
+                p = O.Params(M=0.1, W=c["W"], sigma=0.01, rho_L=1.0 / c["rho_ratio"], rho_H=1.0, nu_L=nu, nu_H=nu,
+                             bc=("periodic", "periodic", "periodic"))
+                phi, u, P = I.sphere((1, L, L), (L / 2 + 0.31, L / 2 - 0.23, 0), c["R"], c["W"], drop=c["drop"])
+                runs.append((O.init_populations(phi, u, P, OL.D2Q9, p), OL.D2Q9, p, L * L))
+        state = [list(r[0]) for r in runs]
+        for _ in range(warmup):
+            for st, (_, lat, p, _) in zip(state, runs):
+                st[0], st[1] = O.step(st[0], st[1], lat, p)
+        barrier.wait()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for st, (_, lat, p, _) in zip(state, runs):
+                st[0], st[1] = O.step(st[0], st[1], lat, p)
+        queue.put((sum(r[3] for r in runs) * steps, time.perf_counter() - t0))
+    except Exception as e:   # reported by the parent
+        queue.put(("error", repr(e)))
+
+
+def oracle_parallel(kind, specs, steps, warmup=0):
+    """The oracle as it stands, one spawned process per sample, all host cores
+    stepping at once (numpy single-threaded in each): aggregate throughput =
+    all lattice updates / the slowest worker's time.  Spawned processes, so it
+    is safe after the GPU was used."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(len(specs)), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_sample, args=(kind, sp, steps, warmup, barrier, queue)) for sp in specs]
+    for pr in procs:
+        pr.start()
+    res = [queue.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    bad = [r for r in res if r[0] == "error"]
+    if bad:
+        raise RuntimeError(f"oracle worker failed: {bad[0][1]}")
+    lu = sum(r[0] for r in res)
+    sec = max(r[1] for r in res)
+    return {"glups": lu / sec / 1e9, "seconds": sec, "lattice_updates": lu, "workers": len(specs)}
+
+
+def cpu_baseline_line(res, sample):
+    return {"value": res["glups"], "unit": "GLUPS", "cores": res["workers"], "kind": "oracle", "sample": sample,
+            "host_cores": host_cores(), "cpu_model": host_cpu_model()}
+
+
+def bubble_baseline(steps, warmup, budget_s):
+    """Oracle GLUPS of the bubble workload on all host cores: one crop per core,
+    the crop edge sized so that warmup + steps take about budget_s."""
+    cores = host_cores()
+    # s per lattice update of one oracle process while every core runs one:
+    # numpy's whole-field passes share the socket's memory bandwidth
+    cost = 6e-6
+    n = int((budget_s / max(1, steps + warmup) / cost) ** (1 / 3))
+    n = max(8, min(96, n))         # <= 0.9 M nodes (~2 GB) per process
+    res = oracle_parallel("bubble", [(n, k) for k in range(cores)], steps, warmup)
+    return res, n
 
 
 def run_reference(args):
-    """The oracle timed on the host cores, each step a bounded crop of the workload."""
+    """The oracle timed on all host cores, each step a bounded crop of the workload per core."""
     world, rank, local, dist = dist_setup()
     if rank != 0:
         return
-    # per-step crop sized so that warmup + steps take about 90 s at ~3 us/node
-    budget, cost = 90.0, 3e-6
-    n = int((budget / max(1, args.steps + args.warmup) / cost) ** (1 / 3))
-    n = max(8, min(SHAPE[0], n))
-    glups, dt, nodes = oracle_glups(n, args.steps, args.warmup)
+    res, n = bubble_baseline(args.steps, args.warmup, 90.0)
+    sample = (f"{args.steps} oracle steps on {res['workers']} periodic {n}^3 crops of the 128^3 fields around the "
+              f"bubble interface, one process per host core")
     line = {
-        "impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "impl": "reference", "metric": METRIC, "value": res["glups"], "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["seconds"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"periodic {n}^3 crop of the 128^3 fields per step"},
-        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle steps on a {n}^3 crop ({nodes} nodes) of the workload"},
-        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": cpu_baseline_line(res, sample),
+        "e2e": {"value": res["glups"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -330,9 +411,10 @@ def run_ours(args):
         "diagnostics": {"sum_phi": diag["sum_phi"], "max_u": diag["max_u"], "nonfinite": diag["nonfinite"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, dt, nodes = oracle_glups(SHAPE[0], 3)
-        line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                                "sample": f"3 oracle steps of the full 128^3 workload ({dt:.1f} s, numpy FP64, 1 thread)"}
+        res, n = bubble_baseline(2, 0, 20.0)
+        line["cpu_baseline"] = cpu_baseline_line(
+            res, f"2 oracle steps (numpy FP64) on each of {res['workers']} periodic {n}^3 crops of the workload, "
+                 f"one process per host core, {res['seconds']:.1f} s")
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -360,28 +442,6 @@ def batch_inputs(lbm, store, n=512):
         shapes.append((L, L))
         fields.append(I.sphere((1, L, L), (L / 2 + 0.31, L / 2 - 0.23, 0), c["R"], c["W"], drop=c["drop"]))
     return cases, shapes, params, fields
-
-
-def batch_oracle_glups(n_cases, steps):
-    """The FP64 oracle on the first n_cases grids of the workload, `steps` steps each."""
-    from oracle import lattice as OL
-    from oracle import pflbm as O
-    from paper_1812_00118_gb300 import inputs as I
-    cases = I.batch_cases(512)[:n_cases]
-    t, nodes = 0.0, 0
-    for c in cases:
-        L = c["L"]
-        nu = (c["tau"] - 0.5) / 3.0
-        p = O.Params(M=0.1, W=c["W"], sigma=0.01, rho_L=1.0 / c["rho_ratio"], rho_H=1.0, nu_L=nu, nu_H=nu,
-                     bc=("periodic", "periodic", "periodic"))
-        phi, u, P = I.sphere((1, L, L), (L / 2 + 0.31, L / 2 - 0.23, 0), c["R"], c["W"], drop=c["drop"])
-        h, g = O.init_populations(phi, u, P, OL.D2Q9, p)
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            h, g = O.step(h, g, OL.D2Q9, p)
-        t += time.perf_counter() - t0
-        nodes += L * L
-    return nodes * steps / t / 1e9, t, nodes
 
 
 def run_batch(args):
@@ -483,9 +543,10 @@ def run_batch(args):
                         "max_u": max(d["max_u"] for d in diag)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, dt, nodes = batch_oracle_glups(8, 3)
-        line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                                "sample": f"3 oracle steps on the first 8 grids ({nodes} nodes, {dt:.1f} s)"}
+        res, n = batch_baseline(2, 0, 20.0)
+        line["cpu_baseline"] = cpu_baseline_line(
+            res, f"2 oracle steps on the first {n} grids, spread over {res['workers']} processes (one per host "
+                 f"core), {res['seconds']:.1f} s")
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
@@ -494,29 +555,37 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-def run_batch_reference(args):
-    world, rank, local, dist = dist_setup()
-    if rank != 0:
-        return
-    # grids of the workload in order, as many as fit ~90 s over warmup + steps at ~3 us/node
+def batch_baseline(steps, warmup, budget_s):
+    """Oracle GLUPS of the batch workload on all host cores: the first grids of
+    the workload, as many as about budget_s of oracle work over warmup + steps
+    on all cores allows, dealt round-robin to one process per core."""
     from paper_1812_00118_gb300 import inputs as I
-    budget, cost = 90.0 / max(1, args.steps + args.warmup), 3e-6
+    cores = host_cores()
+    cost = 6e-6                    # as in bubble_baseline
+    budget = budget_s * cores / max(1, steps + warmup)
     n, acc = 0, 0
     for c in I.batch_cases(512):
         if n > 0 and (acc + c["L"] ** 2) * cost > budget:
             break
         acc += c["L"] ** 2
         n += 1
-    batch_oracle_glups(n, args.warmup) if args.warmup else None
-    glups, dt, nodes = batch_oracle_glups(n, args.steps)
+    specs = [list(range(k, n, cores)) for k in range(min(cores, n))]
+    return oracle_parallel("batch", specs, steps, warmup), n
+
+
+def run_batch_reference(args):
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return
+    res, n = batch_baseline(args.steps, args.warmup, 90.0)
+    sample = f"the first {n} grids of the workload per step, dealt over one process per host core"
     line = {
-        "impl": "reference", "metric": BATCH_METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "impl": "reference", "metric": BATCH_METRIC, "value": res["glups"], "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["seconds"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "sample": f"the first {n} grids ({nodes} nodes) per step"},
-        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle steps on the first {n} grids ({nodes} nodes)"},
-        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": BATCH_WORKLOAD, "sample": sample},
+        "cpu_baseline": cpu_baseline_line(res, sample),
+        "e2e": {"value": res["glups"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -652,11 +721,11 @@ def run_rising(args):
 
 
 # ---------------------------------------------------------------- ttt
-TTT_METRIC = "D2Q9 drop relaxation time-to-tolerance (ms), 8 held-out 128^2 cases, mean"
-TTT_WORKLOAD = ("1-4 static drops in a periodic 128^2 box (radii 12-28, density ratio 1000, sigma 0.01, W 4, "
-                "M 0.1, nu 1/60), started from u = 0, P = 0; converged when ||P(t) - P(t-100)|| / ||P(t)|| < 1e-3 "
-                "on 3 checks in a row; accuracy: phi total, mean-removed P against plain FP32, Laplace jump against "
-                "sigma/R on the single-drop cases")
+TTT_METRIC = "D2Q9 drop/bubble relaxation time-to-tolerance (ms), 8 held-out 256^2 cases, mean"
+TTT_WORKLOAD = ("1-4 static drops or bubbles in a periodic 256^2 box (radii 12-48 capped at L/4, density ratio 1000, "
+                "sigma 0.01, W 4, M 0.1, nu 1/60), started from u = 0, P = 0; converged when "
+                "||P(t) - P(t-100)|| / ||P(t)|| < 1e-6 on 3 checks in a row; accuracy: phi total, mean-removed P "
+                "against plain FP32, Laplace jump against sigma/R on the single-drop cases")
 
 
 def run_ttt(args):
@@ -669,19 +738,25 @@ def run_ttt(args):
     torch.cuda.set_device(0)
     build.build()
     lbm.load()
-    Lsz, T, n_train, iters = 128, 40000, 256, 2000
+    Lsz, K, tol = 256, 20, 1e-6
+    n_cases, iters, k_apply = args.ttt_cases, args.ttt_iters, args.ttt_apply
     eval_seeds = list(range(5000, 5008))
     zeros2, zeros1 = np.zeros(2 * Lsz * Lsz), np.zeros(Lsz * Lsz)
-    # surrogate: training pairs from the batched solver, training on the GPU
+    clocks = ClockSampler(0)   # the whole workload: data, training and every timed run
+    time.sleep(0.3)
+    # surrogate: trajectories from the batched solver, training on the GPU
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     e[0].record()
-    X, Y, dropped = WS.generate_pairs(torch, Lsz, list(range(1000, 1000 + n_train)), T)
+    S, dropped = WS.generate_snapshots(torch, Lsz, list(range(1000, 1000 + n_cases)), K)
     e[1].record()
     sg = Surrogate(8, Lsz, Lsz, seed=0)
-    hist = WS.train(torch, sg, X, Y, iters, lr=2e-3)
+    hist = WS.train(torch, sg, S, iters, lr=1e-3)
     e[2].record()
     e[2].synchronize()
-    identity = float(((X - Y) ** 2).mean().item())
+    identity = WS.identity_loss(S)
+    n_pairs = int(S.shape[0]) * K
+    del S
+    torch.cuda.empty_cache()
     sg1 = Surrogate(1, Lsz, Lsz, params=sg.params())
     forms = {}
 
@@ -690,38 +765,39 @@ def run_ttt(args):
         a, r = P - P.mean(), ref - ref.mean()
         return float(np.linalg.norm(a - r) / np.linalg.norm(r))
 
-    def laplace_err(sim, placed):
-        # single-drop cases: Laplace jump against sigma / R (2-D)
+    def laplace_err(sim, placed, bubble):
+        # single-drop cases: Laplace jump against sigma / R (2-D); a bubble's jump has the other sign
         if len(placed) != 1:
             return None
         cx, cy, R = placed[0]
         W = WS.PHYS["W"]
         dP = sim.laplace((cx % Lsz, cy % Lsz), R - 2 * W, R + 2 * W)
-        return dP / (WS.PHYS["sigma"] / R) - 1.0
+        return dP / ((-1.0 if bubble else 1.0) * WS.PHYS["sigma"] / R) - 1.0
 
-    def finish(name, sim, phi0, placed, res_steps, ms, ref=None):
+    def finish(name, sim, phi0, placed, bubble, res_steps, ms, ref=None):
         f, P, ru = sim.macro()
         rec = forms.setdefault(name, {"steps": [], "ms": [], "phi_drift": [], "P_vs_plain": [], "laplace_err": []})
         rec["steps"].append(res_steps)
         rec["ms"].append(ms)
         rec["phi_drift"].append(abs(f.sum() - phi0.sum()) / phi0.sum())
         rec["P_vs_plain"].append(None if ref is None else pdiff(P, ref))
-        rec["laplace_err"].append(laplace_err(sim, placed) if np.isfinite(P).all() else None)
+        rec["laplace_err"].append(laplace_err(sim, placed, bubble) if np.isfinite(P).all() else None)
         return P
 
     plain_P, plain_steps = [], []
     for sd in eval_seeds:
         phi0, placed = WS.case_fields(Lsz, sd)
+        bubble = sd % 2 == 1
         for name, store, fix in (("plain_f32", lbm.F32, 0), ("plain_f16s", lbm.F16S, 0),
                                  ("plain_f16s_phifix", lbm.F16S, 100), ("plain_bf16s", lbm.BF16S, 0),
                                  ("plain_bf16s_phifix", lbm.BF16S, 100)):
             sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), WS.case_params(store))
             sim.set_phi_correction(fix)
             sim.init_fields(phi0, zeros2, zeros1)
-            cap = 200000 if name == "plain_f32" else 2 * plain_steps[-1]
-            st, ms, r = WS.steps_to_tolerance(torch, sim, max_steps=cap)
+            cap = 400000 if name == "plain_f32" else 2 * plain_steps[-1]
+            st, ms, r = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=cap)
             ref = None if name == "plain_f32" else plain_P[-1]
-            P = finish(name, sim, phi0, placed, st, ms, ref)
+            P = finish(name, sim, phi0, placed, bubble, st, ms, ref)
             if name == "plain_f32":
                 plain_P.append(P)
                 plain_steps.append(st if st is not None else cap)
@@ -730,11 +806,11 @@ def run_ttt(args):
         sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), WS.case_params(lbm.F32))
         w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         w0.record()
-        WS.predict_into(torch, sg1, sim, phi0, WS.case_params(lbm.F32))
+        WS.predict_into(torch, sg1, sim, phi0, WS.case_params(lbm.F32), k_apply)
         w1.record()
         w1.synchronize()
-        st, ms, r = WS.steps_to_tolerance(torch, sim)
-        finish("warm_f32", sim, phi0, placed, st, ms + w0.elapsed_time(w1), plain_P[-1])
+        st, ms, r = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=2 * plain_steps[-1])
+        finish("warm_f32", sim, phi0, placed, bubble, st, ms + w0.elapsed_time(w1), plain_P[-1])
         forms["warm_f32"].setdefault("inference_ms", []).append(w0.elapsed_time(w1))
         sim.close()
     # the same 8 cases as one batch
@@ -745,14 +821,14 @@ def run_ttt(args):
         phis.append(phi0)
         places.append(placed)
         b.grid(k).init_fields(phi0, zeros2, zeros1)
-    done, ms = WS.batch_steps_to_tolerance(torch, b)
+    done, ms = WS.batch_steps_to_tolerance(torch, b, tol=tol, max_steps=2 * max(plain_steps))
     rec = {"steps": done, "ms_all_cases": ms, "ms": [ms / len(eval_seeds)] * len(eval_seeds), "phi_drift": [],
            "P_vs_plain": [], "laplace_err": []}
-    for k in range(len(eval_seeds)):
+    for k, sd in enumerate(eval_seeds):
         f, P, ru = b.grid(k).macro()
         rec["phi_drift"].append(abs(f.sum() - phis[k].sum()) / phis[k].sum())
         rec["P_vs_plain"].append(pdiff(P, plain_P[k]))
-        rec["laplace_err"].append(laplace_err(b.grid(k), places[k]))
+        rec["laplace_err"].append(laplace_err(b.grid(k), places[k], sd % 2 == 1))
     forms["batch_f32"] = rec
     b.close()
     summary = {}
@@ -769,16 +845,23 @@ def run_ttt(args):
     for k in ("plain_f16s_phifix", "plain_bf16s_phifix"):
         summary[k]["note"] = "total of phi re-imposed every 100 steps (lbm_set_phi_correction)"
     summary["warm_f32"]["mean_inference_ms"] = float(np.mean(forms["warm_f32"]["inference_ms"]))
+    ratios = [p / w for p, w in zip(forms["plain_f32"]["steps"], forms["warm_f32"]["steps"])
+              if p is not None and w is not None]
+    summary["warm_f32"]["plain_over_warm_steps"] = ratios
     warm = summary["warm_f32"]["mean_ms"]
+    clk = clocks.stop()
     line = {
         "metric": TTT_METRIC, "value": warm, "unit": "ms", "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": False, "scaling": None, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": TTT_WORKLOAD, "eval_seeds": eval_seeds, "value_is": "warm_f32 mean_ms"},
-        "forms": summary,
+        "config": {"workload": TTT_WORKLOAD, "eval_seeds": eval_seeds, "value_is": "warm_f32 mean_ms",
+                   "k_apply": k_apply, "steps_jumped": k_apply * WS.DT},
+        "forms": summary, "clocks": clk,
         "per_case": {k: {"steps": v["steps"]} for k, v in forms.items()},
-        "surrogate": {"train_pairs": int(X.shape[0]), "dropped_unbounded": dropped, "T_ahead": T,
-                      "iterations": iters, "data_ms": e[0].elapsed_time(e[1]), "train_ms": e[1].elapsed_time(e[2]),
+        "surrogate": {"cases": n_cases, "train_pairs": n_pairs, "dropped_unbounded": dropped, "DT": WS.DT,
+                      "snapshots_per_case": K + 1, "iterations": iters, "batch": 8,
+                      "data_ms": e[0].elapsed_time(e[1]), "train_ms": e[1].elapsed_time(e[2]),
                       "loss_first_last": [hist[0][1], hist[-1][1]], "identity_loss": identity,
+                      "flops_per_image_forward": sg1.flops_per_image(backward=False),
                       "kernels": "lbm_sg_* BF16 mma.sync implicit-GEMM convolutions, FP32 accumulation"},
     }
     print(json.dumps(line), flush=True)

@@ -126,6 +126,20 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params,
 int lbm_init_fields(lbm_ctx* ctx, const double* phi, const double* u, const double* P,
                     int on_device);
 
+/* lbm_init_fields with options.  flags = 0: the same call.  LBM_INIT_NONEQ:
+ * g also carries the filtered non-equilibrium part of a state that has
+ * relaxed onto the given flow, Phi_i : Pi(1) with Phi_i of Eq. 11 and the
+ * Chapman-Enskog estimate Pi(1) = -tau_mix T rho (grad u + grad u^T) of the
+ * non-equilibrium momentum flux (grad u by the central differences of the
+ * stencils after Eq. 12, tau_mix from Eq. 9); it leaves the zeroth and first
+ * moments, so lbm_macro still returns (phi, u, P).  The paper rebuilds no
+ * states; this serves the learned warm start (a state predicted as fields
+ * continues without the start-up transient an equilibrium start has).
+ * Errors: as lbm_init_fields, LBM_EINVAL for an unknown flag. */
+#define LBM_INIT_NONEQ 1
+int lbm_init_fields_ex(lbm_ctx* ctx, const double* phi, const double* u, const double* P, int on_device,
+                       int flags);
+
 /* Advance n >= 0 time steps: each step is one launch of the fused
  * collide-and-pull-stream kernel (Eqs. 1-14) and a buffer swap; the
  * bulk-copy tile (see lbm_set_tile) adds one launch of a small kernel that

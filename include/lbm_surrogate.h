@@ -15,9 +15,9 @@
  *   - Convolutions are periodic 3x3, "same" size:
  *       y[p, co] = bias[co] + sum_{dy, dx, ci} w[co, 3 dy + dx, ci] x[p + (dy - 1, dx - 1), ci]
  *     (offsets wrap inside each image); w is bf16 [Co][9][Ci].  Ci and Co
- *     are multiples of 16 (zero-pad), Co <= 64, N H W a multiple of 16.
- *   - Pooling and upsampling are by LBM_SG_POOL in both directions; H and W
- *     (always the FULL-resolution size) are multiples of it.
+ *     are multiples of 16 (zero-pad), Co <= 128, N H W a multiple of 16.
+ *   - Pooling and upsampling are by a factor f (1..64) in both directions;
+ *     H and W (always the FINE grid's size) are multiples of f.
  *   - The caller owns every buffer; the functions allocate nothing.  All are
  *     asynchronous on `stream` (NULL: default stream).
  *   - Return LBM_OK, LBM_EINVAL (NULL pointer, bad size or stride),
@@ -29,8 +29,6 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
-
-#define LBM_SG_POOL 8
 
 /* y (float) = periodic 3x3 convolution of x (bf16) with w (bf16), plus bias
  * (float[Co], may be NULL).  BF16 tensor-core products, FP32 sums. */
@@ -69,14 +67,15 @@ int lbm_sg_to_bf16(const float* a, int csa, void* y, int csy, long long npix, in
 int lbm_sg_add(const float* a, int csa, const float* b, int csb, float* out, int cso, long long npix, int C,
                void* stream);
 
-/* y (bf16, H/8 x W/8 images) = means of the 8 x 8 blocks of x (bf16, H x W). */
-int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream);
-/* gx (float, H x W) = g (float, H/8 x W/8) / 64 spread over each block. */
-int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream);
-/* y (bf16, H x W) = x (bf16, H/8 x W/8) repeated over each 8 x 8 block. */
-int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream);
-/* gx (float, H/8 x W/8) = sums of g (float, H x W) over each block. */
-int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream);
+/* y (bf16, H/f x W/f images) = means of the f x f blocks of x (bf16, H x W). */
+int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, int f, void* stream);
+/* gx (float, H x W) = g (float, H/f x W/f) / f^2 spread over each block. */
+int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, int f, void* stream);
+/* y (bf16, H x W) = x (bf16, H/f x W/f) repeated over each f x f block. */
+int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, int f, void* stream);
+/* gx (float, H/f x W/f) = sums of g (float, H x W) over each block. */
+int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, int f,
+                        void* stream);
 
 /* Mean squared error of out = x + delta against target over the first C
  * channels: *loss (device double) = mean (out - target)^2 (FP64 sums), and
@@ -99,8 +98,10 @@ int lbm_sg_pack(const double* phi, const double* rux, const double* ruy, const d
                 float* x32, int cs32, void* x16, int cs16, long long npix, void* stream);
 
 /* Fields for lbm_init_fields from the network output: (phi, rho u, P) =
- * (x32 + delta) * scale, written as phi, u = rho u / (rho_L + phi rho_dif)
- * (the density of the paper's rho(phi)) and P. */
+ * (x32 + delta) * scale, written as phi, u = rho u / (rho_L + phi_c rho_dif)
+ * (the density of the paper's rho(phi), phi_c = phi clipped to [0, 1] so
+ * that a slight undershoot of the prediction in the light phase cannot make
+ * it vanish) and P. */
 int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
                   double* P, const double scale[4], double rho_L, double rho_dif, long long npix, void* stream);
 

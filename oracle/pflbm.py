@@ -43,6 +43,11 @@ R10 Initialisation: h = h^eq, g = g^eq of the given (phi, u, P).
 R17 A buoyancy-driven start at rest takes the hydrostatic pressure,
     grad P = F (``hydrostatic_pressure``); the paper gives no initial
     pressure for its Rayleigh-Taylor cases.
+R19 Rebuilding populations from macroscopic fields (the learned warm start
+    of this library; the paper has none): g = g^eq + Phi_i : Pi(1) with the
+    Chapman-Enskog estimate Pi(1) = -tau_mix T rho (grad u + grad u^T) of the
+    non-equilibrium momentum flux, the part the filtered collision (Eq. 10)
+    keeps; h = h^eq.
 R18 The diffusion correction of Eq. 14 (Section 3) leaves the constant C and
     the function F open, asking only that F vanish on "decent" drops and
     bubbles.  Reading: F(phi, lap phi) = -W^2 max(0, (2 phi - 1) lap phi).
@@ -448,9 +453,24 @@ def hydrostatic_pressure(phi, p: Params):
     return P - P.mean()
 
 
-def init_populations(phi, u, P, lat: Lattice, p: Params):
+def chapman_enskog_pi(phi, u, lat: Lattice, p: Params):
+    """Reading R19 (for rebuilding populations from macroscopic fields; the
+    paper does not rebuild states): the first-order non-equilibrium second
+    moment of g, Pi(1) = -tau_mix T rho (grad u + grad u^T), with grad u by
+    the central differences of Section 2 applied to each velocity component
+    and tau_mix from Eq. 9.  Returns a (3, 3, ...) tensor."""
+    du = np.stack([gradient(u[b], lat, p.bc) for b in range(3)], axis=1)   # du[a, b] = d_a u_b
+    tau = 1.0 / inv_tau_mix(phi, p)
+    coef = -tau * T * density(phi, p)
+    return coef[None, None] * (du + np.swapaxes(du, 0, 1))
+
+
+def init_populations(phi, u, P, lat: Lattice, p: Params, nonequilibrium=False):
     """Reading R10: h = h^eq(phi, u), g = g^eq(phi, u, P) with the stencils of the
-    given phi.  Returns (h, g), pre-collision populations at t = 0."""
+    given phi.  With `nonequilibrium` (R19) g also carries the filtered
+    non-equilibrium part Phi_i : Pi(1) of Eq. 11, Pi(1) the Chapman-Enskog
+    estimate of chapman_enskog_pi.  Returns (h, g), pre-collision populations
+    at t = 0."""
     if p.force_mode == 1 and p.rho_bar is None:
         p.rho_bar = mean_density(phi, p)
     grad = gradient(phi, lat, p.bc)
@@ -462,6 +482,8 @@ def init_populations(phi, u, P, lat: Lattice, p: Params):
     h = h_equilibrium(phi, u, grad, lat, p, G, lap)
     K = forcing(u, grad, mu, F, lat, p, G)
     g = g_equilibrium(rho, u, P, K, lap, lat, p, G)
+    if nonequilibrium:
+        g = g + hermite_projection(chapman_enskog_pi(phi, u, lat, p), lat)
     return h, g
 
 

@@ -1,5 +1,5 @@
 """Oracle of the learned warm-start network: a plain FP64 numpy forward and
-backward pass of the small convolutional surrogate.
+backward pass of the convolutional surrogate.
 
 TEST INFRASTRUCTURE: imported only by tests/, __graft_entry__.smoke() and the
 CPU baseline of bench.py; the product path never calls it.
@@ -11,29 +11,30 @@ definitions:
 * periodic 3x3 convolution ("same" size, the LB domains are periodic):
   out[p, co] = b[co] + sum_{ci, dy, dx} W[co, ci, dy, dx] in[p + (dy - 1, dx - 1), ci]
   with p + offset wrapped on the grid;
-* ReLU, 8x8 average pooling, nearest upsampling by 8, channel concatenation;
+* ReLU, 2x2 average pooling, nearest upsampling by 2, channel concatenation;
 * the residual map out = in + net(in) on normalised fields.
 
 Layout: one sample is an (H, W, C) array (channels last), a batch is
 (N, H, W, C).  Weights W[co, ci, 3, 3], biases b[co].
 
-Architecture (channel counts):
-  e1:  conv 4 -> 16, ReLU                  (full resolution, x1)
-  pool 8x8                                 (coarse grid)
-  c1:  conv 16 -> 32, ReLU
-  c2:  conv 32 -> 32, ReLU
-  c3:  conv 32 -> 32, ReLU
-  c4:  conv 32 -> 16, ReLU
-  up 8x nearest, concat [x1, up]  -> 32 channels
-  d1:  conv 32 -> 16, ReLU
-  d2:  conv 16 -> 4                        (delta)
-  out = in + delta
+Architecture: a U-Net of four levels (grids H, H/2, H/4, H/8; H and W
+multiples of 8), 32 to 128 channels:
+  e1:  conv 4 -> 32, ReLU                          level 1: s1
+  pool, e2: conv 32 -> 64, ReLU                    level 2: s2
+  pool, e3: conv 64 -> 128, ReLU                   level 3: s3
+  pool, b:  conv 128 -> 128, ReLU                  level 4
+  up, concat [s3, up] (256), d3: conv -> 64, ReLU  level 3
+  up, concat [s2, up] (128), d2: conv -> 32, ReLU  level 2
+  up, concat [s1, up] (64),  d1: conv -> 32, ReLU  level 1
+  out: conv 32 -> 4                                (delta)
+  result = in + delta
 """
 import numpy as np
 
-LAYERS = [("e1", 4, 16), ("c1", 16, 32), ("c2", 32, 32), ("c3", 32, 32), ("c4", 32, 16),
-          ("d1", 32, 16), ("d2", 16, 4)]
-POOL = 8
+LAYERS = [("e1", 4, 32), ("e2", 32, 64), ("e3", 64, 128), ("b", 128, 128),
+          ("d3", 256, 64), ("d2", 128, 32), ("d1", 64, 32), ("out", 32, 4)]
+POOL = 2
+LEVELS = 4
 
 
 def init_params(seed=0):
@@ -42,7 +43,7 @@ def init_params(seed=0):
     params = {}
     for name, ci, co in LAYERS:
         std = np.sqrt(2.0 / (ci * 9))
-        if name == "d2":
+        if name == "out":
             std *= 0.1   # start close to the identity map
         params[name + ".W"] = rng.normal(0.0, std, size=(co, ci, 3, 3))
         params[name + ".b"] = np.zeros(co)
@@ -76,38 +77,46 @@ def conv3x3_backward(x, W, gout):
     return gx, gW, gb
 
 
-def pool(x):
+def pool(x, f=POOL):
+    """f x f block means."""
     N, H, W, C = x.shape
-    return x.reshape(N, H // POOL, POOL, W // POOL, POOL, C).mean(axis=(2, 4))
+    return x.reshape(N, H // f, f, W // f, f, C).mean(axis=(2, 4))
 
 
-def pool_backward(g, shape):
-    return np.repeat(np.repeat(g, POOL, axis=1), POOL, axis=2) / (POOL * POOL)
+def pool_backward(g, f=POOL):
+    return np.repeat(np.repeat(g, f, axis=1), f, axis=2) / (f * f)
 
 
-def upsample(x):
-    return np.repeat(np.repeat(x, POOL, axis=1), POOL, axis=2)
+def upsample(x, f=POOL):
+    """Nearest upsampling: every value repeated over an f x f block."""
+    return np.repeat(np.repeat(x, f, axis=1), f, axis=2)
 
 
-def upsample_backward(g):
+def upsample_backward(g, f=POOL):
     N, H, W, C = g.shape
-    return g.reshape(N, H // POOL, POOL, W // POOL, POOL, C).sum(axis=(2, 4))
+    return g.reshape(N, H // f, f, W // f, f, C).sum(axis=(2, 4))
 
 
 def forward(params, x):
     """Returns (output, cache) for input x (N, H, W, 4), H and W multiples of 8."""
-    c = {"x": x}
     P = params
-    a = conv3x3(x, P["e1.W"], P["e1.b"]); c["e1"] = a; x1 = np.maximum(a, 0.0); c["x1"] = x1
-    h = pool(x1); c["pool"] = h
-    for name in ("c1", "c2", "c3", "c4"):
-        c[name + ".in"] = h
-        a = conv3x3(h, P[name + ".W"], P[name + ".b"]); c[name] = a
-        h = np.maximum(a, 0.0)
-    up = upsample(h)
-    cat = np.concatenate([x1, up], axis=3); c["cat"] = cat
-    a = conv3x3(cat, P["d1.W"], P["d1.b"]); c["d1"] = a; hd = np.maximum(a, 0.0); c["hd"] = hd
-    delta = conv3x3(hd, P["d2.W"], P["d2.b"])
+    c = {"x": x}
+
+    def layer(name, inp):
+        c[name + ".in"] = inp
+        a = conv3x3(inp, P[name + ".W"], P[name + ".b"])
+        c[name] = a
+        return np.maximum(a, 0.0)
+
+    s1 = layer("e1", x)
+    s2 = layer("e2", pool(s1))
+    s3 = layer("e3", pool(s2))
+    hb = layer("b", pool(s3))
+    t3 = layer("d3", np.concatenate([s3, upsample(hb)], axis=3))
+    t2 = layer("d2", np.concatenate([s2, upsample(t3)], axis=3))
+    t1 = layer("d1", np.concatenate([s1, upsample(t2)], axis=3))
+    c["out.in"] = t1
+    delta = conv3x3(t1, P["out.W"], P["out.b"])
     return x + delta, c
 
 
@@ -121,17 +130,27 @@ def backward(params, cache, out, target):
     P = params
     g = {}
     gout = 2.0 * (out - target) / out.size
-    # out = x + d2(hd): the identity branch carries no parameters
-    ghd, g["d2.W"], g["d2.b"] = conv3x3_backward(cache["hd"], P["d2.W"], gout)
-    ga = ghd * (cache["d1"] > 0)
-    gcat, g["d1.W"], g["d1.b"] = conv3x3_backward(cache["cat"], P["d1.W"], ga)
-    n1 = cache["x1"].shape[3]
-    gx1 = gcat[..., :n1]
-    gh = upsample_backward(gcat[..., n1:])
-    for name in ("c4", "c3", "c2", "c1"):
-        ga = gh * (cache[name] > 0)
-        gh, g[name + ".W"], g[name + ".b"] = conv3x3_backward(cache[name + ".in"], P[name + ".W"], ga)
-    gx1 = gx1 + pool_backward(gh, cache["x1"].shape)
-    ga = gx1 * (cache["e1"] > 0)
-    _, g["e1.W"], g["e1.b"] = conv3x3_backward(cache["x"], P["e1.W"], ga)
+
+    def layer_back(name, gy):
+        """gy: gradient w.r.t. the layer's ReLU output; returns the gradient
+        w.r.t. its input and stores the parameter gradients."""
+        ga = gy * (cache[name] > 0)
+        gi, g[name + ".W"], g[name + ".b"] = conv3x3_backward(cache[name + ".in"], P[name + ".W"], ga)
+        return gi
+
+    # out = x + conv(t1): the identity branch carries no parameters
+    gt1, g["out.W"], g["out.b"] = conv3x3_backward(cache["out.in"], P["out.W"], gout)
+    gc1 = layer_back("d1", gt1)
+    n1 = P["e1.W"].shape[0]
+    gs1, gt2 = gc1[..., :n1], upsample_backward(gc1[..., n1:])
+    gc2 = layer_back("d2", gt2)
+    n2 = P["e2.W"].shape[0]
+    gs2, gt3 = gc2[..., :n2], upsample_backward(gc2[..., n2:])
+    gc3 = layer_back("d3", gt3)
+    n3 = P["e3.W"].shape[0]
+    gs3, ghb = gc3[..., :n3], upsample_backward(gc3[..., n3:])
+    gs3 = gs3 + pool_backward(layer_back("b", ghb))
+    gs2 = gs2 + pool_backward(layer_back("e3", gs3))
+    gs1 = gs1 + pool_backward(layer_back("e2", gs2))
+    layer_back("e1", gs1)
     return g

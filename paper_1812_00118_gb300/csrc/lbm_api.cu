@@ -398,8 +398,7 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void
     int rc = ctx_setup(c, grid, lattice, params, cuda_stream);
     if (rc) { delete c; return rc; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
-    // the node-pair kernels read (never use) up to a warp strip past the last row
-    const size_t bytes = c->elem * ((size_t)Q * (size_t)c->G.NP + kPairTail);
+    const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
     for (int b = 0; b < 2; ++b) {
         if (cudaMallocAsync(&c->h[b], bytes, c->stream) != cudaSuccess ||
             cudaMallocAsync(&c->g[b], bytes, c->stream) != cudaSuccess) {
@@ -436,7 +435,11 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double* P, int on_device) {
-    if (!c || !phi || !u || !P) return LBM_EINVAL;
+    return lbm_init_fields_ex(c, phi, u, P, on_device, 0);
+}
+
+int lbm_init_fields_ex(lbm_ctx* c, const double* phi, const double* u, const double* P, int on_device, int flags) {
+    if (!c || !phi || !u || !P || (flags & ~LBM_INIT_NONEQ)) return LBM_EINVAL;
     const long long N = c->G.N;
     int rc = ensure_scratch(c);
     if (rc) return rc;
@@ -460,9 +463,9 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
     // the buffer all its grids hold the state in)
     const int b = c->cur;
     if (check_cuda(c->K->init(c->h[b], c->g[b], c->G, c->P, f_phi(c), f_u(c, 0), f_u(c, 1), f_u(c, 2), f_P(c),
-                              c->stream)))
+                              (flags & LBM_INIT_NONEQ) ? 1 : 0, c->stream)))
         return LBM_ECUDA;
-    c->ghosts[b] = c->xghosts[b] = true;   // the initialisation writes the periodic images too
+    c->ghosts[b] = true;   // the initialisation writes the periodic images too
     c->diverged = false;
     if (check_cuda(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream))) return LBM_ECUDA;
     c->launches += 1;
@@ -498,7 +501,6 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
     if (!c || n < 0 || c->owner) return LBM_EINVAL;
     if (c->diverged) return LBM_EDIVERGED;
     const bool tma = c->K->tile_tma[c->tile] != 0;
-    const bool pair = c->K->tile_pair[c->tile] != 0;
     if (tma && c->maps_tile != c->tile) {
         for (int b = 0; b < 2; ++b)
             if (check_cuda(c->K->make_maps(c->tile, &c->maps[b], c->h[b], c->g[b], c->G))) return LBM_ECUDA;
@@ -518,11 +520,9 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
         a.maps = &c->maps[i];
         // bulk-copy tiles read the ghost band unwrapped: it must hold the
         // periodic images (per-thread-load tiles wrap their pulls instead)
-        // the node-pair tiles pull x from the ghost columns: after a state
-        // written by a one-node tile they need the periodic images first
-        if ((tma && !c->ghosts[i]) || (pair && !c->ghosts[i] && !c->xghosts[i])) {
+        if (tma && !c->ghosts[i]) {
             if (check_cuda(c->K->halo(c->h[i], c->g[i], c->G, c->stream))) return LBM_ECUDA;
-            c->ghosts[i] = c->xghosts[i] = true;
+            c->ghosts[i] = true;
             c->launches += 1;
         }
         if (ev) cudaEventRecord(ev[2 * s], c->stream);
@@ -530,10 +530,9 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
         if (ev) cudaEventRecord(ev[2 * s + 1], c->stream);
         c->launches += 1;
         c->ghosts[o] = false;
-        c->xghosts[o] = pair;   // a pair step writes the x images it pulls next
         if (tma) {
             if (check_cuda(c->K->halo(c->h[o], c->g[o], c->G, c->stream))) return LBM_ECUDA;
-            c->ghosts[o] = c->xghosts[o] = true;
+            c->ghosts[o] = true;
             c->launches += 1;
         }
         c->cur = o;
@@ -613,7 +612,7 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
     }
     const int b = c->cur;
     int rc = check_cuda(c->K->set(c->h[b], c->g[b], c->G, c->P, dh, dg, c->stream));
-    c->ghosts[b] = c->xghosts[b] = true;
+    c->ghosts[b] = true;
     c->diverged = false;
     if (!rc) rc = check_cuda(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->launches += 1;
@@ -683,7 +682,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         cudaFreeAsync(save_h, c->stream);
         return LBM_ENOMEM;
     }
-    const bool saved_ghosts = c->ghosts[c->cur], saved_xghosts = c->xghosts[c->cur];
+    const bool saved_ghosts = c->ghosts[c->cur];
     int rc = check_cuda(cudaMemcpyAsync(save_h, c->h[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     if (!rc) rc = check_cuda(cudaMemcpyAsync(save_g, c->g[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t e0, e1;
@@ -716,8 +715,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
         if (!rc) rc = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
         c->cur = 0;
         c->ghosts[0] = saved_ghosts;
-        c->xghosts[0] = saved_xghosts;
-        c->ghosts[1] = c->xghosts[1] = false;
+        c->ghosts[1] = false;
     }
     cudaFreeAsync(save_h, c->stream);
     cudaFreeAsync(save_g, c->stream);

@@ -241,8 +241,7 @@ int lbm_batch_create(int n, const lbm_grid* grids, const lbm_params* params, voi
     b->NP = base;
     b->rho_bar_up.assign(n, 0.0);
     b->pversion_up.assign(n, 0);
-    // tail: the node-pair kernels read (never use) up to a warp strip past the last row
-    const size_t bytes = b->elem * (9 * (size_t)b->NP + kPairTail);
+    const size_t bytes = b->elem * 9 * (size_t)b->NP;
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
         ok = cudaMallocAsync(&b->h[k], bytes, b->stream) == cudaSuccess &&

@@ -7,7 +7,6 @@
 #include <new>
 
 #include "lbm_internal.h"
-#include "lbm_pair.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
@@ -224,42 +223,6 @@ cudaError_t launch_tma_tile(const StepArgs& a) {
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- node-pair tiles (FP32 arithmetic)
-template <int LAT, int ST, int TX, int TY>
-bool pair_tile_ok(const Geom&) {
-    return ST != ST_F64 && sizeof(PairSmem<LAT, ST, TX, TY>) <= 227 * 1024;
-}
-
-template <int LAT, int ST, int TX, int TY, int MINB, bool GFIRST, bool SRING, bool HG>
-cudaError_t launch_pair_tile(const StepArgs& a) {
-    if constexpr (ST == ST_F64) {
-        return cudaErrorNotSupported;
-    } else {
-        using S = typename Storage<ST>::S;
-        const Geom& G = a.G;
-        const bool walls = G.wall[0] || G.wall[1] || G.wall[2];
-        auto kern = walls ? step_pair_kernel<LAT, ST, TX, TY, MINB, true, GFIRST, SRING, HG>
-                          : step_pair_kernel<LAT, ST, TX, TY, MINB, false, GFIRST, SRING, HG>;
-        constexpr size_t bytes = sizeof(PairSmem<LAT, ST, TX, TY>);
-        static PerDevice attr_cache;
-        int done = 0;
-        cudaError_t e = per_device(attr_cache, walls ? 1 : 0, [&](int* v) {
-            *v = 1;
-            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-            // MINB CTAs of `bytes` each must fit the shared-memory carveout
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-            return r;
-        }, &done);
-        if (e != cudaSuccess) return e;
-        dim3 grid((G.NX + TX - 1) / TX, (G.NY + TY - 1) / TY, (G.NZ + a.lz - 1) / a.lz);
-        kern<<<grid, TX / 2 * TY, bytes, a.stream>>>(dir_ptrs<S, Lattice<LAT>::Q>(a.hin, a.gin, a.hout, a.gout, G.NP),
-                                                     G, phys_as<float>(a.p), a.lz);
-        return cudaGetLastError();
-    }
-}
-
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <int LAT, int ST>
@@ -278,10 +241,11 @@ struct Launchers {
         return cudaGetLastError();
     }
     static cudaError_t init(void* hout, void* gout, const Geom& G, const Phys& p, const double* phi,
-                            const double* ux, const double* uy, const double* uz, const double* P,
+                            const double* ux, const double* uy, const double* uz, const double* P, int neq,
                             cudaStream_t s) {
         init_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>(
-            dir_ptrs<S, Q>(hout, gout, hout, gout, G.NP), G, p, phi, ux, uy, uz, P);
+            dir_ptrs<S, Q>(hout, gout, hout, gout, G.NP), G, phys_as<typename Storage<ST>::R>(p), phi, ux, uy, uz, P,
+            neq);
         return cudaGetLastError();
     }
     static cudaError_t get(const void* hin, const void* gin, const Geom& G, const Phys& p, double* h, double* g,

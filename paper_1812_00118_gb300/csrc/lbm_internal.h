@@ -11,7 +11,7 @@ namespace lbm {
 
 struct TmaMaps;
 
-constexpr int kMaxTiles = 16;   // step kernel variants per (lattice, storage)
+constexpr int kMaxTiles = 10;   // step kernel variants per (lattice, storage)
 
 // Everything one step launch needs.
 struct StepArgs {
@@ -56,7 +56,7 @@ struct KernelTable {
     cudaError_t (*macro)(const void* gin, const Geom& G, const Phys& p, const double* phi, double* P,
                          double* ux, double* uy, double* uz, cudaStream_t s);
     cudaError_t (*init)(void* hout, void* gout, const Geom& G, const Phys& p, const double* phi,
-                        const double* ux, const double* uy, const double* uz, const double* P,
+                        const double* ux, const double* uy, const double* uz, const double* P, int neq,
                         cudaStream_t s);
     cudaError_t (*get)(const void* hin, const void* gin, const Geom& G, const Phys& p, double* h,
                        double* g, cudaStream_t s);
@@ -69,7 +69,6 @@ struct KernelTable {
     int n_tiles;            // number of compiled step tile shapes
     int tile_tx[kMaxTiles], tile_ty[kMaxTiles];
     int tile_tma[kMaxTiles];   // 1: bulk tensor copy pipeline, 0: per-thread loads
-    int tile_pair[kMaxTiles];  // 1: node-pair kernel (pulls x from the ghost columns)
     // batches of grids (D2Q9; null and 0 for D3Q19)
     cudaError_t (*batch_step)(const BatchArgs& a);
     // BatchCase<R> of n grids from their geometries and parameters into d_cases
@@ -114,8 +113,6 @@ struct lbm_ctx {
     lbm::TmaMaps maps[2];  // tensor maps of buffer pair 0 and 1 for a bulk-copy tile
     int maps_tile = -1;    // tile the maps were made for
     bool ghosts[2] = {false, false};   // ghost band of buffer b holds the periodic images
-    bool xghosts[2] = {false, false};  // ghost columns x = -1, NX of buffer b hold what the
-                                       // node-pair kernel pulls (x images, unwrapped wall ghosts)
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up
     bool diverged = false; // the last lbm_diagnostics found the state diverged
     long wait_polls = 1L << 22;   // bulk-copy pipeline wait limit (lbm_set_wait_limit)

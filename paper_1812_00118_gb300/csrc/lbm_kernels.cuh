@@ -31,10 +31,6 @@ namespace lbm {
 
 // ---------------------------------------------------------------- geometry
 constexpr int kRep = 2;   // periodic replication depth in x and y
-// Elements allocated after the last population array of a buffer: a warp
-// strip of the node-pair kernels (lbm_pair.cuh) that overhangs the last row
-// of a grid reads, but never uses, up to one strip width past the row end.
-constexpr int kPairTail = 1024;
 
 struct Geom {
     int NX, NY, NZ;   // nodes (internal axes)
@@ -180,6 +176,60 @@ template <> __device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(co
     unsigned short v; asm("ld.global.nc.L1::no_allocate.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
     return __ushort_as_bfloat16(v);
 }
+
+// Predicated read-only load (default caching, as ld_keep): 0 where !pred.
+// The load sits in the same basic block as its neighbours, so a thread's
+// unconditional and predicated loads are issued back to back.
+template <typename S> __device__ __forceinline__ S ld_keep_if(const S* p, bool pred);
+template <> __device__ __forceinline__ double ld_keep_if<double>(const double* p, bool pred) {
+    double v = 0.0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.L2::256B.f64 %0, [%1];\n\t}"
+        : "+d"(v) : "l"(p), "r"((unsigned)pred));
+    return v;
+}
+template <> __device__ __forceinline__ float ld_keep_if<float>(const float* p, bool pred) {
+    float v = 0.0f;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.L2::256B.f32 %0, [%1];\n\t}"
+        : "+f"(v) : "l"(p), "r"((unsigned)pred));
+    return v;
+}
+template <> __device__ __forceinline__ __half ld_keep_if<__half>(const __half* p, bool pred) {
+    unsigned short v = 0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.L2::256B.b16 %0, [%1];\n\t}"
+        : "+h"(v) : "l"(p), "r"((unsigned)pred));
+    return __ushort_as_half(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 ld_keep_if<__nv_bfloat16>(const __nv_bfloat16* p, bool pred) {
+    unsigned short v = 0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.L2::256B.b16 %0, [%1];\n\t}"
+        : "+h"(v) : "l"(p), "r"((unsigned)pred));
+    return __ushort_as_bfloat16(v);
+}
+
+// phi = sum_i h_i (after Eq. 4) in the kernels' arithmetic type.  FP32 sums
+// are compensated: a running sum seeded with 1 (so every addend is smaller in
+// magnitude than the sum, as Fast2Sum requires, while phi stays in [-1/2, 1])
+// collects each addition's rounding error exactly, and phi = (s - 1) + e with
+// s - 1 exact (Sterbenz).  An uncompensated FP32 sum of 19 values up to phi/3
+// carries ~1e-7 of error into phi, ten times the rounding of the stored h
+// themselves, and the stencils of Eq. 12 amplify it; at tau near 1/2 it grows
+// over the steps.  FP64 sums plainly.
+template <typename R>
+struct PhiSum {
+    R s = 0, e = 0;
+    __device__ __forceinline__ void add(R v) { s += v; }
+    __device__ __forceinline__ R value() const { return s; }
+};
+template <>
+struct PhiSum<float> {
+    float s = 1.0f, e = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = __fadd_rn(s, v);
+        e = __fadd_rn(e, __fsub_rn(v, __fsub_rn(t, s)));
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(__fsub_rn(s, 1.0f), e); }
+};
 
 // Padded flat offset of (possibly ghost) coordinates.
 __device__ __forceinline__ int pidx(const Geom& G, int x, int y, int z) {
@@ -829,6 +879,7 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
     // ring has no more positions than the CTA has threads, its ring position
     PullOffsets own_xy, ring_xy;
     pull_xy(G, stencil_coord(x0 + tx, G.NX, G.wall[0]), HY ? stencil_coord(y0 + ty, G.NY, G.wall[1]) : y0, own_xy);
+    ring_xy = own_xy;   // threads without a ring position: valid offsets, loads predicated off
     constexpr bool kOneRing = NRING <= TX * TY;
     int ring_off = 0;
     if (kOneRing && tid < NRING) {
@@ -839,38 +890,55 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
                 HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0, ring_xy);
     }
     auto ring_phi = [&](PullOffsets po) {
-        R phi = (R)0;
+        PhiSum<R> phi;
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr double W = L::w[i];
-            phi += St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
+            phi.add(St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1));
         });
-        return phi;
+        return phi.value();
     };
-    // the thread's own position first (its pulled h kept in hown[hs]), then
-    // its share of the halo ring
+    // the thread's own position (its pulled h kept in hown[hs]) and its share
+    // of the halo ring; with one ring position per thread, both sets of loads
+    // are issued before either is summed (one latency instead of two)
     auto fill = [&](int zp, int slot, int hs) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
-        {
-            PullOffsets po = own_xy;
+        if constexpr (kOneRing) {
+            PullOffsets po = own_xy, pr = ring_xy;
             pull_z(G, zz, po);
-            R phi = (R)0;
+            pull_z(G, zz, pr);
+            const bool ring = tid < NRING;
+            typename St::S hv[Q], rv[Q];
+            Unroll<0, Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                hv[i] = ld_keep(pull_ptr<LAT, i>(D.hin, po));
+                rv[i] = ld_keep_if(pull_ptr<LAT, i>(D.hin, pr), ring);
+            });
+            PhiSum<R> phi, rphi;
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr double W = L::w[i];
-                const R v = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
+                const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
                 hown[hs][i][tid] = v;
-                phi += v;
+                phi.add(v);
+                rphi.add(St::load(rv[i], (R)W * p.h_shift, (R)1));
             });
-            phis[slot][ty + HY][tx + 1] = phi;
-        }
-        if constexpr (kOneRing) {
-            if (tid < NRING) {
-                PullOffsets po = ring_xy;
-                pull_z(G, zz, po);
-                (&phis[slot][0][0])[ring_off] = ring_phi(po);
-            }
+            phis[slot][ty + HY][tx + 1] = phi.value();
+            if (ring) (&phis[slot][0][0])[ring_off] = rphi.value();
         } else {
+            {
+                PullOffsets po = own_xy;
+                pull_z(G, zz, po);
+                PhiSum<R> phi;
+                Unroll<0, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    constexpr double W = L::w[i];
+                    const R v = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
+                    hown[hs][i][tid] = v;
+                    phi.add(v);
+                });
+                phis[slot][ty + HY][tx + 1] = phi.value();
+            }
             for (int k = tid; k < NRING; k += TX * TY) {
                 int lx, ly;
                 ring_pos(k, &lx, &ly);
@@ -1006,15 +1074,15 @@ __device__ __forceinline__ void march_async(const DirPtrs<float, Lattice<LAT>::Q
     };
     // phi of the landed plane (own h in hown[hs]) into ring slot `slot`
     auto sum_fill = [&](int slot, int hs) {
-        float phi = 0.0f;
-        Unroll<0, Q>::run([&](auto ic) { phi += sm.hown[hs][decltype(ic)::value][tid]; });
-        sm.phis[slot][ty + HY][tx + 1] = phi;
+        PhiSum<float> phi;
+        Unroll<0, Q>::run([&](auto ic) { phi.add(sm.hown[hs][decltype(ic)::value][tid]); });
+        sm.phis[slot][ty + HY][tx + 1] = phi.value();
         for (int r = tid; r < NRING; r += NT) {
             int lx, ly;
             ring_pos<TX, TY, HY>(r, &lx, &ly);
-            float v = 0.0f;
-            Unroll<0, Q>::run([&](auto ic) { v += sm.ring[decltype(ic)::value][r]; });
-            sm.phis[slot][ly][lx] = v;
+            PhiSum<float> v;
+            Unroll<0, Q>::run([&](auto ic) { v.add(sm.ring[decltype(ic)::value][r]); });
+            sm.phis[slot][ly][lx] = v.value();
         }
     };
     auto issue_g = [&](int zg) {
@@ -1225,13 +1293,30 @@ __device__ __forceinline__ void pull_cell(const Geom& G, int x, int y, int z, in
     *tx = a; *ty = b; *tz = c;
 }
 
+// Store v at ghost-padded (x, y, z) of one population array and, for a cell
+// within kRep of an x or y edge, at its periodic images (store_rep); a cell
+// away from the edges has none, and is written once.
+template <typename S>
+__device__ __forceinline__ void store_cell(S* __restrict__ arr, const Geom& G, int x, int y, int z, S v) {
+    const bool near_x = !G.wall[0] && (x < kRep || x >= G.NX - kRep);
+    const bool near_y = G.GY > 0 && !G.wall[1] && (y < kRep || y >= G.NY - kRep);
+    if (near_x || near_y || x < 0 || x >= G.NX || y < 0 || y >= G.NY) store_rep(arr, G, x, y, z, v);
+    else arr[pidx(G, x, y, z)] = v;
+}
+
 // Equilibrium initialisation (h = h^eq, g = g^eq of the given fields),
-// written where the next pull reads it.
+// written where the next pull reads it, in the kernels' arithmetic type R
+// (FP32 for FP32 and 16-bit storage, FP64 for FP64 storage): the stored
+// values carry the storage rounding either way.
+// With neq, g also carries the filtered non-equilibrium part of a state
+// that has relaxed onto its flow: Phi_i : Pi(1) (Eq. 11) with the
+// Chapman-Enskog estimate Pi(1) = -tau_mix T rho (grad u + grad u^T), grad u
+// by the central differences of grad phi.
 template <int LAT, int ST>
-__global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, Phys p,
-                            const double* __restrict__ phi, const double* __restrict__ ux,
-                            const double* __restrict__ uy, const double* __restrict__ uz,
-                            const double* __restrict__ P) {
+__global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G,
+                            PhysT<typename Storage<ST>::R> p, const double* __restrict__ phi,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ uz, const double* __restrict__ P, int neq) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using R = typename St::R;
@@ -1239,44 +1324,68 @@ __global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
     if (n >= G.N) return;
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
-    NodeState<double> s;
-    s.phi = phi[n];
-    stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
-    const double rho_dif = p.rho_dif;
+    double gx, gy, gz, lap;
+    stencils<LAT>(phi, G, x, y, z, &gx, &gy, &gz, &lap);
+    NodeState<R> s;
+    s.phi = (R)phi[n];
+    s.gx = (R)gx; s.gy = (R)gy; s.gz = (R)gz; s.lap = (R)lap;
+    const R rho_dif = p.rho_dif;
     s.rho = p.rho_L + s.phi * rho_dif;
-    s.mu = p.beta * s.phi * (s.phi - 1) * (s.phi - 0.5) - p.kappa * s.lap;
-    const double fr = p.force_mode == 0 ? s.rho : s.rho - p.rho_bar;
+    s.mu = p.beta * s.phi * (s.phi - (R)1) * (s.phi - (R)0.5) - p.kappa * s.lap;
+    const R fr = p.force_mode == 0 ? s.rho : s.rho - p.rho_bar;
     s.Fx = fr * p.g[0]; s.Fy = fr * p.g[1]; s.Fz = fr * p.g[2];
-    s.ux = ux[n]; s.uy = L::kHasY ? uy[n] : 0.0; s.uz = uz[n];
-    s.P = P[n];
+    s.ux = (R)ux[n]; s.uy = L::kHasY ? (R)uy[n] : (R)0; s.uz = (R)uz[n];
+    s.P = (R)P[n];
     s.usq = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
     s.ug = s.ux * s.gx + s.uy * s.gy + s.uz * s.gz;
     s.uF = s.ux * s.Fx + s.uy * s.Fy + s.uz * s.Fz;
-    const double gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
-    s.nx = s.gx / (gmag + p.eps); s.ny = s.gy / (gmag + p.eps); s.nz = s.gz / (gmag + p.eps);
-    const double d = s.phi - 0.5;
-    s.theta = p.theta_coef * (1 - 4 * d * d);
-    if (p.dtheta_coef != 0.0) {   // Eq. 14, as in node_state
-        const double t = (2 * s.phi - 1) * s.lap;
-        s.theta -= p.dtheta_coef * (t > 0 ? t : 0.0) * gmag;
+    const R gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
+    const R inv = (R)1 / (gmag + p.eps);
+    s.nx = s.gx * inv; s.ny = s.gy * inv; s.nz = s.gz * inv;
+    const R d = s.phi - (R)0.5;
+    s.theta = p.theta_coef * ((R)1 - (R)4 * d * d);
+    if (p.dtheta_coef != (R)0) {   // Eq. 14, as in node_state
+        const R t = ((R)2 * s.phi - (R)1) * s.lap;
+        s.theta -= p.dtheta_coef * (t > (R)0 ? t : (R)0) * gmag;
+    }
+    // Pi(1) components (zero without neq)
+    R nxx = 0, nyy = 0, nzz = 0, nxy = 0, nxz = 0, nyz = 0, ntr3 = 0;
+    if (neq) {
+        double d[3][3], l;   // d[a][b] = d_a u_b
+        stencils<LAT>(ux, G, x, y, z, &d[0][0], &d[1][0], &d[2][0], &l);
+        if (L::kHasY) stencils<LAT>(uy, G, x, y, z, &d[0][1], &d[1][1], &d[2][1], &l);
+        else d[0][1] = d[1][1] = d[2][1] = 0.0;
+        stencils<LAT>(uz, G, x, y, z, &d[0][2], &d[1][2], &d[2][2], &l);
+        const double pc = s.phi < (R)0 ? 0.0 : (s.phi > (R)1 ? 1.0 : (double)s.phi);
+        const double tau = 1.0 / ((double)p.om_L + pc * (double)p.om_dif);
+        const double cf = -tau * (1.0 / 3.0) * (double)s.rho;
+        nxx = (R)(cf * 2 * d[0][0]); nyy = (R)(cf * 2 * d[1][1]); nzz = (R)(cf * 2 * d[2][2]);
+        nxy = (R)(cf * (d[0][1] + d[1][0])); nxz = (R)(cf * (d[0][2] + d[2][0])); nyz = (R)(cf * (d[1][2] + d[2][1]));
+        ntr3 = (nxx + nyy + nzz) * (R)(1.0 / 3.0);
     }
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
-        const double w = L::w[i];
-        const double cu = CX * s.ux + CY * s.uy + CZ * s.uz;
-        const double Gm1 = w * (3 * cu + 4.5 * cu * cu - 1.5 * s.usq);   // Gamma_i - w_i
-        const double Gm = w + Gm1;
-        const double cgr = CX * s.gx + CY * s.gy + CZ * s.gz;
-        const double cF = CX * s.Fx + CY * s.Fy + CZ * s.Fz;
-        const double K = (Gm1 * rho_dif + 3 * Gm * s.mu) * (cgr - s.ug) + 3 * Gm * (cF - s.uF);
-        double geq = s.rho * Gm1 + 3 * w * s.P - 0.5 * K;
-        if (p.hocorr) geq += w * cu * 0.75 * rho_dif * s.lap;
-        const double heq = s.phi * Gm + s.theta * w * (CX * s.nx + CY * s.ny + CZ * s.nz);
+        constexpr double W = L::w[i];
+        const R w = (R)W;
+        const R cu = cdot3<CX, CY, CZ>(s.ux, s.uy, s.uz);
+        const R Gm1 = w * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * s.usq);   // Gamma_i - w_i
+        const R Gm = w + Gm1;
+        const R cgr = cdot3<CX, CY, CZ>(s.gx, s.gy, s.gz);
+        const R cF = cdot3<CX, CY, CZ>(s.Fx, s.Fy, s.Fz);
+        const R K = (Gm1 * rho_dif + (R)3 * Gm * s.mu) * (cgr - s.ug) + (R)3 * Gm * (cF - s.uF);
+        R geq = s.rho * Gm1 + (R)3 * w * s.P - (R)0.5 * K;
+        if (p.hocorr) geq += w * cu * (R)0.75 * rho_dif * s.lap;
+        if (neq) {   // w_i / (2 T^2) (c_i c_i : Pi(1) - T tr Pi(1))
+            const R ccp = cdot3<CX * CX, CY * CY, CZ * CZ>(nxx, nyy, nzz) +
+                          (R)2 * cdot3<CX * CY, CX * CZ, CY * CZ>(nxy, nxz, nyz);
+            geq += (R)4.5 * w * (ccp - ntr3);
+        }
+        const R heq = s.phi * Gm + s.theta * w * cdot3<CX, CY, CZ>(s.nx, s.ny, s.nz);
         int tx, ty, tz;
         pull_cell<LAT, i>(G, x, y, z, &tx, &ty, &tz);
-        store_rep(D.hout[i], G, tx, ty, tz, St::store((R)heq, (R)(w * p.h_shift), (R)1));
-        store_rep(D.gout[i], G, tx, ty, tz, St::store((R)geq, (R)(w * p.g_shift), (R)p.g_scale));
+        store_cell(D.hout[i], G, tx, ty, tz, St::store(heq, w * p.h_shift, (R)1));
+        store_cell(D.gout[i], G, tx, ty, tz, St::store(geq, w * p.g_shift, p.g_scale));
     });
 }
 

@@ -202,10 +202,10 @@ __global__ void add_kernel(const float* __restrict__ a, int csa, const float* __
     out[p * cso + c] = a[p * csa + c] + b[p * csb + c];
 }
 
-// 8x8 average pooling, bf16 -> bf16; (N, H, W) the full-resolution grid
+// f x f average pooling, bf16 -> bf16; (N, H, W) the fine grid
 __global__ void pool_kernel(const bf16* __restrict__ x, int csx, bf16* __restrict__ y, int csy, int N, int H, int W,
-                            int C) {
-    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+                            int C, int f) {
+    const int Hc = H / f, Wc = W / f;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)N * Hc * Wc * C) return;
     const int c = (int)(k % C);
@@ -213,46 +213,46 @@ __global__ void pool_kernel(const bf16* __restrict__ x, int csx, bf16* __restric
     const int xc = (int)(q % Wc), yc = (int)((q / Wc) % Hc);
     const long long n = q / ((long long)Hc * Wc);
     float s = 0.0f;
-    for (int i = 0; i < LBM_SG_POOL; ++i)
-        for (int j = 0; j < LBM_SG_POOL; ++j) {
-            const long long p = (n * H + yc * LBM_SG_POOL + i) * W + xc * LBM_SG_POOL + j;
+    for (int i = 0; i < f; ++i)
+        for (int j = 0; j < f; ++j) {
+            const long long p = (n * H + yc * f + i) * W + xc * f + j;
             s += __bfloat162float(x[p * csx + c]);
         }
-    y[q * csy + c] = __float2bfloat16_rn(s * (1.0f / (LBM_SG_POOL * LBM_SG_POOL)));
+    y[q * csy + c] = __float2bfloat16_rn(s / (float)(f * f));
 }
 
-// gx[full] = g[coarse] / 64
+// gx[fine] = g[coarse] / f^2
 __global__ void pool_bwd_kernel(const float* __restrict__ g, int csg, float* __restrict__ gx, int csx, int N, int H,
-                                int W, int C) {
+                                int W, int C, int f) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)N * H * W * C) return;
     const int c = (int)(k % C);
     const long long p = k / C;
     const int x = (int)(p % W), y = (int)((p / W) % H);
     const long long n = p / ((long long)H * W);
-    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
-    const long long q = (n * Hc + y / LBM_SG_POOL) * Wc + x / LBM_SG_POOL;
-    gx[p * csx + c] = g[q * csg + c] * (1.0f / (LBM_SG_POOL * LBM_SG_POOL));
+    const int Hc = H / f, Wc = W / f;
+    const long long q = (n * Hc + y / f) * Wc + x / f;
+    gx[p * csx + c] = g[q * csg + c] / (float)(f * f);
 }
 
-// nearest upsampling by 8, bf16 -> bf16; (N, H, W) the full-resolution grid
+// nearest upsampling by f, bf16 -> bf16; (N, H, W) the fine grid
 __global__ void upsample_kernel(const bf16* __restrict__ x, int csx, bf16* __restrict__ y, int csy, int N, int H,
-                                int W, int C) {
+                                int W, int C, int f) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)N * H * W * C) return;
     const int c = (int)(k % C);
     const long long p = k / C;
     const int xx = (int)(p % W), yy = (int)((p / W) % H);
     const long long n = p / ((long long)H * W);
-    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
-    const long long q = (n * Hc + yy / LBM_SG_POOL) * Wc + xx / LBM_SG_POOL;
+    const int Hc = H / f, Wc = W / f;
+    const long long q = (n * Hc + yy / f) * Wc + xx / f;
     y[p * csy + c] = x[q * csx + c];
 }
 
-// gx[coarse] = sum of g over the 8x8 block
+// gx[coarse] = sum of g over the f x f block
 __global__ void upsample_bwd_kernel(const float* __restrict__ g, int csg, float* __restrict__ gx, int csx, int N,
-                                    int H, int W, int C) {
-    const int Hc = H / LBM_SG_POOL, Wc = W / LBM_SG_POOL;
+                                    int H, int W, int C, int f) {
+    const int Hc = H / f, Wc = W / f;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)N * Hc * Wc * C) return;
     const int c = (int)(k % C);
@@ -260,9 +260,9 @@ __global__ void upsample_bwd_kernel(const float* __restrict__ g, int csg, float*
     const int xc = (int)(q % Wc), yc = (int)((q / Wc) % Hc);
     const long long n = q / ((long long)Hc * Wc);
     float s = 0.0f;
-    for (int i = 0; i < LBM_SG_POOL; ++i)
-        for (int j = 0; j < LBM_SG_POOL; ++j) {
-            const long long p = (n * H + yc * LBM_SG_POOL + i) * W + xc * LBM_SG_POOL + j;
+    for (int i = 0; i < f; ++i)
+        for (int j = 0; j < f; ++j) {
+            const long long p = (n * H + yc * f + i) * W + xc * f + j;
             s += g[p * csg + c];
         }
     gx[q * csx + c] = s;
@@ -357,6 +357,8 @@ __global__ void pack_kernel(const double* __restrict__ f0, const double* __restr
 }
 
 // (phi, rho u_x, rho u_y, P) = (x + delta) * scale, then u = rho u / rho(phi)
+// with phi clipped to [0, 1] inside rho only (a predicted phi a little below
+// 0 in the light phase must not make the density vanish or turn negative)
 __global__ void unpack_kernel(const float* __restrict__ x32, int cs32, const float* __restrict__ delta, int csd,
                               double* __restrict__ f0, double* __restrict__ f1, double* __restrict__ f2,
                               double* __restrict__ f3, double s0, double s1, double s2, double s3, double rho_L,
@@ -366,7 +368,8 @@ __global__ void unpack_kernel(const float* __restrict__ x32, int cs32, const flo
     double v[4];
     const double s[4] = {s0, s1, s2, s3};
     for (int c = 0; c < 4; ++c) v[c] = ((double)x32[p * cs32 + c] + (double)delta[p * csd + c]) * s[c];
-    const double rho = rho_L + v[0] * rho_dif;
+    const double pc = v[0] < 0.0 ? 0.0 : (v[0] > 1.0 ? 1.0 : v[0]);
+    const double rho = rho_L + pc * rho_dif;
     f0[p] = v[0];
     f1[p] = v[1] / rho;
     f2[p] = v[2] / rho;
@@ -431,7 +434,7 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     const long long M = (long long)N * H * W;
     if (!x || !w || !y || N < 1 || H < 1 || W < 1 || !conv_dims_ok(M, Ci, Co) || csx < Ci || csx % 2 || csy < Co)
         return LBM_EINVAL;
-    if (Co > 64) return LBM_EINVAL;
+    if (Co > 128) return LBM_EINVAL;
     const long long warps = M / 16;
     const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
     cudaStream_t s = (cudaStream_t)stream;
@@ -442,6 +445,10 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
         case 2: conv_fwd_kernel<4><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
         case 3: conv_fwd_kernel<6><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
         case 4: conv_fwd_kernel<8><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 5: conv_fwd_kernel<10><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 6: conv_fwd_kernel<12><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 7: conv_fwd_kernel<14><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
+        case 8: conv_fwd_kernel<16><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
         default: return LBM_EINVAL;
     }
     return check(cudaGetLastError());
@@ -511,34 +518,37 @@ int lbm_sg_add(const float* a, int csa, const float* b, int csb, float* out, int
     return check(cudaGetLastError());
 }
 
-static bool pool_dims_ok(int N, int H, int W, int C) {
-    return N >= 1 && H >= LBM_SG_POOL && W >= LBM_SG_POOL && H % LBM_SG_POOL == 0 && W % LBM_SG_POOL == 0 && C >= 1;
+static bool pool_dims_ok(int N, int H, int W, int C, int f) {
+    return N >= 1 && f >= 1 && f <= 64 && H >= f && W >= f && H % f == 0 && W % f == 0 && C >= 1;
 }
 
-int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream) {
-    if (!x || !y || !pool_dims_ok(N, H, W, C) || csx < C || csy < C) return LBM_EINVAL;
-    const long long n = (long long)N * (H / LBM_SG_POOL) * (W / LBM_SG_POOL) * C;
-    pool_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)x, csx, (bf16*)y, csy, N, H, W, C);
+int lbm_sg_pool(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, int f, void* stream) {
+    if (!x || !y || !pool_dims_ok(N, H, W, C, f) || csx < C || csy < C) return LBM_EINVAL;
+    const long long n = (long long)N * (H / f) * (W / f) * C;
+    pool_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)x, csx, (bf16*)y, csy, N, H, W, C, f);
     return check(cudaGetLastError());
 }
 
-int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream) {
-    if (!g || !gx || !pool_dims_ok(N, H, W, C) || csx < C || csg < C) return LBM_EINVAL;
-    pool_bwd_kernel<<<blocks((long long)N * H * W * C), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W, C);
+int lbm_sg_pool_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, int f, void* stream) {
+    if (!g || !gx || !pool_dims_ok(N, H, W, C, f) || csx < C || csg < C) return LBM_EINVAL;
+    pool_bwd_kernel<<<blocks((long long)N * H * W * C), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W,
+                                                                                            C, f);
     return check(cudaGetLastError());
 }
 
-int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, void* stream) {
-    if (!x || !y || !pool_dims_ok(N, H, W, C) || csx < C || csy < C) return LBM_EINVAL;
+int lbm_sg_upsample(const void* x, int csx, void* y, int csy, int N, int H, int W, int C, int f, void* stream) {
+    if (!x || !y || !pool_dims_ok(N, H, W, C, f) || csx < C || csy < C) return LBM_EINVAL;
     upsample_kernel<<<blocks((long long)N * H * W * C), kThreads, 0, (cudaStream_t)stream>>>((const bf16*)x, csx,
-                                                                                            (bf16*)y, csy, N, H, W, C);
+                                                                                            (bf16*)y, csy, N, H, W, C,
+                                                                                            f);
     return check(cudaGetLastError());
 }
 
-int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, void* stream) {
-    if (!g || !gx || !pool_dims_ok(N, H, W, C) || csx < C || csg < C) return LBM_EINVAL;
-    const long long n = (long long)N * (H / LBM_SG_POOL) * (W / LBM_SG_POOL) * C;
-    upsample_bwd_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W, C);
+int lbm_sg_upsample_bwd(const float* g, int csg, float* gx, int csx, int N, int H, int W, int C, int f,
+                        void* stream) {
+    if (!g || !gx || !pool_dims_ok(N, H, W, C, f) || csx < C || csg < C) return LBM_EINVAL;
+    const long long n = (long long)N * (H / f) * (W / f) * C;
+    upsample_bwd_kernel<<<blocks(n), kThreads, 0, (cudaStream_t)stream>>>(g, csg, gx, csx, N, H, W, C, f);
     return check(cudaGetLastError());
 }
 

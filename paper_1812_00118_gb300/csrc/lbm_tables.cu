@@ -17,9 +17,7 @@ namespace {
 // D3Q19: CTA shapes in the x-y plane (nodes).  Tiles 0-3 use per-thread
 // loads, 4 the bulk tensor copy pipeline, 5-6 are tiles 0-1 as a one-wave
 // launch, 7 loads through cp.async ahead of use (FP32 storage only), 8-9 are
-// tile 1 and its one-wave form at 7 CTAs per SM (72 registers instead of 64),
-// 10-13 the node-pair kernel (two nodes per thread, paired FP32 arithmetic;
-// FP32 and 16-bit storage), 64 nodes per warp along x.
+// tile 1 and its one-wave form at 7 CTAs per SM (72 registers instead of 64).
 #define LBM_TILES(X)         \
     X(0, hoist, 32, 4, 4)    \
     X(1, split, 32, 4, 8)    \
@@ -30,13 +28,7 @@ namespace {
     X(6, splitbal, 32, 4, 8) \
     X(7, async, 32, 4, 4)    \
     X(8, split, 32, 4, 7)    \
-    X(9, splitbal, 32, 4, 7) \
-    X(10, pair, 64, 4, 4)    \
-    X(11, pairg, 64, 4, 4)   \
-    X(12, pairs, 64, 8, 2)   \
-    X(13, pairgs, 64, 8, 2)  \
-    X(14, pair, 64, 4, 5)    \
-    X(15, pairh, 64, 4, 4)
+    X(9, splitbal, 32, 4, 7)
 #else
 // D2Q9: the 2-D grid is stored as (nx, 1, ny); CTAs are rows along x
 #define LBM_TILES(X)           \
@@ -49,13 +41,7 @@ namespace {
     X(6, splitbal, 128, 1, 8)  \
     X(7, async, 128, 1, 8)     \
     X(8, split, 128, 1, 7)     \
-    X(9, splitbal, 128, 1, 7)  \
-    X(10, pair, 128, 1, 8)     \
-    X(11, pairg, 128, 1, 8)    \
-    X(12, pairs, 256, 1, 4)    \
-    X(13, pairgs, 256, 1, 4)   \
-    X(14, pair, 128, 1, 10)    \
-    X(15, pairh, 128, 1, 8)
+    X(9, splitbal, 128, 1, 7)
 #endif
 
 #define LBM_LAUNCH_hoist(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false>(a)
@@ -64,11 +50,6 @@ namespace {
 #define LBM_LAUNCH_splitbal(TX, TY, MB) launch_step_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true>(a)
 #define LBM_LAUNCH_async(TX, TY, MB) launch_async_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
 #define LBM_LAUNCH_tma(TX, TY, MB) launch_tma_tile<LBM_LAT, LBM_ST, TX, TY, MB>(a)
-#define LBM_LAUNCH_pair(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false, false>(a)
-#define LBM_LAUNCH_pairg(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, false, false>(a)
-#define LBM_LAUNCH_pairs(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, true, false>(a)
-#define LBM_LAUNCH_pairgs(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, true, true, false>(a)
-#define LBM_LAUNCH_pairh(TX, TY, MB) launch_pair_tile<LBM_LAT, LBM_ST, TX, TY, MB, false, false, true>(a)
 #define LBM_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_LAUNCH_##KIND(TX, TY, MB);
 
@@ -85,11 +66,6 @@ cudaError_t step_dispatch(const StepArgs& a) {
 #define LBM_MAPS_splitbal(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_async(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_tma(TX, TY) make_maps_tile<LBM_LAT, LBM_ST, TX, TY>(out, h, g, G)
-#define LBM_MAPS_pair(TX, TY) cudaErrorInvalidValue
-#define LBM_MAPS_pairg(TX, TY) cudaErrorInvalidValue
-#define LBM_MAPS_pairs(TX, TY) cudaErrorInvalidValue
-#define LBM_MAPS_pairgs(TX, TY) cudaErrorInvalidValue
-#define LBM_MAPS_pairh(TX, TY) cudaErrorInvalidValue
 #define LBM_MAPS_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_MAPS_##KIND(TX, TY);
 
@@ -106,11 +82,6 @@ cudaError_t maps_dispatch(int tile, TmaMaps* out, const void* h, const void* g, 
 #define LBM_OK_splitbal(TX, TY) true
 #define LBM_OK_async(TX, TY) async_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_tma(TX, TY) tma_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
-#define LBM_OK_pair(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
-#define LBM_OK_pairg(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
-#define LBM_OK_pairs(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
-#define LBM_OK_pairgs(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
-#define LBM_OK_pairh(TX, TY) pair_tile_ok<LBM_LAT, LBM_ST, TX, TY>(G)
 #define LBM_OK_CASE(ID, KIND, TX, TY, MB) \
     case ID: return LBM_OK_##KIND(TX, TY);
 
@@ -152,24 +123,7 @@ cudaError_t batch_dispatch(const BatchArgs& a) {
 #define LBM_ISTMA_splitbal 0
 #define LBM_ISTMA_async 0
 #define LBM_ISTMA_tma 1
-#define LBM_ISTMA_pair 0
-#define LBM_ISTMA_pairg 0
-#define LBM_ISTMA_pairs 0
-#define LBM_ISTMA_pairgs 0
-#define LBM_ISTMA_pairh 0
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
-#define LBM_ISPAIR_hoist 0
-#define LBM_ISPAIR_split 0
-#define LBM_ISPAIR_hoistbal 0
-#define LBM_ISPAIR_splitbal 0
-#define LBM_ISPAIR_async 0
-#define LBM_ISPAIR_tma 0
-#define LBM_ISPAIR_pair 1
-#define LBM_ISPAIR_pairg 1
-#define LBM_ISPAIR_pairs 1
-#define LBM_ISPAIR_pairgs 1
-#define LBM_ISPAIR_pairh 1
-#define LBM_PAIR(ID, KIND, TX, TY, MB) LBM_ISPAIR_##KIND,
 
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
@@ -177,7 +131,7 @@ const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo,
                             Launchers<LBM_LAT, LBM_ST>::shift_rest, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
-                            {LBM_TILES(LBM_TMA)}, {LBM_TILES(LBM_PAIR)}, LBM_BATCH_FIELDS};
+                            {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS};
 
 }  // namespace
 

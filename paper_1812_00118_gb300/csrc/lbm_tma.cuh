@@ -195,14 +195,14 @@ step_tma_kernel(const __grid_constant__ TmaMaps maps, const DirPtrs<typename Sto
         const S* hb = reinterpret_cast<const S*>(smem + C::off_h + s * C::HL::bytes);
         for (int k = tid; k < C::SX * C::SY; k += TX * TY) {
             const int lx = k % C::SX, ly = k / C::SX;
-            R phi = (R)0;
+            PhiSum<R> phi;
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr int off = C::HL::dir_offset(i) / C::ES + A - 1 - L::cx[i];
                 constexpr double W = L::w[i];
-                phi += St::load(hb[off + ly * C::BX + lx], (R)W * p.h_shift, (R)1);
+                phi.add(St::load(hb[off + ly * C::BX + lx], (R)W * p.h_shift, (R)1));
             });
-            phis[r][ly][lx] = phi;
+            phis[r][ly][lx] = phi.value();
         }
         if (G.wall[0] || (HY && G.wall[1])) {
             __syncthreads();

@@ -97,13 +97,14 @@ def batch_cases(n_cases=512, L_min=32, L_max=512, seed=0):
     return cases
 
 
-def drops(L, seed, n_min=1, n_max=4, R_min=12.0, R_max=48.0, W=4.0, gap=None):
+def drops(L, seed, n_min=1, n_max=4, R_min=12.0, R_max=48.0, W=4.0, gap=None, bubbles=False):
     """(phi, u, P, drops) of 1-4 static drops (phi = 1 inside) in a periodic
     L x L box, shape (1, L, L): radii uniform in [R_min, R_max], centres
     uniform and off the nodes, drops at least `gap` (default 2 W) apart along
     the periodic distance, phi the sum of the tanh profiles (clipped to 1).
-    A drop that finds no room after 200 tries is left out; the drop list
-    gives (x, y, R)."""
+    With `bubbles` the phases are exchanged: light-phase bubbles (phi = 0
+    inside) in the heavy phase.  A drop that finds no room after 200 tries is
+    left out; the drop list gives (x, y, R)."""
     rng = np.random.default_rng([seed, 1812])
     gap = 2.0 * W if gap is None else gap
     n = int(rng.integers(n_min, n_max + 1))
@@ -129,6 +130,8 @@ def drops(L, seed, n_min=1, n_max=4, R_min=12.0, R_max=48.0, W=4.0, gap=None):
         p, _, _ = sphere((1, L, L), (cx, cy, 0.0), R, W, drop=True)
         phi += p
     phi = np.minimum(phi, 1.0)
+    if bubbles:
+        phi = 1.0 - phi
     return phi, np.zeros((3, 1, L, L)), np.zeros((1, L, L)), placed
 
 

@@ -22,6 +22,7 @@ F64, F32, F16S, BF16S = 0, 1, 2, 3
 STORE_NAMES = {F64: "f64", F32: "f32", F16S: "f16s", BF16S: "bf16s"}
 
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+INIT_NONEQ = 1
 
 
 class LbmLibraryMissing(RuntimeError):
@@ -57,6 +58,7 @@ SIGNATURES = [
     ("lbm_create", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), _VP,
                                   ctypes.POINTER(_VP)]),
     ("lbm_init_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    ("lbm_init_fields_ex", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_step_profiled", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     ("lbm_macro", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -100,10 +102,10 @@ SIGNATURES = [
     ("lbm_sg_to_bf16", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, _VP]),
     ("lbm_sg_add", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
                                   ctypes.c_int, _VP]),
-    ("lbm_sg_pool", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
-    ("lbm_sg_pool_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
-    ("lbm_sg_upsample", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
-    ("lbm_sg_upsample_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 4 + [_VP]),
+    ("lbm_sg_pool", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
+    ("lbm_sg_pool_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
+    ("lbm_sg_upsample", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
+    ("lbm_sg_upsample_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
     ("lbm_sg_mse", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP,
                                   ctypes.c_longlong, ctypes.c_int, _VP]),
     ("lbm_sg_adam", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
@@ -279,11 +281,16 @@ class Simulation:
         self.close()
 
     # -- C-ABI calls
-    def init_fields(self, phi, u, P):
+    def init_fields(self, phi, u, P, nonequilibrium=False):
+        """Populations from (phi, u, P); with nonequilibrium, g also carries
+        the Chapman-Enskog non-equilibrium part (lbm_init_fields_ex)."""
         (pp, d0), (pu, d1), (pP, d2) = _ptr(phi), _ptr(u), _ptr(P)
         if not (d0 == d1 == d2):
             raise ValueError("phi, u and P must all be host or all device")
-        _check(load().lbm_init_fields(self._ctx, pp, pu, pP, d0), "lbm_init_fields")
+        if nonequilibrium:
+            _check(load().lbm_init_fields_ex(self._ctx, pp, pu, pP, d0, INIT_NONEQ), "lbm_init_fields_ex")
+        else:
+            _check(load().lbm_init_fields(self._ctx, pp, pu, pP, d0), "lbm_init_fields")
 
     def step(self, n=1):
         _check(load().lbm_step(self._ctx, int(n)), "lbm_step")

@@ -1,22 +1,23 @@
-"""Learned warm-start surrogate: a small periodic conv U-Net trained and run on
-the library's own BF16 tensor-core kernels (include/lbm_surrogate.h).
+"""Learned warm-start surrogate: a periodic convolutional U-Net of four levels
+(32 to 128 channels) trained and run on the library's own BF16 tensor-core
+kernels (include/lbm_surrogate.h).
 
 Every operation of the forward pass, the backward pass and the Adam update is
 one lbm_sg_* kernel launched through the C-ABI; PyTorch only provides device
 memory (allocation and zero-fill) and the stream.
 
-Network (channels; all convolutions periodic 3x3, every channel count padded
-to a multiple of 16 with zero weights that stay zero):
-  e1   conv 4 -> 16, ReLU              full resolution: x1
-  pool 8 x 8 average
-  c1   conv 16 -> 32, ReLU             coarse grid
-  c2   conv 32 -> 32, ReLU
-  c3   conv 32 -> 32, ReLU
-  c4   conv 32 -> 16, ReLU
-  up   8 x nearest, concatenated after x1 (32 channels)
-  d1   conv 32 -> 16, ReLU
-  d2   conv 16 -> 4                    delta
-  out  = in + delta, in = (phi, ux, uy, P) / scale
+Network (all convolutions periodic 3x3; grids H, H/2, H/4, H/8 with H and W
+multiples of 8; every channel count padded to a multiple of 16 with zero
+weights that stay zero):
+  e1   conv 4 -> 32, ReLU                      level 1: s1   (cat1[:, :32])
+  pool 2x2, e2 conv 32 -> 64, ReLU             level 2: s2   (cat2[:, :64])
+  pool 2x2, e3 conv 64 -> 128, ReLU            level 3: s3   (cat3[:, :128])
+  pool 2x2, b  conv 128 -> 128, ReLU           level 4
+  up x2 into cat3[:, 128:], d3 conv 256 -> 64, ReLU    level 3
+  up x2 into cat2[:, 64:],  d2 conv 128 -> 32, ReLU    level 2
+  up x2 into cat1[:, 32:],  d1 conv 64 -> 32, ReLU     level 1
+  out  conv 32 -> 4                            delta
+  result = in + delta, in = (phi, rho u_x, rho u_y, P) / scale
 """
 import ctypes
 
@@ -24,10 +25,12 @@ import numpy as np
 
 from . import lbm as L
 
-LAYERS = [("e1", 4, 16), ("c1", 16, 32), ("c2", 32, 32), ("c3", 32, 32), ("c4", 32, 16),
-          ("d1", 32, 16), ("d2", 16, 4)]
-POOL = 8
-NC = 4   # real channels of the input and output: phi, ux, uy, P
+LAYERS = [("e1", 4, 32), ("e2", 32, 64), ("e3", 64, 128), ("b", 128, 128),
+          ("d3", 256, 64), ("d2", 128, 32), ("d1", 64, 32), ("out", 32, 4)]
+POOL = 2      # pooling / upsampling factor between levels
+LEVELS = 4
+NC = 4        # real channels of the input and output: phi, rho u_x, rho u_y, P
+CO_MAX = 128  # output channels one lbm_sg_conv3x3 call produces at most
 
 
 def _pad16(c):
@@ -40,7 +43,7 @@ def init_params(seed=0):
     rng = np.random.default_rng(seed)
     params = {}
     for name, ci, co in LAYERS:
-        std = np.sqrt(2.0 / (ci * 9)) * (0.1 if name == "d2" else 1.0)
+        std = np.sqrt(2.0 / (ci * 9)) * (0.1 if name == "out" else 1.0)
         params[name + ".W"] = rng.normal(0.0, std, size=(co, ci, 3, 3))
         params[name + ".b"] = np.zeros(co)
     return params
@@ -48,6 +51,11 @@ def init_params(seed=0):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _off(t, channels):
+    """Address of channel `channels` of the first pixel of a channels-last tensor."""
+    return ctypes.c_void_p(t.data_ptr() + channels * t.element_size())
 
 
 def _ck(rc, what):
@@ -63,11 +71,12 @@ class Surrogate:
         import torch
         self.torch = torch
         self.lib = L.load()
-        if H % POOL or W % POOL or (N * H * W // (POOL * POOL)) % 16:
+        f = POOL ** (LEVELS - 1)
+        if H % f or W % f or (N * H * W // (f * f)) % 16:
             raise ValueError("H, W multiples of 8 and N H W / 64 a multiple of 16")
         self.N, self.H, self.W = N, H, W
-        self.M = N * H * W
-        self.Mc = self.M // (POOL * POOL)
+        self.M = [N * H * W // (POOL ** (2 * l)) for l in range(LEVELS)]   # pixels per level
+        self.HW = [(H // POOL ** l, W // POOL ** l) for l in range(LEVELS)]
         self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         dev = "cuda"
         f32, b16 = torch.float32, torch.bfloat16
@@ -80,23 +89,33 @@ class Surrogate:
                                      mW=z(cop, 9, cip), vW=z(cop, 9, cip), mb=z(cop), vb=z(cop),
                                      gW=z(cop, 9, cip), gb=z(cop))
         self.set_params(params if params is not None else init_params(seed))
-        M, Mc = self.M, self.Mc
-        self.x16, self.x32 = z(M, 16, dt=b16), z(M, NC)
-        self.a_e1, self.cat16 = z(M, 16), z(M, 32, dt=b16)
-        self.p16 = z(Mc, 16, dt=b16)
-        self.a_c, self.h_c = {}, {}
-        for name in ("c1", "c2", "c3", "c4"):
-            co = self.layers[name]["cop"]
-            self.a_c[name], self.h_c[name] = z(Mc, co), z(Mc, co, dt=b16)
-        self.a_d1, self.hd = z(M, 16), z(M, 16, dt=b16)
-        self.delta = z(M, 16)
-        # backward buffers
-        self.g_delta, self.g16 = z(M, 32), z(M, 32, dt=b16)
-        self.gf_full, self.ga_full = z(M, 32), z(M, 32)
-        self.gf_c, self.ga_c, self.ga16_c = z(Mc, 32), z(Mc, 32), z(Mc, 32, dt=b16)
-        self.g_pool, self.g_x1 = z(M, 16), z(M, 16)
-        scratch = max(self.lib.lbm_sg_wgrad_scratch_floats(N, H, W, 32, 32),
-                      self.lib.lbm_sg_wgrad_scratch_floats(N, H // POOL, W // POOL, 32, 32), 64 * 32)
+        M1, M2, M3, M4 = self.M
+        # forward activations: pre-activations (FP32) for the ReLU backward,
+        # post-activations (bf16) as the next layer's input
+        self.x16, self.x32 = z(M1, 16, dt=b16), z(M1, NC)
+        self.a = {"e1": z(M1, 32), "e2": z(M2, 64), "e3": z(M3, 128), "b": z(M4, 128),
+                  "d3": z(M3, 64), "d2": z(M2, 32), "d1": z(M1, 32)}
+        self.cat1, self.cat2, self.cat3 = z(M1, 64, dt=b16), z(M2, 128, dt=b16), z(M3, 256, dt=b16)
+        self.p1, self.p2, self.p3 = z(M2, 32, dt=b16), z(M3, 64, dt=b16), z(M4, 128, dt=b16)
+        self.hb, self.h3, self.h2, self.h1 = z(M4, 128, dt=b16), z(M3, 64, dt=b16), z(M2, 32, dt=b16), z(M1, 32, dt=b16)
+        self.delta = z(M1, 16)
+        # backward buffers (FP32 gradients and their bf16 copies per level)
+        self.g_delta, self.g16_1 = z(M1, 16), z(M1, 64, dt=b16)
+        self.gc1, self.gs1, self.ga1 = z(M1, 64), z(M1, 32), z(M1, 32)
+        self.gc2, self.gs2, self.ga2, self.g16_2 = z(M2, 128), z(M2, 64), z(M2, 64), z(M2, 64, dt=b16)
+        self.gc3, self.gs3, self.ga3, self.g16_3 = z(M3, 256), z(M3, 128), z(M3, 128), z(M3, 128, dt=b16)
+        self.gt2, self.gt3 = z(M2, 32), z(M3, 64)
+        self.ghb, self.ga4, self.g16_4, self.gp3 = z(M4, 128), z(M4, 128), z(M4, 128, dt=b16), z(M4, 128)
+        self.gp2, self.gp1, self.gpool = z(M3, 64), z(M2, 32), z(M1, 32)
+        lib = self.lib
+        scratch = max(lib.lbm_sg_wgrad_scratch_floats(N, H, W, 64, 32),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H, W, 16, 32),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H, W, 32, 16),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H // 2, W // 2, 128, 32),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H // 2, W // 2, 32, 64),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H // 4, W // 4, 256, 64),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H // 4, W // 4, 64, 128),
+                      lib.lbm_sg_wgrad_scratch_floats(N, H // 8, W // 8, 128, 128), 64 * 256)
         self.scratch = z(int(scratch))
         self.mse_scratch = torch.zeros(256, dtype=torch.float64, device=dev)
         self.loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -148,95 +167,152 @@ class Surrogate:
             out[name + ".b"] = ly["gb"].cpu().numpy().astype(np.float64)[:co]
         return out
 
-    # ---------------------------------------------------------------- passes
-    def _conv(self, name, x, csx, y, csy, N, H, W, flip=False):
+    # ---------------------------------------------------------------- primitives
+    def _conv(self, name, x, csx, y, csy, level):
         ly = self.layers[name]
-        if flip:   # input gradient: Ci and Co exchanged, no bias
-            _ck(self.lib.lbm_sg_conv3x3(x, csx, _ptr(ly["Wt"]), None, y, csy, N, H, W, ly["cop"], ly["cip"],
-                                        self.stream), "lbm_sg_conv3x3")
-        else:
-            _ck(self.lib.lbm_sg_conv3x3(x, csx, _ptr(ly["W16"]), _ptr(ly["b"]), y, csy, N, H, W, ly["cip"],
-                                        ly["cop"], self.stream), "lbm_sg_conv3x3")
+        h, w = self.HW[level]
+        _ck(self.lib.lbm_sg_conv3x3(x, csx, _ptr(ly["W16"]), _ptr(ly["b"]), y, csy, self.N, h, w, ly["cip"],
+                                    ly["cop"], self.stream), "lbm_sg_conv3x3")
 
+    def _conv_input_grad(self, name, g16, csg, gx, csx, level):
+        """gx = gradient w.r.t. the layer's input: the convolution of g with the
+        flipped weights, in slices of at most CO_MAX output channels."""
+        ly = self.layers[name]
+        h, w = self.HW[level]
+        cip, cop = ly["cip"], ly["cop"]
+        for c0 in range(0, cip, CO_MAX):
+            nco = min(CO_MAX, cip - c0)
+            wt = ctypes.c_void_p(ly["Wt"].data_ptr() + c0 * 9 * cop * 2)
+            out = ctypes.c_void_p(gx.data_ptr() + c0 * 4)
+            _ck(self.lib.lbm_sg_conv3x3(g16, csg, wt, None, out, csx, self.N, h, w, cop, nco, self.stream),
+                "lbm_sg_conv3x3")
+
+    def _wgrad(self, name, x, csx, g16, csg, level):
+        ly = self.layers[name]
+        h, w = self.HW[level]
+        _ck(self.lib.lbm_sg_conv3x3_wgrad(x, csx, g16, csg, _ptr(ly["gW"]), _ptr(self.scratch), self.scratch.numel(),
+                                          self.N, h, w, ly["cip"], ly["cop"], self.stream), "lbm_sg_conv3x3_wgrad")
+
+    def _bgrad(self, name, g, csg, level):
+        ly = self.layers[name]
+        _ck(self.lib.lbm_sg_bias_grad(g, csg, _ptr(ly["gb"]), _ptr(self.scratch), self.M[level], ly["cop"],
+                                      self.stream), "lbm_sg_bias_grad")
+
+    def _relu(self, a, csa, y, csy, level, C):
+        _ck(self.lib.lbm_sg_relu(a, csa, y, csy, self.M[level], C, self.stream), "lbm_sg_relu")
+
+    def _pool(self, x, csx, y, csy, level_fine, C):
+        h, w = self.HW[level_fine]
+        _ck(self.lib.lbm_sg_pool(x, csx, y, csy, self.N, h, w, C, POOL, self.stream), "lbm_sg_pool")
+
+    def _up(self, x, csx, y, csy, level_fine, C):
+        h, w = self.HW[level_fine]
+        _ck(self.lib.lbm_sg_upsample(x, csx, y, csy, self.N, h, w, C, POOL, self.stream), "lbm_sg_upsample")
+
+    def _up_bwd(self, g, csg, gx, csx, level_fine, C):
+        h, w = self.HW[level_fine]
+        _ck(self.lib.lbm_sg_upsample_bwd(g, csg, gx, csx, self.N, h, w, C, POOL, self.stream), "lbm_sg_upsample_bwd")
+
+    def _pool_bwd(self, g, csg, gx, csx, level_fine, C):
+        h, w = self.HW[level_fine]
+        _ck(self.lib.lbm_sg_pool_bwd(g, csg, gx, csx, self.N, h, w, C, POOL, self.stream), "lbm_sg_pool_bwd")
+
+    def _relu_bwd(self, g, csg, a, csa, ga, ga16, level, C):
+        _ck(self.lib.lbm_sg_relu_bwd(g, csg, a, csa, ga, ga16, self.M[level], C, self.stream), "lbm_sg_relu_bwd")
+
+    def _add(self, a, csa, b, csb, out, cso, level, C):
+        _ck(self.lib.lbm_sg_add(a, csa, b, csb, out, cso, self.M[level], C, self.stream), "lbm_sg_add")
+
+    # ---------------------------------------------------------------- passes
     def set_input(self, x32):
         """x32: (M, 4) float32 device tensor of normalised inputs; builds the
         padded bf16 copy."""
         self.x32.copy_(x32)
-        _ck(self.lib.lbm_sg_to_bf16(_ptr(self.x32), NC, _ptr(self.x16), 16, self.M, NC, self.stream),
+        _ck(self.lib.lbm_sg_to_bf16(_ptr(self.x32), NC, _ptr(self.x16), 16, self.M[0], NC, self.stream),
             "lbm_sg_to_bf16")
 
     def forward(self):
         """delta (M, 16) float32 for the current input; out = input + delta[:, :4]."""
-        lib, s, N, H, W = self.lib, self.stream, self.N, self.H, self.W
-        Hc, Wc = H // POOL, W // POOL
-        M, Mc = self.M, self.Mc
-        p = _ptr
-        self._conv("e1", p(self.x16), 16, p(self.a_e1), 16, N, H, W)
-        _ck(lib.lbm_sg_relu(p(self.a_e1), 16, p(self.cat16), 32, M, 16, s), "relu")            # x1 -> cat[:, :16]
-        _ck(lib.lbm_sg_pool(p(self.cat16), 32, p(self.p16), 16, N, H, W, 16, s), "pool")
-        h, ch = self.p16, 16
-        for name in ("c1", "c2", "c3", "c4"):
-            co = self.layers[name]["cop"]
-            self._conv(name, p(h), ch, p(self.a_c[name]), co, N, Hc, Wc)
-            _ck(lib.lbm_sg_relu(p(self.a_c[name]), co, p(self.h_c[name]), co, Mc, co, s), "relu")
-            h, ch = self.h_c[name], co
-        up = ctypes.c_void_p(self.cat16.data_ptr() + 16 * 2)                                    # cat[:, 16:]
-        _ck(lib.lbm_sg_upsample(p(h), 16, up, 32, N, H, W, 16, s), "upsample")
-        self._conv("d1", p(self.cat16), 32, p(self.a_d1), 16, N, H, W)
-        _ck(lib.lbm_sg_relu(p(self.a_d1), 16, p(self.hd), 16, M, 16, s), "relu")
-        self._conv("d2", p(self.hd), 16, p(self.delta), 16, N, H, W)
+        p, a = _ptr, self.a
+        self._conv("e1", p(self.x16), 16, p(a["e1"]), 32, 0)
+        self._relu(p(a["e1"]), 32, p(self.cat1), 64, 0, 32)                 # s1 -> cat1[:, :32]
+        self._pool(p(self.cat1), 64, p(self.p1), 32, 0, 32)
+        self._conv("e2", p(self.p1), 32, p(a["e2"]), 64, 1)
+        self._relu(p(a["e2"]), 64, p(self.cat2), 128, 1, 64)                # s2 -> cat2[:, :64]
+        self._pool(p(self.cat2), 128, p(self.p2), 64, 1, 64)
+        self._conv("e3", p(self.p2), 64, p(a["e3"]), 128, 2)
+        self._relu(p(a["e3"]), 128, p(self.cat3), 256, 2, 128)              # s3 -> cat3[:, :128]
+        self._pool(p(self.cat3), 256, p(self.p3), 128, 2, 128)
+        self._conv("b", p(self.p3), 128, p(a["b"]), 128, 3)
+        self._relu(p(a["b"]), 128, p(self.hb), 128, 3, 128)
+        self._up(p(self.hb), 128, _off(self.cat3, 128), 256, 2, 128)        # cat3[:, 128:]
+        self._conv("d3", p(self.cat3), 256, p(a["d3"]), 64, 2)
+        self._relu(p(a["d3"]), 64, p(self.h3), 64, 2, 64)
+        self._up(p(self.h3), 64, _off(self.cat2, 64), 128, 1, 64)          # cat2[:, 64:]
+        self._conv("d2", p(self.cat2), 128, p(a["d2"]), 32, 1)
+        self._relu(p(a["d2"]), 32, p(self.h2), 32, 1, 32)
+        self._up(p(self.h2), 32, _off(self.cat1, 32), 64, 0, 32)           # cat1[:, 32:]
+        self._conv("d1", p(self.cat1), 64, p(a["d1"]), 32, 0)
+        self._relu(p(a["d1"]), 32, p(self.h1), 32, 0, 32)
+        self._conv("out", p(self.h1), 32, p(self.delta), 16, 0)
         return self.delta
-
-    def _wgrad(self, name, x, csx, gy16, csg, N, H, W):
-        ly = self.layers[name]
-        _ck(self.lib.lbm_sg_conv3x3_wgrad(x, csx, gy16, csg, _ptr(ly["gW"]), _ptr(self.scratch), self.scratch.numel(),
-                                          N, H, W, ly["cip"], ly["cop"], self.stream), "lbm_sg_conv3x3_wgrad")
-
-    def _bgrad(self, name, g, csg, npix):
-        ly = self.layers[name]
-        _ck(self.lib.lbm_sg_bias_grad(g, csg, _ptr(ly["gb"]), _ptr(self.scratch), npix, ly["cop"], self.stream),
-            "lbm_sg_bias_grad")
 
     def backward(self, target32):
         """Loss (device FP64 scalar) and gradients of the MSE of out against
         target32 ((M, 4) float32)."""
-        lib, s, N, H, W = self.lib, self.stream, self.N, self.H, self.W
-        Hc, Wc = H // POOL, W // POOL
-        M, Mc = self.M, self.Mc
-        p = _ptr
+        lib, s = self.lib, self.stream
+        p, a = _ptr, self.a
+        M1 = self.M[0]
         _ck(lib.lbm_sg_mse(p(self.x32), NC, p(self.delta), 16, p(target32), NC, p(self.g_delta), p(self.mse_scratch),
-                           p(self.loss_dev), M, NC, s), "lbm_sg_mse")
-        _ck(lib.lbm_sg_to_bf16(p(self.g_delta), 16, p(self.g16), 16, M, 16, s), "to_bf16")
-        # d2
-        self._wgrad("d2", p(self.hd), 16, p(self.g16), 16, N, H, W)
-        self._bgrad("d2", p(self.g_delta), 16, M)
-        self._conv("d2", p(self.g16), 16, p(self.gf_full), 16, N, H, W, flip=True)      # g wrt hd
-        # d1
-        _ck(lib.lbm_sg_relu_bwd(p(self.gf_full), 16, p(self.a_d1), 16, p(self.ga_full), p(self.g16), M, 16, s), "relu_bwd")
-        self._wgrad("d1", p(self.cat16), 32, p(self.g16), 16, N, H, W)
-        self._bgrad("d1", p(self.ga_full), 16, M)
-        self._conv("d1", p(self.g16), 16, p(self.gf_full), 32, N, H, W, flip=True)      # g wrt cat (32 ch)
-        # coarse path: upsample backward of cat[:, 16:]
-        g_up = ctypes.c_void_p(self.gf_full.data_ptr() + 16 * 4)
-        _ck(lib.lbm_sg_upsample_bwd(g_up, 32, p(self.gf_c), 16, N, H, W, 16, s), "upsample_bwd")
-        gin, cin = self.gf_c, 16
-        prev = {"c4": "c3", "c3": "c2", "c2": "c1", "c1": None}
-        for name in ("c4", "c3", "c2", "c1"):
-            ly = self.layers[name]
-            co, ci = ly["cop"], ly["cip"]
-            _ck(lib.lbm_sg_relu_bwd(p(gin), cin, p(self.a_c[name]), co, p(self.ga_c), p(self.ga16_c), Mc, co, s),
-                "relu_bwd")
-            xin = self.h_c[prev[name]] if prev[name] else self.p16
-            self._wgrad(name, p(xin), ci, p(self.ga16_c), co, N, Hc, Wc)
-            self._bgrad(name, p(self.ga_c), co, Mc)
-            self._conv(name, p(self.ga16_c), co, p(self.gf_c), ci, N, Hc, Wc, flip=True)
-            gin, cin = self.gf_c, ci
-        # x1 receives the pooled path and the skip
-        _ck(lib.lbm_sg_pool_bwd(p(gin), 16, p(self.g_pool), 16, N, H, W, 16, s), "pool_bwd")
-        _ck(lib.lbm_sg_add(p(self.gf_full), 32, p(self.g_pool), 16, p(self.g_x1), 16, M, 16, s), "add")
-        _ck(lib.lbm_sg_relu_bwd(p(self.g_x1), 16, p(self.a_e1), 16, p(self.ga_full), p(self.g16), M, 16, s), "relu_bwd")
-        self._wgrad("e1", p(self.x16), 16, p(self.g16), 16, N, H, W)
-        self._bgrad("e1", p(self.ga_full), 16, M)
+                           p(self.loss_dev), M1, NC, s), "lbm_sg_mse")
+        _ck(lib.lbm_sg_to_bf16(p(self.g_delta), 16, p(self.g16_1), 16, M1, 16, s), "lbm_sg_to_bf16")
+        # out: input gradient -> gt1 (FP32, 32 channels, reusing gs1)
+        self._wgrad("out", p(self.h1), 32, p(self.g16_1), 16, 0)
+        self._bgrad("out", p(self.g_delta), 16, 0)
+        self._conv_input_grad("out", p(self.g16_1), 16, self.gs1, 32, 0)
+        # d1 (level 1): d cat1
+        self._relu_bwd(p(self.gs1), 32, p(a["d1"]), 32, p(self.ga1), p(self.g16_1), 0, 32)
+        self._wgrad("d1", p(self.cat1), 64, p(self.g16_1), 32, 0)
+        self._bgrad("d1", p(self.ga1), 32, 0)
+        self._conv_input_grad("d1", p(self.g16_1), 32, self.gc1, 64, 0)
+        self._up_bwd(_off(self.gc1, 32), 64, p(self.gt2), 32, 0, 32)       # -> d h2 (level 2)
+        # d2 (level 2): d cat2
+        self._relu_bwd(p(self.gt2), 32, p(a["d2"]), 32, p(self.ga2), p(self.g16_2), 1, 32)
+        self._wgrad("d2", p(self.cat2), 128, p(self.g16_2), 32, 1)
+        self._bgrad("d2", p(self.ga2), 32, 1)
+        self._conv_input_grad("d2", p(self.g16_2), 32, self.gc2, 128, 1)
+        self._up_bwd(_off(self.gc2, 64), 128, p(self.gt3), 64, 1, 64)      # -> d h3 (level 3)
+        # d3 (level 3): d cat3
+        self._relu_bwd(p(self.gt3), 64, p(a["d3"]), 64, p(self.ga3), p(self.g16_3), 2, 64)
+        self._wgrad("d3", p(self.cat3), 256, p(self.g16_3), 64, 2)
+        self._bgrad("d3", p(self.ga3), 64, 2)
+        self._conv_input_grad("d3", p(self.g16_3), 64, self.gc3, 256, 2)
+        self._up_bwd(_off(self.gc3, 128), 256, p(self.ghb), 128, 2, 128)   # -> d hb (level 4)
+        # b (level 4)
+        self._relu_bwd(p(self.ghb), 128, p(a["b"]), 128, p(self.ga4), p(self.g16_4), 3, 128)
+        self._wgrad("b", p(self.p3), 128, p(self.g16_4), 128, 3)
+        self._bgrad("b", p(self.ga4), 128, 3)
+        self._conv_input_grad("b", p(self.g16_4), 128, self.gp3, 128, 3)
+        # s3 receives the skip (gc3[:, :128]) and the pooled path
+        self._pool_bwd(p(self.gp3), 128, p(self.ga3), 128, 2, 128)
+        self._add(p(self.gc3), 256, p(self.ga3), 128, p(self.gs3), 128, 2, 128)
+        self._relu_bwd(p(self.gs3), 128, p(a["e3"]), 128, p(self.ga3), p(self.g16_3), 2, 128)
+        self._wgrad("e3", p(self.p2), 64, p(self.g16_3), 128, 2)
+        self._bgrad("e3", p(self.ga3), 128, 2)
+        self._conv_input_grad("e3", p(self.g16_3), 128, self.gp2, 64, 2)
+        # s2
+        self._pool_bwd(p(self.gp2), 64, p(self.ga2), 64, 1, 64)
+        self._add(p(self.gc2), 128, p(self.ga2), 64, p(self.gs2), 64, 1, 64)
+        self._relu_bwd(p(self.gs2), 64, p(a["e2"]), 64, p(self.ga2), p(self.g16_2), 1, 64)
+        self._wgrad("e2", p(self.p1), 32, p(self.g16_2), 64, 1)
+        self._bgrad("e2", p(self.ga2), 64, 1)
+        self._conv_input_grad("e2", p(self.g16_2), 64, self.gp1, 32, 1)
+        # s1
+        self._pool_bwd(p(self.gp1), 32, p(self.gpool), 32, 0, 32)
+        self._add(p(self.gc1), 64, p(self.gpool), 32, p(self.gs1), 32, 0, 32)
+        self._relu_bwd(p(self.gs1), 32, p(a["e1"]), 32, p(self.ga1), p(self.g16_1), 0, 32)
+        self._wgrad("e1", p(self.x16), 16, p(self.g16_1), 32, 0)
+        self._bgrad("e1", p(self.ga1), 32, 0)
         return self.loss_dev
 
     def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
@@ -255,3 +331,16 @@ class Surrogate:
         loss = self.backward(target32)
         self.adam(lr)
         return loss
+
+    def flops_per_image(self, backward=True):
+        """Multiply-add FLOPs of the convolutions of one image (padded channel
+        counts, as the kernels compute them): forward, and with `backward` the
+        input- and weight-gradient convolutions too."""
+        level = {"e1": 0, "e2": 1, "e3": 2, "b": 3, "d3": 2, "d2": 1, "d1": 0, "out": 0}
+        tot = 0
+        for name, _, _ in LAYERS:
+            ly = self.layers[name]
+            h, w = self.HW[level[name]]
+            fwd = 2 * h * w * 9 * ly["cip"] * ly["cop"]
+            tot += fwd * (3 if backward else 1)
+        return tot

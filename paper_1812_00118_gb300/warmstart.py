@@ -1,14 +1,18 @@
 """Learned warm start of the phase-field LB solver, and time-to-tolerance.
 
-A static-drop state relaxes slowly from its initial fields: starting from
-u = 0, P = 0 the Laplace pressure jump builds up as acoustic waves that the
-viscosity damps over tens of thousands of steps.  The surrogate
-(paper_1812_00118_gb300.surrogate) is trained on pairs the solver itself
-generates -- the initial fields (phi0, 0, 0) and the pressure field T steps
-later -- and its prediction replaces the initial pressure: populations are
-rebuilt as equilibria of (phi0, 0, P_predicted) (lbm_init_fields), so phi
-and its total are exactly those of the plain start.  The plain solver then continues and
-decides convergence, so the method stays the judge and the fallback.
+A state of drops and bubbles relaxes slowly from its initial fields:
+starting from u = 0, P = 0 the Laplace pressure jumps build up as acoustic
+waves that the viscosity damps over tens of thousands of steps.  The
+surrogate (paper_1812_00118_gb300.surrogate, a four-level U-Net) learns the
+map of the state (phi, rho u, P) over DT = 2000 steps from snapshot pairs
+the solver itself generates (1-4 drops or bubbles, radii 12-48, density
+ratio 1000).  At inference it is applied k times to the initial fields,
+jumping k DT steps ahead towards the end of the transient; the populations
+are rebuilt from the prediction as equilibria plus the filtered
+non-equilibrium part (lbm_init_fields_ex, LBM_INIT_NONEQ), with the total
+of phi re-imposed exactly (FP64 sum on the GPU, uniform shift).  The plain
+solver then continues and decides convergence, so the method stays the
+judge and the fallback.
 
 Convergence (time-to-tolerance): every `check_every` steps the pressure
 field P(t) is compared with P(t - check_every); the run has converged when
@@ -27,21 +31,26 @@ from . import lbm as L
 from .surrogate import NC, _ck, _ptr
 
 # normalisation of (phi, rho u_x, rho u_y, P) for the network: spurious
-# currents are ~1e-5, Laplace jumps sigma / R ~ 4e-4 - 1e-3
+# currents are ~1e-5, Laplace jumps sigma / R ~ 2e-4 - 1e-3
 SCALE = (1.0, 1e-5, 1e-5, 2e-4)
-# the warm-start workload: drops at density ratio 1000, water-like viscosity
-# of the paper's shear and Galilean tests (nu = 1.7e-2)
+# the warm-start workload: drops and bubbles at density ratio 1000, the
+# water-like viscosity of the paper's shear and Galilean tests
 PHYS = dict(M=0.1, W=4.0, sigma=0.01, rho_L=1e-3, rho_H=1.0, nu_L=1.0 / 60.0, nu_H=1.0 / 60.0)
-RADII = (12.0, 28.0)
+RADII = (12.0, 48.0)
+DT = 2000          # steps between the snapshots of a training pair
 
 
 def case_params(store=L.F32):
     return L.make_params(store=store, g_scale=(1e3 if store == L.F16S else 0.0), **PHYS)
 
 
-def case_fields(Lsz, seed, R_min=RADII[0], R_max=RADII[1]):
-    # drops three interface widths apart: static, no coalescence
-    phi, u, P, placed = I.drops(Lsz, seed, R_min=R_min, R_max=R_max, W=PHYS["W"], gap=3.0 * PHYS["W"])
+def case_fields(Lsz, seed, R_min=RADII[0], R_max=RADII[1], bubbles=None):
+    """phi (flat) of case `seed`: 1-4 drops, or (odd seeds) 1-4 bubbles,
+    three interface widths apart (static, no coalescence); and their
+    (x, y, R)."""
+    b = (seed % 2 == 1) if bubbles is None else bubbles
+    R_max = min(R_max, Lsz / 4.0)
+    phi, u, P, placed = I.drops(Lsz, seed, R_min=R_min, R_max=R_max, W=PHYS["W"], gap=3.0 * PHYS["W"], bubbles=b)
     return phi.reshape(-1).copy(), placed
 
 
@@ -67,96 +76,121 @@ def pack(lib, f, x32, x16, stream):
                         ctypes.c_void_p(x32), NC, ctypes.c_void_p(x16), 16, n, stream), "lbm_sg_pack")
 
 
-def generate_pairs(torch, Lsz, seeds, T, store=L.F32, max_u=0.05):
-    """Training pairs from the batched solver: inputs (phi0, 0, 0) and the
-    state after T steps, normalised; returns (X, Y), each (n, L*L, 4)
-    float32 on the device, and the number of cases left out because their
-    run did not stay bounded (non-finite fields or |u| > max_u)."""
+def generate_snapshots(torch, Lsz, seeds, K, dt=DT, store=L.F32, max_u=0.05, chunk=256):
+    """Trajectories of the batched solver: for every case the normalised
+    state at t = 0, dt, ..., K dt as an (n, K + 1, L*L, 4) float32 device
+    tensor; cases whose run does not stay bounded (non-finite fields or
+    |u| > max_u at some snapshot) are left out.  Returns (S, n_left_out).
+    Cases run `chunk` at a time as one batch."""
     lib = L.load()
-    n, npix = len(seeds), Lsz * Lsz
+    npix = Lsz * Lsz
     prm = case_params(store)
-    batch = L.Batch([(Lsz, Lsz)] * n, prm)
-    X = torch.zeros(n, npix, NC, dtype=torch.float32, device="cuda")
-    Y = torch.zeros(n, npix, NC, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
     tmp16 = torch.zeros(npix, 16, dtype=torch.bfloat16, device="cuda")
     f = DeviceFields(torch, npix)
-    stream = torch.cuda.current_stream().cuda_stream
-    for k, sd in enumerate(seeds):
-        phi0, _ = case_fields(Lsz, sd)
-        f.phi.copy_(torch.from_numpy(phi0))
-        for t in (f.P, f.ru, f.u):
-            t.zero_()
-        batch.grid(k).init_fields(f.phi, f.u, f.P)
-        pack(lib, f, X[k].data_ptr(), tmp16.data_ptr(), stream)
-    batch.step(T)
-    keep = []
-    for k in range(n):
-        d = batch.grid(k).diagnostics(raise_on_divergence=False)
-        if d["nonfinite"] > 0 or not d["max_u"] < max_u:
-            continue
-        batch.grid(k).macro(f.phi, f.P, f.ru)
-        pack(lib, f, Y[k].data_ptr(), tmp16.data_ptr(), stream)
-        keep.append(k)
-    torch.cuda.synchronize()
-    batch.close()
-    idx = torch.tensor(keep, dtype=torch.long, device="cuda")
-    X, Y = X.index_select(0, idx), Y.index_select(0, idx)
-    # the network predicts the pressure only: phi and u of the warm start stay
-    # the initial ones (u = 0).  The residual flows of the relaxing state are
-    # not a function of the initial fields, and a wrong velocity field feeds
-    # instabilities of the restarted run.
-    Y[:, :, :3].copy_(X[:, :, :3])
-    return X, Y, n - len(keep)
+    kept = []
+    dropped = 0
+    for c0 in range(0, len(seeds), chunk):
+        part = seeds[c0:c0 + chunk]
+        n = len(part)
+        S = torch.zeros(n, K + 1, npix, NC, dtype=torch.float32, device="cuda")
+        batch = L.Batch([(Lsz, Lsz)] * n, prm, stream=stream)
+        for k, sd in enumerate(part):
+            phi0, _ = case_fields(Lsz, sd)
+            f.phi.copy_(torch.from_numpy(phi0))
+            for t in (f.P, f.ru, f.u):
+                t.zero_()
+            batch.grid(k).init_fields(f.phi, f.u, f.P)
+        ok = [True] * n
+
+        def record(j):
+            for k in range(n):
+                if not ok[k]:
+                    continue
+                d = batch.grid(k).diagnostics(raise_on_divergence=False)
+                if d["nonfinite"] > 0 or not d["max_u"] < max_u:
+                    ok[k] = False
+                    continue
+                batch.grid(k).macro(f.phi, f.P, f.ru)
+                pack(lib, f, S[k, j].data_ptr(), tmp16.data_ptr(), stream)
+
+        record(0)
+        for j in range(1, K + 1):
+            batch.step(dt)
+            record(j)
+        torch.cuda.synchronize()
+        batch.close()
+        idx = [k for k in range(n) if ok[k]]
+        dropped += n - len(idx)
+        if idx:
+            kept.append(S.index_select(0, torch.tensor(idx, dtype=torch.long, device="cuda")))
+        del S
+    return torch.cat(kept, 0), dropped
 
 
-def train(torch, sg, X, Y, iters, lr=2e-3, seed=0, log_every=100, decay_at=0.7):
-    """Adam on random mini-batches of sg.N images (indices drawn on the host);
-    the learning rate drops tenfold after decay_at of the iterations.
-    Returns [(iteration, loss)]."""
+def train(torch, sg, S, iters, lr=1e-3, seed=0, log_every=100, decay_at=0.7):
+    """Adam on random mini-batches of sg.N pairs (snapshot k of a case as
+    input, snapshot k + 1 as target; indices drawn on the host); the learning
+    rate drops tenfold after decay_at of the iterations.  Returns
+    [(iteration, loss)]."""
     rng = np.random.default_rng(seed)
-    n, npix = X.shape[0], X.shape[1]
+    n, K1, npix = S.shape[0], S.shape[1], S.shape[2]
     xb = torch.zeros(sg.N * npix, NC, dtype=torch.float32, device="cuda")
     yb = torch.zeros_like(xb)
     hist = []
     for it in range(iters):
-        idx = rng.choice(n, size=sg.N, replace=n < sg.N)
-        for j, k in enumerate(idx):   # gather the mini-batch (device copies)
-            xb[j * npix:(j + 1) * npix].copy_(X[int(k)])
-            yb[j * npix:(j + 1) * npix].copy_(Y[int(k)])
+        cs = rng.integers(0, n, size=sg.N)
+        ks = rng.integers(0, K1 - 1, size=sg.N)
+        for j, (c, k) in enumerate(zip(cs, ks)):   # gather the mini-batch (device copies)
+            xb[j * npix:(j + 1) * npix].copy_(S[int(c), int(k)])
+            yb[j * npix:(j + 1) * npix].copy_(S[int(c), int(k) + 1])
         loss = sg.train_step(xb, yb, lr=lr if it < decay_at * iters else 0.1 * lr)
         if it % log_every == 0 or it == iters - 1:
             hist.append((it, float(loss.item())))
     return hist
 
 
-def predict_into(torch, sg1, sim, phi0_host, prm, smooth=3):
-    """Warm start: predict the pressure of (phi0, 0, 0) with a one-image
-    surrogate, smooth it (2 `smooth` diffusion passes of the block-scale
-    roughness of the coarse path), and initialise sim from (phi0, 0, P).
-    phi is phi0 itself, so its total is exactly that of the plain start; the
-    network's phi and rho u channels are not used (a phi a little below 0
-    in the light phase would make rho(phi) negative)."""
+def identity_loss(S):
+    """MSE of the map that keeps the state (the loss to beat)."""
+    return float(((S[:, 1:] - S[:, :-1]) ** 2).mean().item())
+
+
+def predict_into(torch, sg1, sim, phi0_host, prm, k_apply):
+    """Warm start: apply the one-image surrogate k_apply times to the initial
+    fields (phi0, 0, 0) -- a jump of k_apply DT steps --, re-impose the
+    initial total of phi (FP64 sum, uniform shift), and rebuild sim's
+    populations from the predicted (phi, u, P) as equilibria plus the
+    Chapman-Enskog non-equilibrium part.  Returns the predicted fields."""
     lib = L.load()
-    n = sg1.M
+    n = sg1.M[0]
     stream = torch.cuda.current_stream().cuda_stream
     f = DeviceFields(torch, n)
     f.phi.copy_(torch.from_numpy(phi0_host))
     tmp16 = torch.zeros(n, 16, dtype=torch.bfloat16, device="cuda")
     x32 = torch.zeros(n, NC, dtype=torch.float32, device="cuda")
+    x32n = torch.zeros_like(x32)
     pack(lib, f, x32.data_ptr(), tmp16.data_ptr(), stream)
-    sg1.set_input(x32)
-    delta = sg1.forward()
+    delta = None
+    for k in range(k_apply):
+        if delta is not None:   # x <- x + delta of the previous application
+            _ck(lib.lbm_sg_add(_ptr(x32), NC, _ptr(delta), 16, _ptr(x32n), NC, n, NC, stream), "lbm_sg_add")
+            x32, x32n = x32n, x32
+        sg1.set_input(x32)
+        delta = sg1.forward()
     u = f.u.data_ptr()
     rho_dif = prm.rho_H - prm.rho_L
-    _ck(lib.lbm_sg_unpack(_ptr(sg1.x32), NC, _ptr(delta), 16, _ptr(f.phi), ctypes.c_void_p(u),
+    if delta is None:
+        delta = torch.zeros(n, 16, dtype=torch.float32, device="cuda")
+    _ck(lib.lbm_sg_unpack(_ptr(x32), NC, _ptr(delta), 16, _ptr(f.phi), ctypes.c_void_p(u),
                           ctypes.c_void_p(u + 8 * n), _ptr(f.P), _scale_arr(), prm.rho_L, rho_dif, n, stream),
         "lbm_sg_unpack")
-    if smooth > 0:
-        tmp = torch.zeros(n, dtype=torch.float64, device="cuda")
-        _ck(lib.lbm_sg_smooth(_ptr(f.P), _ptr(tmp), 1, sg1.H, sg1.W, int(smooth), 0.2, stream), "lbm_sg_smooth")
-    f.phi.copy_(torch.from_numpy(phi0_host))
-    f.u.zero_()
-    sim.init_fields(f.phi, f.u, f.P)
+    # the total of phi of the start, restored exactly (Eq. 1 conserves it)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    L.field_sums_noalloc(f.phi, f.P, None, prm.rho_L, rho_dif, out, stream=stream)
+    shift = (float(phi0_host.sum()) - float(out[0].item())) / n
+    _ck(lib.lbm_sg_shift(_ptr(f.phi), n, shift, stream), "lbm_sg_shift")
+    sim.init_fields(f.phi, f.u, f.P, nonequilibrium=True)
+    return f
 
 
 def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max_steps=200000):

@@ -6,7 +6,7 @@ rho(phi) for g).
   walled axis sliding with different velocities, through the library's FP64
   tile (one-node kernel: 8 for D3Q19, 1 for D2Q9), the bulk-copy tile and
   (D2Q9) a grid of a batch: 1e-10 normwise (operation order only);
-* the same in FP32 through the node-pair tile (10): 1e-5 normwise;
+* the same in FP32 through the cp.async tile (7): 1e-5 normwise;
 * the layered Couette flow of Section 3 in FP32 against the quadrature of
   (eta u')' = 0: within 3 % of the wall speed, as the oracle;
 * argument errors."""
@@ -79,18 +79,18 @@ def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False, s
     return out, oracle_macro_flat(h, g, lat, p, lat_id), b
 
 
-PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy", "batch", "pair")
+PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy", "batch", "async")
          if not (path == "batch" and CASES[c][0] == 1)]   # batches hold D2Q9 grids
 
 
 @pytest.mark.parametrize("case,path", PATHS, ids=[f"{('d2q9', 'd3q19')[CASES[c][0]]}-{p}" for c, p in PATHS])
 def test_sliding_walls_against_oracle(lbm, case, path):
     lat_id, shape, bc, axis, walls = CASES[case]
-    tile = {"bulkcopy": (4, 3), "pair": (10, 5)}.get(path)
-    store = lbm.F32 if path == "pair" else lbm.F64
+    tile = {"bulkcopy": (4, 3), "async": (7, 5)}.get(path)
+    store = lbm.F32 if path == "async" else lbm.F64
     (f, Pg, ru), (fo, Po, ruo), _ = run_case(lbm, lat_id, shape, bc, axis, walls, 40, tile=tile,
                                              batch=path == "batch", store=store)
-    tol = 1e-5 if path == "pair" else 1e-10
+    tol = 1e-5 if path == "async" else 1e-10
     assert normwise(f, fo) < tol and normwise(Pg, Po) < tol and normwise(ru, ruo) < tol
 
 

@@ -235,22 +235,21 @@ def test_config1_static_droplet_f64(lbm):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_tile_shapes_agree(lbm, lat_id, shape, bc):
-    """Every compiled one-node tile that runs FP64 (per-thread loads, tiles
-    0-3; the bulk tensor copy pipeline, tile 4; one-wave launches, tiles 5-6
-    and 9; 7 CTAs per SM, tile 8) and z-chunk length computes the same
-    arithmetic: FP64 results agree to rounding (the compiler may contract
-    a*b+c differently per instantiation).  The cp.async tile (7) and the
-    node-pair tiles (10-13) compute in FP32 only."""
+    """Every compiled tile that runs FP64 (per-thread loads, tiles 0-3; the
+    bulk tensor copy pipeline, tile 4; one-wave launches, tiles 5-6 and 9; 7
+    CTAs per SM, tile 8) and z-chunk length computes the same arithmetic: FP64
+    results agree to rounding (the compiler may contract a*b+c differently per
+    instantiation).  The cp.async tile (7) computes in FP32 only."""
     ref = None
     for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (4, 7), (5, 5), (6, 1), (6, 100),
-                     (7, 4), (8, 16), (8, 1), (9, 3), (9, 100), (10, 16)):
+                     (7, 4), (8, 16), (8, 1), (9, 3), (9, 100)):
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            # bulk copies (4) may not apply to a grid; cp.async (7) and the
-            # node-pair tiles (10-15) have no FP64 form
-            assert e.code == lbm.ENOTSUP and tile in (4, 7, 10, 11, 12, 13, 14, 15), tile
+            # bulk copies (4) may not apply to a grid; cp.async (7) has no
+            # FP64 form
+            assert e.code == lbm.ENOTSUP and tile in (4, 7), tile
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
@@ -260,9 +259,7 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
             assert normwise(hg, ref[0]) < 1e-14 and normwise(gg, ref[1]) < 1e-13, (tile, lz)
 
 
-SAME_ARITH_TILES = ((7, 16), (7, 1), (7, 5), (8, 16), (8, 1), (9, 5))
-PAIR_TILES = ((10, 16), (10, 1), (10, 5), (11, 3), (11, 100), (12, 7), (12, 1), (13, 16), (13, 2), (14, 4),
-              (15, 16), (15, 3))
+F32_TILES = ((7, 16), (7, 1), (7, 5), (8, 16), (8, 1), (9, 5))
 
 
 def oracle_pops_after(lbm, lat_id, shape, bc, steps):
@@ -272,14 +269,10 @@ def oracle_pops_after(lbm, lat_id, shape, bc, steps):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_f32_tiles_agree(lbm, lat_id, shape, bc):
-    """The FP32 tiles against the FP64 oracle after 7 steps (populations,
-    1e-5 normwise) and after one step (phi, P, rho u, 1e-5).  The tiles that
-    share the one-node kernel's arithmetic -- cp.async (7), 7 CTAs per SM
-    (8-9) -- also equal tile 1 to a few FP32 roundings (1e-6).  The node-pair
-    tiles (10-13: two nodes per thread on paired FP32 instructions, x pulled
-    from the ghost columns) group the same sums differently; near nodes where
-    grad phi nearly vanishes the interface normal of Eq. 2 amplifies such
-    rounding differences, so they are held to the oracle, not to tile 1."""
+    """The FP32 tiles -- cp.async (7) and 7 CTAs per SM (8-9) -- against the
+    per-thread-load tile 1 (same arithmetic: a few FP32 roundings, 1e-6
+    normwise after 7 steps) and against the FP64 oracle (populations after 7
+    steps, and phi, P, rho u after one step: 1e-5 normwise)."""
     ref, _, _, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
     ref.set_tile(1, 16)
     ref.step(7)
@@ -287,16 +280,14 @@ def test_f32_tiles_agree(lbm, lat_id, shape, bc):
     ho, go = oracle_pops_after(lbm, lat_id, shape, bc, 7)
     hof, gof = oracle_to_lib_pops(ho, lat_id), oracle_to_lib_pops(go, lat_id)
     assert normwise(hr, hof) < 1e-5 and normwise(gr, gof) < 1e-5
-    for tile, lz in SAME_ARITH_TILES + PAIR_TILES:
+    for tile, lz in F32_TILES:
         sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, lz)
         sim.step(7)
         hg, gg = sim.get_populations()
-        eh, eg = normwise(hg, hof), normwise(gg, gof)
-        assert eh < 1e-5 and eg < 1e-5, (tile, lz, eh, eg)
-        if (tile, lz) in SAME_ARITH_TILES:
-            assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz, normwise(hg, hr), normwise(gg, gr))
-    for tile in (7, 8, 9, 10, 11, 12, 13, 14, 15):
+        assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz, normwise(hg, hr), normwise(gg, gr))
+        assert normwise(hg, hof) < 1e-5 and normwise(gg, gof) < 1e-5, (tile, lz)
+    for tile in (7, 8, 9):
         sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, 16)
         sim.step(1)
@@ -308,16 +299,15 @@ def test_f32_tiles_agree(lbm, lat_id, shape, bc):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_tile_switching_f32(lbm, lat_id, shape, bc):
-    """Changing tiles between steps: the node-pair tiles pull x from ghost
-    columns that a one-node tile does not write (the library first fills
-    them), and a one-node tile after a pair step finds the bounce-back
-    values where it wraps x.  A run that switches tiles every few steps stays
+    """Changing tiles between steps: the bulk-copy tile (4) reads the ghost
+    band unwrapped, so the library first fills the periodic images of a state
+    another tile wrote.  A run that switches tiles every step or two stays
     within 1e-5 (normwise, populations) of the FP64 oracle after 7 steps, as
     a run on one tile does."""
     ho, go = oracle_pops_after(lbm, lat_id, shape, bc, 7)
     hof, gof = oracle_to_lib_pops(ho, lat_id), oracle_to_lib_pops(go, lat_id)
     sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
-    for tile, n in ((8, 1), (10, 2), (8, 1), (4, 1), (11, 1), (12, 1)):
+    for tile, n in ((8, 1), (4, 2), (0, 1), (4, 1), (7, 1), (9, 1)):
         try:
             sim.set_tile(tile, 5)
         except lbm.LbmError as e:
@@ -391,8 +381,8 @@ def test_delta_theta_against_oracle(lbm, lat_id, shape, bc):
     """The diffusion correction of Eq. 14 (C = 2, F of the oracle's reading
     R18) on smooth random fields, where (2 phi - 1) lap phi > 0 in places:
     FP64 populations after one step to 1e-13, after 100 steps 1e-10
-    normwise; FP32 through the one-node (8) and node-pair (10) tiles after
-    one step 1e-5 normwise."""
+    normwise; FP32 through tiles 8 and 7 (cp.async) after one step 1e-5
+    normwise."""
     sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F64, C_dtheta=2.0)
     assert p.C_dtheta == 2.0
     rng = np.random.default_rng(8)
@@ -415,7 +405,7 @@ def test_delta_theta_against_oracle(lbm, lat_id, shape, bc):
     f3, _, _ = oracle_macro_flat(h3, g3, lat, p, lat_id)
     p.C_dtheta = 2.0
     assert normwise(f3, fo) > 1e-8
-    for tile in (8, 10):
+    for tile in (8, 7):
         s32, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32, C_dtheta=2.0)
         s32.set_tile(tile, 16)
         s32.step(1)
@@ -423,3 +413,30 @@ def test_delta_theta_against_oracle(lbm, lat_id, shape, bc):
         f, Pg, ru = s32.macro()
         fo, Po, ruo = oracle_macro_flat(h, g, lat, p, lat_id)
         assert normwise(f, fo) < 1e-5 and normwise(Pg, Po) < 1e-5 and normwise(ru, ruo) < 1e-5, tile
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[3], CASES[4]],
+                         ids=[IDS[0], IDS[1], IDS[3], IDS[4]])
+def test_init_nonequilibrium_against_oracle(lbm, lat_id, shape, bc):
+    """lbm_init_fields_ex with LBM_INIT_NONEQ (oracle reading R19: g^eq plus
+    Phi_i : Pi(1), Pi(1) the Chapman-Enskog estimate from central differences
+    of u): FP64 populations equal the oracle's to 1e-14, and lbm_macro still
+    returns the given fields."""
+    nz, ny, nx = shape
+    phi, u, P = I.smooth_random(shape, 13, dim=2 if lat_id == 0 else 3)
+    prm = lbm.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.1, rho_H=1.0, nu_L=0.05, nu_H=0.02, store=lbm.F64)
+    user = (nx, ny) if lat_id == 0 else (nx, ny, nz)
+    sim = lbm.Simulation(lat_id, user, prm, bc=bc)
+    sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, lat_id),
+                    np.ascontiguousarray(P.reshape(-1)), nonequilibrium=True)
+    hg, gg = sim.get_populations()
+    lat = oracle_lattice(lat_id)
+    p = oracle_params(prm, bc, lat_id)
+    h, g = O.init_populations(phi, u, P, lat, p, nonequilibrium=True)
+    np.testing.assert_allclose(lib_to_oracle_pops(hg, lat_id, shape), h, atol=1e-14, rtol=0)
+    np.testing.assert_allclose(lib_to_oracle_pops(gg, lat_id, shape), g, atol=1e-14, rtol=0)
+    h0, g0 = O.init_populations(phi, u, P, lat, p)
+    assert np.abs(g - g0).max() > 1e-6          # the case exercises the non-equilibrium part
+    f, Pg, ru = sim.macro()
+    np.testing.assert_allclose(f, phi.reshape(-1), atol=1e-14)
+    np.testing.assert_allclose(Pg, P.reshape(-1), atol=1e-15)

@@ -260,3 +260,51 @@ def test_tau_mix_interpolation():
     assert T * (1 / om[1] - 0.5) == pytest.approx(0.0017, rel=1e-14)
     assert om[2] == om[0] and om[3] == om[1]
     assert om[4] == pytest.approx(0.5 * (om[0] + om[1]), rel=1e-15)
+
+
+def test_chapman_enskog_rebuild():
+    """Reading R19: g = g^eq + Phi : Pi(1) keeps the zeroth and first moments
+    of g^eq (so the rebuilt state has the given P and u), its non-equilibrium
+    second moment is Pi(1) itself, and on a sheared single-phase flow that has
+    relaxed under the filtered collision the measured pre-collision
+    non-equilibrium momentum flux agrees with Pi(1) = -tau T rho (du + du^T)."""
+    from oracle import lattice as LL
+    from paper_1812_00118_gb300 import inputs as II
+    lat = LL.D3Q19
+    phi, u, P = II.smooth_random((6, 7, 8), 21)
+    p = O.Params(M=0.1, W=4.0, sigma=0.01, rho_L=0.1, rho_H=1.0, nu_L=0.05, nu_H=0.02)
+    h0, g0 = O.init_populations(phi, u, P, lat, p)
+    h1, g1 = O.init_populations(phi, u, P, lat, p, nonequilibrium=True)
+    assert np.array_equal(h0, h1)
+    d = g1 - g0
+    c = lat.c.astype(float)
+    np.testing.assert_allclose(d.sum(axis=0), 0.0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("ia,i...->a...", c, d), 0.0, atol=1e-16)
+    Pi = O.chapman_enskog_pi(phi, u, lat, p)
+    np.testing.assert_allclose(O.second_moment(d, lat), Pi, atol=1e-15)
+    # single phase (phi = 1), a long shear wave u_x = U sin(k y) decaying under
+    # the filtered collision: after it has relaxed onto its slow mode the
+    # pre-collision sum c c (g - g^eq) matches Pi(1) to O(k^2)
+    ny = 64
+    k = 2 * np.pi / ny
+    q = O.Params(M=0.1, W=4.0, sigma=0.0, rho_L=1.0, rho_H=1.0, nu_L=0.05, nu_H=0.05, hocorr=False,
+                 modified_velocity=False)
+    shape = (1, ny, 1)
+    phi1 = np.ones(shape)
+    uu = np.zeros((3,) + shape)
+    uu[0] = 1e-3 * np.sin(k * np.arange(ny))[None, :, None]
+
+    def mismatch(hh, gg):
+        m = O.macroscopic(hh, gg, lat, q)
+        G = O.gamma(m["u"], lat)
+        K = O.forcing(m["u"], m["grad"], m["mu"], m["F"], lat, q, G)
+        geq = O.g_equilibrium(m["rho"], m["u"], m["P"], K, m["lap"], lat, q, G)
+        meas = O.second_moment(gg - geq, lat)[0, 1]
+        est = O.chapman_enskog_pi(m["phi"], m["u"], lat, q)[0, 1]
+        return np.abs(meas - est).max() / np.abs(est).max()
+
+    hh, gg = O.init_populations(phi1, uu, np.zeros(shape), lat, q)
+    assert mismatch(*O.run(hh, gg, lat, q, 300)) < 0.01      # relaxed: O(k^2) apart (2e-3)
+    assert mismatch(*O.run(hh, gg, lat, q, 1)) > 0.3         # an equilibrium start is not
+    hn, gn = O.init_populations(phi1, uu, np.zeros(shape), lat, q, nonequilibrium=True)
+    assert mismatch(*O.run(hn, gn, lat, q, 1)) < 0.01        # the rebuilt start already is

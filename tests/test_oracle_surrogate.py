@@ -1,7 +1,8 @@
 """Pins of the surrogate network oracle (oracle/surrogate.py) against what
 the definitions fix: a brute-force loop convolution, the response to a unit
-impulse, adjoint identities of pooling and upsampling, and central finite
-differences of the loss for every parameter tensor."""
+impulse, adjoint identities of pooling and upsampling, the identity map when
+the last layer is zero, and central finite differences of the loss for
+every parameter tensor of the four-level U-Net."""
 import numpy as np
 import pytest
 
@@ -48,20 +49,23 @@ def test_conv_impulse_response():
     assert np.allclose(out[0, 5, 0], b)   # untouched pixel
 
 
-def test_pool_and_upsample_adjoints():
+@pytest.mark.parametrize("f", [2, 8])
+def test_pool_and_upsample_adjoints(f):
     rng = np.random.default_rng(2)
     x = rng.normal(size=(2, 16, 24, 3))
-    y = rng.normal(size=(2, 2, 3, 3))
-    assert np.isclose(np.sum(S.pool(x) * y), np.sum(x * S.pool_backward(y, x.shape)))
-    assert np.isclose(np.sum(S.upsample(y) * x), np.sum(y * S.upsample_backward(x)))
-    np.testing.assert_allclose(S.pool(S.upsample(y)), y)
+    y = rng.normal(size=(2, 16 // f, 24 // f, 3))
+    assert np.isclose(np.sum(S.pool(x, f) * y), np.sum(x * S.pool_backward(y, f)))
+    assert np.isclose(np.sum(S.upsample(y, f) * x), np.sum(y * S.upsample_backward(x, f)))
+    np.testing.assert_allclose(S.pool(S.upsample(y, f), f), y)
+    # a block mean by hand
+    np.testing.assert_allclose(S.pool(x, f)[1, 1, 2, 0], x[1, f:2 * f, 2 * f:3 * f, 0].mean())
 
 
 def test_identity_when_last_layer_is_zero():
     rng = np.random.default_rng(3)
     P = S.init_params(3)
-    P["d2.W"][:] = 0.0
-    P["d2.b"][:] = 0.0
+    P["out.W"][:] = 0.0
+    P["out.b"][:] = 0.0
     x = rng.normal(size=(1, 16, 16, 4))
     out, _ = S.forward(P, x)
     assert np.array_equal(out, x)
@@ -100,6 +104,8 @@ def test_network_gradient_finite_differences():
     t = rng.normal(size=(2, 16, 16, 4))
     out, cache = S.forward(P, x)
     g = S.backward(P, cache, out, t)
+    # every layer and the skip paths carry gradient
+    assert all(np.abs(g[k]).max() > 0 for k in g)
     e = 1e-6
     for name in P:
         for _ in range(3):
@@ -109,4 +115,6 @@ def test_network_gradient_finite_differences():
             Pp[name][idx] += e
             Pm[name][idx] -= e
             fd = (S.loss(S.forward(Pp, x)[0], t) - S.loss(S.forward(Pm, x)[0], t)) / (2 * e)
-            assert fd == pytest.approx(g[name][idx], rel=1e-5, abs=1e-10), (name, idx)
+            # abs: the rounding of the two losses (~2e-16 of a loss of ~2)
+            # divided by the step 2e-6
+            assert fd == pytest.approx(g[name][idx], rel=1e-5, abs=1e-9), (name, idx)
