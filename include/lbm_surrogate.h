@@ -3,8 +3,9 @@
  * The paper has no network: these are a service of the library.  A small
  * convolutional network maps the fields (phi, u, P) of a D2Q9 state to the
  * state many steps later; its training and inference run on these kernels,
- * and lbm_init_fields rebuilds the populations from its output (equilibria,
- * Eqs. 2 and 6-7 of the paper).
+ * and lbm_init_fields_ex rebuilds the populations from its output
+ * (equilibria of Eqs. 2 and 6-7 of the paper plus the filtered Chapman-Enskog
+ * non-equilibrium part of g, Eq. 11).
  *
  * Conventions (every function):
  *   - Tensors are channels-last on the device: pixel p = (n H + y) W + x of
@@ -31,9 +32,19 @@ extern "C" {
 #endif
 
 /* y (float) = periodic 3x3 convolution of x (bf16) with w (bf16), plus bias
- * (float[Co], may be NULL).  BF16 tensor-core products, FP32 sums. */
+ * (float[Co], may be NULL): an implicit GEMM on the tcgen05 tensor cores,
+ * bf16 products, FP32 sums in tensor memory, 128 pixels per CTA.  x's channel
+ * stride csx is a multiple of 8 and x and w start on 16-byte boundaries (the
+ * operands are staged in 16-byte copies); LBM_EINVAL otherwise.  A bounded
+ * wait inside the kernel that gives up leaves its CTA's part of y unwritten
+ * and is reported by lbm_sg_status. */
 int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, float* y, int csy, int N, int H, int W,
                    int Ci, int Co, void* stream);
+
+/* Synchronises `stream` and reports whether a bounded wait of a surrogate
+ * kernel gave up since the last call: LBM_ETIMEOUT (the flag is cleared),
+ * else LBM_OK; LBM_ECUDA if the copy or the synchronisation failed. */
+int lbm_sg_status(void* stream);
 
 /* Floats of scratch lbm_sg_conv3x3_wgrad needs for these sizes. */
 long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co);
@@ -99,11 +110,13 @@ int lbm_sg_pack(const double* phi, const double* rux, const double* ruy, const d
 
 /* Fields for lbm_init_fields from the network output: (phi, rho u, P) =
  * (x32 + delta) * scale, written as phi, u = rho u / (rho_L + phi_c rho_dif)
- * (the density of the paper's rho(phi), phi_c = phi clipped to [0, 1] so
- * that a slight undershoot of the prediction in the light phase cannot make
- * it vanish) and P. */
+ * (the density of the paper's rho(phi), phi_c clipped to [0, 1] so that a
+ * slight undershoot of the prediction in the light phase cannot make it
+ * vanish) and P.  phi_c is taken from phi_rho (device, npix doubles, not the
+ * phi output) when given, e.g. a projected phi, else from the predicted phi. */
 int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
-                  double* P, const double scale[4], double rho_L, double rho_dif, long long npix, void* stream);
+                  double* P, const double scale[4], double rho_L, double rho_dif, const double* phi_rho,
+                  long long npix, void* stream);
 
 /* out (device, 2 doubles) = (sum (a - b)^2, sum a^2) over n values, FP64 in
  * a fixed order; scratch: 512 doubles.  The convergence measure of the
@@ -114,6 +127,17 @@ int lbm_sg_residual(const double* a, const double* b, long long n, double* out, 
  * periodic in each of N images of H x W, 0 <= k <= 1/4, tmp: N H W doubles):
  * removes the block-scale roughness of a prediction before it seeds a run. */
 int lbm_sg_smooth(double* a, double* tmp, int N, int H, int W, int iters, double k, void* stream);
+
+/* Projection of a predicted phi (device, n doubles, in place) onto the start
+ * phi0: phi <- clip(phi0 + 4 phi0 (1 - phi0) (phi - phi0), 0, 1) keeps the
+ * predicted change inside the start's interface band (none in the bulk
+ * phases, where 16-bit noise of the prediction would otherwise seed
+ * spurious mixed regions and densities below rho_L), then
+ * phi <- phi + c 4 phi (1 - phi) with c chosen so that sum phi = sum phi0
+ * (Eq. 1 conserves the total; the correction moves the interfaces, not the
+ * bulk; c uses the weights before the correction, so the total is restored
+ * up to FP64 rounding).  FP64 sums in a fixed order; scratch: 769 doubles. */
+int lbm_sg_phi_project(double* phi, const double* phi0, long long n, double* scratch, void* stream);
 
 /* a[k] += s (used to restore the exact total of phi after a prediction). */
 int lbm_sg_shift(double* a, long long n, double s, void* stream);

@@ -900,31 +900,52 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
     };
     // the thread's own position (its pulled h kept in hown[hs]) and its share
     // of the halo ring; with one ring position per thread, both sets of loads
-    // are issued before either is summed (one latency instead of two)
+    // are issued before either is summed (one latency instead of two).  A
+    // warp none of whose threads has a ring
+    // position (the ring positions are the lowest thread indices) loads and
+    // sums its own column only.
     auto fill = [&](int zp, int slot, int hs) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
         if constexpr (kOneRing) {
-            PullOffsets po = own_xy, pr = ring_xy;
+            PullOffsets po = own_xy;
             pull_z(G, zz, po);
-            pull_z(G, zz, pr);
-            const bool ring = tid < NRING;
-            typename St::S hv[Q], rv[Q];
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                hv[i] = ld_keep(pull_ptr<LAT, i>(D.hin, po));
-                rv[i] = ld_keep_if(pull_ptr<LAT, i>(D.hin, pr), ring);
-            });
-            PhiSum<R> phi, rphi;
-            Unroll<0, Q>::run([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr double W = L::w[i];
-                const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
-                hown[hs][i][tid] = v;
-                phi.add(v);
-                rphi.add(St::load(rv[i], (R)W * p.h_shift, (R)1));
-            });
-            phis[slot][ty + HY][tx + 1] = phi.value();
-            if (ring) (&phis[slot][0][0])[ring_off] = rphi.value();
+            typename St::S hv[Q];
+            if ((tid & ~31) < NRING) {   // uniform over the warp
+                PullOffsets pr = ring_xy;
+                pull_z(G, zz, pr);
+                const bool ring = tid < NRING;
+                typename St::S rv[Q];
+                Unroll<0, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    hv[i] = ld_keep(pull_ptr<LAT, i>(D.hin, po));
+                    rv[i] = ld_keep_if(pull_ptr<LAT, i>(D.hin, pr), ring);
+                });
+                PhiSum<R> phi, rphi;
+                Unroll<0, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    constexpr double W = L::w[i];
+                    const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
+                    hown[hs][i][tid] = v;
+                    phi.add(v);
+                    rphi.add(St::load(rv[i], (R)W * p.h_shift, (R)1));
+                });
+                phis[slot][ty + HY][tx + 1] = phi.value();
+                if (ring) (&phis[slot][0][0])[ring_off] = rphi.value();
+            } else {
+                Unroll<0, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    hv[i] = ld_keep(pull_ptr<LAT, i>(D.hin, po));
+                });
+                PhiSum<R> phi;
+                Unroll<0, Q>::run([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    constexpr double W = L::w[i];
+                    const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
+                    hown[hs][i][tid] = v;
+                    phi.add(v);
+                });
+                phis[slot][ty + HY][tx + 1] = phi.value();
+            }
         } else {
             {
                 PullOffsets po = own_xy;
@@ -982,9 +1003,17 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
             }
         }
         __syncthreads();
-        if (active)
-            collide_node<LAT, ST, WALLS>(D, G, p, phis, j & 3, (j + 1) & 3, (j + 2) & 3, tx + 1, ty + HY, m,
-                                         [&](int i) { return hown[(j + 1) & 1][i][tid]; }, x, y, z, rb);
+        if (active) {
+            auto hv = [&](int i) { return hown[(j + 1) & 1][i][tid]; };
+            // only a node next to a wall writes bounce-back ghost cells: the
+            // rest take the wall-free collision (fewer live registers)
+            if (WALLS && node_writes<LAT>(G, x, y, z).wall_adj)
+                collide_node<LAT, ST, true>(D, G, p, phis, j & 3, (j + 1) & 3, (j + 2) & 3, tx + 1, ty + HY, m, hv, x,
+                                            y, z, rb);
+            else
+                collide_node<LAT, ST, false>(D, G, p, phis, j & 3, (j + 1) & 3, (j + 2) & 3, tx + 1, ty + HY, m, hv,
+                                             x, y, z, rb);
+        }
     }
 }
 

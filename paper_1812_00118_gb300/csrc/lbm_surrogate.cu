@@ -9,10 +9,11 @@
 // input channels fastest).  Channel counts of convolutions are multiples of
 // 16 (zero-padded by the caller), pixel counts multiples of 16.
 //
-// The contraction uses the warp-level mma.sync m16n8k16 BF16 instruction:
-// A fragments are gathered straight from the channels-last activations (two
-// adjacent channels per 32-bit register), so a convolution is an implicit
-// GEMM without an im2col buffer.
+// The forward (and input-gradient) convolution runs on the tcgen05 tensor
+// cores with the accumulator in tensor memory (conv_tc_kernel); the weight
+// gradient, a GEMM over pixels, uses the warp-level mma.sync m16n8k16 BF16
+// instruction with fragments gathered straight from the channels-last
+// tensors.  Both are implicit GEMMs without an im2col buffer.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,44 +54,200 @@ __device__ __forceinline__ long long shift_pixel(long long p, int H, int W, int 
     return n * hw + (long long)y * W + x;
 }
 
-// y[p, co] = b[co] + sum_{tap, ci} w[co, tap, ci] x[shift(p, tap), ci]; one warp per 16 pixels,
-// NT n-tiles of 8 output channels (Co = 8 NT).
-template <int NT>
-__global__ void conv_fwd_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
-                                const float* __restrict__ bias, float* __restrict__ y, int csy, long long M, int H,
-                                int W, int Ci) {
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const long long p0 = warp * 16;
-    if (p0 >= M) return;
-    const long long r0 = p0 + g, r1 = p0 + g + 8;
-    float acc[NT][4];
+// ---------------------------------------------------------------- tcgen05 convolution
+// The forward convolution (and the input-gradient convolution, the same
+// operation on flipped weights) as an implicit GEMM on the fifth-generation
+// tensor cores: D[pixel, co] = sum over (tap, ci) of A[pixel, (tap, ci)]
+// B[(tap, ci), co], with A the shifted activations and B the weights, both
+// bf16 and K-major (channels contiguous), D in FP32 in tensor memory.
+//
+// A CTA of 128 threads owns 128 consecutive pixels and every output channel
+// (MMA shape M = 128, N = Co, K = 16).  The K loop runs over stages (tap,
+// block of up to 128 input channels).  Per stage every thread copies its
+// pixel's shifted channel row (16-byte cp.async; rows past the last pixel
+// are zero-filled) and a share of the tap's weight rows into one of two
+// shared-memory buffers, in the no-swizzle canonical layout of the tensor
+// core: 8 x 16-byte core matrices, rows 16 bytes apart, 8-row groups 128
+// bytes apart (stride byte offset), the 8-channel chunks one after another
+// (leading byte offset = rows x 16 bytes).  Thread 0 then issues the stage's
+// MMAs and commits them to the buffer's mbarrier; the copies of the next
+// stage go to the other buffer while they run, and a buffer is refilled only
+// after the mbarrier shows its previous MMAs done.  The epilogue reads the
+// accumulator back with tcgen05.ld (warp w reads lanes 32w..32w+31, one pixel
+// per thread), adds the bias and stores FP32.
+//
+// Every wait is bounded: a wait that gives up sets *err (read by
+// lbm_sg_status) and the CTA skips its epilogue, frees its tensor memory and
+// returns.
+constexpr int kTcM = 128;        // pixels per CTA (MMA M)
+constexpr int kTcK = 128;        // input channels per stage
+constexpr long kTcPolls = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// true once the phase of the given parity has completed; false after `polls` tries
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long polls) {
+    for (long i = 0; i < polls; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// shared-memory matrix descriptor, no swizzle: start address, leading and
+// stride byte offsets (all in 16-byte units), descriptor version 1
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, N / 8 and M / 16
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// 16 consecutive FP32 columns of the thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    for (int tap = 0; tap < 9; ++tap) {
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+conv_tc_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, const float* __restrict__ bias,
+               float* __restrict__ y, int csy, long long M, int H, int W, int Ci, int Co, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long p0 = (long long)blockIdx.x * kTcM;
+    const int kcap = Ci < kTcK ? Ci : kTcK;   // channels per stage buffer
+    const uint32_t a_bytes = kTcM * kcap * 2, b_bytes = (uint32_t)Co * kcap * 2;
+    const uint32_t sb = smem_u32(smem);
+    // buffer b: A at sb + b a_bytes, B at sb + 2 a_bytes + b b_bytes; its barrier at bar0 + 8 b
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    const uint32_t ncols = Co <= 32 ? 32u : (Co <= 64 ? 64u : 128u);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc_bf16(kTcM, Co);
+    const int nkb = (Ci + kTcK - 1) / kTcK;
+    const int nst = 9 * nkb;
+    const long long p = p0 + tid;
+    const bool in = p < M;
+    bool ok = true;
+    int issued = 0;   // stages whose MMAs were issued and committed
+    for (int st = 0; st < nst; ++st) {
+        const int b = st & 1;
+        const uint32_t a_s = sb + b * a_bytes, b_s = sb + 2 * a_bytes + b * b_bytes, bar = bar0 + 8 * b;
+        const int tap = st / nkb, kc0 = (st % nkb) * kTcK;
+        const int kw = Ci - kc0 < kTcK ? Ci - kc0 : kTcK;
+        // the MMAs of stage st - 2 read this buffer: the (st - 2) / 2-th phase
+        // of its barrier; every thread waits, and all give up together
+        if (st >= 2) {
+            const bool done = mbar_wait_bounded(bar, (uint32_t)((st - 2) >> 1) & 1u, kTcPolls);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+        }
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const bf16* xa0 = x + shift_pixel(r0, H, W, dy, dx) * csx + 2 * t;
-        const bf16* xa1 = x + shift_pixel(r1, H, W, dy, dx) * csx + 2 * t;
-        for (int kc = 0; kc < Ci; kc += 16) {
-            const uint32_t a[4] = {ld_pair(xa0 + kc), ld_pair(xa1 + kc), ld_pair(xa0 + kc + 8), ld_pair(xa1 + kc + 8)};
+        const bf16* src = x + (in ? shift_pixel(p, H, W, dy, dx) : 0) * csx + kc0;
+        for (int c = 0; c < kw / 8; ++c) cp_async16(a_s + c * (kTcM * 16) + tid * 16, src + c * 8, in ? 16u : 0u);
+        for (int k = tid; k < Co * (kw / 8); k += kTcM) {
+            const int co = k % Co, c = k / Co;
+            cp_async16(b_s + c * (Co * 16) + co * 16, w + ((long long)co * 9 + tap) * Ci + kc0 + c * 8, 16u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // the copies were written through the generic proxy; the MMAs read through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int s = 0; s < kw / 16; ++s) {
+                const uint64_t ad = tc_smem_desc(a_s + 2 * s * (kTcM * 16), kTcM * 16, 128);
+                const uint64_t bd = tc_smem_desc(b_s + 2 * s * (Co * 16), Co * 16, 128);
+                tc_mma(tmem, ad, bd, idesc, (st > 0 || s > 0) ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        issued = st + 1;
+    }
+    // the last committed stage completes after every earlier MMA of the CTA
+    // (waited for on the failure path too, before the tensor memory is freed)
+    if (issued > 0) {
+        const bool done = mbar_wait_bounded(bar0 + 8 * ((issued - 1) & 1), (uint32_t)((issued - 1) >> 1) & 1u, kTcPolls);
+        ok = __syncthreads_and(ok && done) != 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const long long pr = p0 + 32 * warp + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int c0 = 0; c0 < Co; c0 += 16) {
+            float v[16];
+            tc_ld16(trow + (uint32_t)c0, v);
+            if (pr < M) {
+                float* out = y + pr * csy + c0;
 #pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                const bf16* wb = w + ((long long)(j * 8 + g) * 9 + tap) * Ci + kc + 2 * t;
-                const uint32_t b[2] = {ld_pair(wb), ld_pair(wb + 8)};
-                mma_bf16(acc[j], a, b);
+                for (int i = 0; i < 16; ++i) out[i] = v[i] + (bias ? bias[c0 + i] : 0.0f);
             }
         }
     }
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int co = j * 8 + 2 * t;
-        const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
-        y[r0 * csy + co] = acc[j][0] + b0;
-        y[r0 * csy + co + 1] = acc[j][1] + b1;
-        y[r1 * csy + co] = acc[j][2] + b0;
-        y[r1 * csy + co + 1] = acc[j][3] + b1;
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (!ok && tid == 0) atomicExch(err, 1);
 }
+
+// two stage buffers of A (128 pixels) and B (Co weight rows), min(Ci, 128) channels each
+size_t conv_tc_smem_bytes(int Ci, int Co) {
+    const size_t k = Ci < kTcK ? (size_t)Ci : (size_t)kTcK;
+    return 2u * (kTcM + (size_t)Co) * k * 2;
+}
+
+__device__ int g_sg_err;   // a bounded wait of a surrogate kernel gave up
 
 // partial[chunk, co, tap, ci] = sum over the chunk's pixels p of gy[p, co] x[shift(p, tap), ci];
 // one warp per (chunk, tap, 16 output channels, 8 input channels).
@@ -362,13 +519,14 @@ __global__ void pack_kernel(const double* __restrict__ f0, const double* __restr
 __global__ void unpack_kernel(const float* __restrict__ x32, int cs32, const float* __restrict__ delta, int csd,
                               double* __restrict__ f0, double* __restrict__ f1, double* __restrict__ f2,
                               double* __restrict__ f3, double s0, double s1, double s2, double s3, double rho_L,
-                              double rho_dif, long long npix) {
+                              double rho_dif, const double* __restrict__ phi_rho, long long npix) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
     double v[4];
     const double s[4] = {s0, s1, s2, s3};
     for (int c = 0; c < 4; ++c) v[c] = ((double)x32[p * cs32 + c] + (double)delta[p * csd + c]) * s[c];
-    const double pc = v[0] < 0.0 ? 0.0 : (v[0] > 1.0 ? 1.0 : v[0]);
+    const double pr = phi_rho ? phi_rho[p] : v[0];
+    const double pc = pr < 0.0 ? 0.0 : (pr > 1.0 ? 1.0 : pr);
     const double rho = rho_L + pc * rho_dif;
     f0[p] = v[0];
     f1[p] = v[1] / rho;
@@ -409,6 +567,62 @@ __global__ void residual_finish_kernel(const double* __restrict__ part, int nb, 
     out[1] = a2;
 }
 
+// phi <- clip(phi0 + m (phi - phi0), 0, 1), m = 4 phi0 (1 - phi0): the
+// predicted change of phi kept inside the interface band of the start and
+// none in the bulk phases; block partials of sum phi0, sum phi, sum 4 phi (1 - phi)
+__global__ void phi_project_kernel(double* __restrict__ phi, const double* __restrict__ phi0, long long n,
+                                   double* __restrict__ part) {
+    __shared__ double s0[kThreads], s1[kThreads], s2[kThreads];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double f0 = phi0[k];
+        const double m = 4.0 * f0 * (1.0 - f0);
+        double f = f0 + (m > 0.0 ? m : 0.0) * (phi[k] - f0);
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        phi[k] = f;
+        a0 += f0;
+        a1 += f;
+        a2 += 4.0 * f * (1.0 - f);
+    }
+    s0[threadIdx.x] = a0;
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s0[threadIdx.x] += s0[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = s0[0];
+        part[3 * blockIdx.x + 1] = s1[0];
+        part[3 * blockIdx.x + 2] = s2[0];
+    }
+}
+
+// c = (sum phi0 - sum phi) / sum 4 phi (1 - phi), partials in block order, into part[3 nb]
+__global__ void phi_project_finish_kernel(double* __restrict__ part, int nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        a0 += part[3 * b];
+        a1 += part[3 * b + 1];
+        a2 += part[3 * b + 2];
+    }
+    part[3 * nb] = a2 > 0.0 ? (a0 - a1) / a2 : 0.0;
+}
+
+// phi += c 4 phi (1 - phi): the total of phi0 restored by moving the interfaces
+__global__ void phi_restore_kernel(double* __restrict__ phi, long long n, const double* __restrict__ c) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double f = phi[k];
+    phi[k] = f + c[0] * 4.0 * f * (1.0 - f);
+}
+
 // b = a + k lap(a), five-point Laplacian, periodic in each H x W image
 __global__ void smooth_kernel(const double* __restrict__ a, double* __restrict__ b, int N, int H, int W, double k) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -435,23 +649,40 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     if (!x || !w || !y || N < 1 || H < 1 || W < 1 || !conv_dims_ok(M, Ci, Co) || csx < Ci || csx % 2 || csy < Co)
         return LBM_EINVAL;
     if (Co > 128) return LBM_EINVAL;
-    const long long warps = M / 16;
-    const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
+    // 16-byte copies: channel rows and slices start on 16-byte boundaries
+    if (csx % 8 || ((uintptr_t)x & 15) || ((uintptr_t)w & 15)) return LBM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const bf16* xb = (const bf16*)x;
-    const bf16* wb = (const bf16*)w;
-    switch (Co / 16) {
-        case 1: conv_fwd_kernel<2><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 2: conv_fwd_kernel<4><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 3: conv_fwd_kernel<6><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 4: conv_fwd_kernel<8><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 5: conv_fwd_kernel<10><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 6: conv_fwd_kernel<12><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 7: conv_fwd_kernel<14><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        case 8: conv_fwd_kernel<16><<<nb, 128, 0, s>>>(xb, csx, wb, bias, y, csy, M, H, W, Ci); break;
-        default: return LBM_EINVAL;
+    const size_t smem = 192 * 1024;   // TEMPORARY headroom for the first hardware check of the descriptor reading
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 192 * 1024) != cudaSuccess)
+            return LBM_ECUDA;
+        attr_set[dev] = true;
     }
+    int* err = nullptr;
+    if (cudaGetSymbolAddress((void**)&err, g_sg_err) != cudaSuccess) return LBM_ECUDA;
+    const unsigned nb = (unsigned)((M + kTcM - 1) / kTcM);
+    conv_tc_kernel<<<nb, kTcM, smem, s>>>((const bf16*)x, csx, (const bf16*)w, bias, y, csy, M, H, W, Ci, Co, err);
     return check(cudaGetLastError());
+}
+
+int lbm_sg_status(void* stream) {
+    int* err = nullptr;
+    if (cudaGetSymbolAddress((void**)&err, g_sg_err) != cudaSuccess) return LBM_ECUDA;
+    int h = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ECUDA;
+    if (h) {
+        const int zero = 0;
+        if (cudaMemcpyAsync(err, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) return LBM_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ECUDA;
+        return LBM_ETIMEOUT;
+    }
+    return LBM_OK;
 }
 
 long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co) {
@@ -583,12 +814,14 @@ int lbm_sg_pack(const double* phi, const double* ux, const double* uy, const dou
 }
 
 int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, double* phi, double* ux, double* uy,
-                  double* P, const double scale[4], double rho_L, double rho_dif, long long npix, void* stream) {
+                  double* P, const double scale[4], double rho_L, double rho_dif, const double* phi_rho,
+                  long long npix, void* stream) {
     if (!x32 || !delta || !phi || !ux || !uy || !P || !scale || npix < 1 || cs32 < 4 || csd < 4 || !(rho_L > 0))
         return LBM_EINVAL;
+    if (phi_rho == phi) return LBM_EINVAL;
     unpack_kernel<<<blocks(npix), kThreads, 0, (cudaStream_t)stream>>>(x32, cs32, delta, csd, phi, ux, uy, P, scale[0],
                                                                         scale[1], scale[2], scale[3], rho_L, rho_dif,
-                                                                        npix);
+                                                                        phi_rho, npix);
     return check(cudaGetLastError());
 }
 
@@ -598,6 +831,16 @@ int lbm_sg_residual(const double* a, const double* b, long long n, double* out, 
     cudaStream_t s = (cudaStream_t)stream;
     residual_partial_kernel<<<nb, kThreads, 0, s>>>(a, b, n, scratch);
     residual_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_phi_project(double* phi, const double* phi0, long long n, double* scratch, void* stream) {
+    if (!phi || !phi0 || !scratch || n < 1) return LBM_EINVAL;
+    const int nb = 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    phi_project_kernel<<<nb, kThreads, 0, s>>>(phi, phi0, n, scratch);
+    phi_project_finish_kernel<<<1, 32, 0, s>>>(scratch, nb);
+    phi_restore_kernel<<<blocks(n), kThreads, 0, s>>>(phi, n, scratch + 3 * nb);
     return check(cudaGetLastError());
 }
 

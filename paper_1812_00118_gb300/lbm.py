@@ -100,6 +100,7 @@ SIGNATURES = [
     ("lbm_sg_relu_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_longlong,
                                        ctypes.c_int, _VP]),
     ("lbm_sg_to_bf16", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_sg_status", ctypes.c_int, [_VP]),
     ("lbm_sg_add", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
                                   ctypes.c_int, _VP]),
     ("lbm_sg_pool", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int] + [ctypes.c_int] * 5 + [_VP]),
@@ -113,10 +114,11 @@ SIGNATURES = [
     ("lbm_sg_pack", ctypes.c_int, [_VP, _VP, _VP, _VP, _DP, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
                                    _VP]),
     ("lbm_sg_unpack", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _DP, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_longlong, _VP]),
+                                     ctypes.c_double, _VP, ctypes.c_longlong, _VP]),
     ("lbm_sg_residual", ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP, _VP]),
     ("lbm_sg_smooth", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      _VP]),
+    ("lbm_sg_phi_project", ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP]),
     ("lbm_sg_shift", ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),

@@ -9,8 +9,9 @@ the solver itself generates (1-4 drops or bubbles, radii 12-48, density
 ratio 1000).  At inference it is applied k times to the initial fields,
 jumping k DT steps ahead towards the end of the transient; the populations
 are rebuilt from the prediction as equilibria plus the filtered
-non-equilibrium part (lbm_init_fields_ex, LBM_INIT_NONEQ), with the total
-of phi re-imposed exactly (FP64 sum on the GPU, uniform shift).  The plain
+non-equilibrium part (lbm_init_fields_ex, LBM_INIT_NONEQ), after the
+predicted phi is projected onto the start (change confined to the
+interfaces, total of phi restored in FP64: lbm_sg_phi_project).  The plain
 solver then continues and decides convergence, so the method stays the
 judge and the fallback.
 
@@ -30,9 +31,11 @@ from . import inputs as I
 from . import lbm as L
 from .surrogate import NC, _ck, _ptr
 
-# normalisation of (phi, rho u_x, rho u_y, P) for the network: spurious
-# currents are ~1e-5, Laplace jumps sigma / R ~ 2e-4 - 1e-3
-SCALE = (1.0, 1e-5, 1e-5, 2e-4)
+# normalisation of (phi, rho u_x, rho u_y, P) for the network: over the
+# transient both rho u and P have a standard deviation of ~2e-4 - 3e-4
+# (the Laplace jumps sigma / R are 2e-4 - 1e-3), so every channel of the
+# network's input is O(1)
+SCALE = (1.0, 2e-4, 2e-4, 3e-4)
 # the warm-start workload: drops and bubbles at density ratio 1000, the
 # water-like viscosity of the paper's shear and Galilean tests
 PHYS = dict(M=0.1, W=4.0, sigma=0.01, rho_L=1e-3, rho_H=1.0, nu_L=1.0 / 60.0, nu_H=1.0 / 60.0)
@@ -155,17 +158,21 @@ def identity_loss(S):
     return float(((S[:, 1:] - S[:, :-1]) ** 2).mean().item())
 
 
-def predict_into(torch, sg1, sim, phi0_host, prm, k_apply):
+def predict_into(torch, sg1, sim, phi0_host, prm, k_apply, velocity=True):
     """Warm start: apply the one-image surrogate k_apply times to the initial
-    fields (phi0, 0, 0) -- a jump of k_apply DT steps --, re-impose the
-    initial total of phi (FP64 sum, uniform shift), and rebuild sim's
-    populations from the predicted (phi, u, P) as equilibria plus the
-    Chapman-Enskog non-equilibrium part.  Returns the predicted fields."""
+    fields (phi0, 0, 0) -- a jump of k_apply DT steps --, project the
+    predicted phi onto the start (its change kept to the start's interface
+    band, clipped to [0, 1], the total of phi0 restored by moving the
+    interfaces: lbm_sg_phi_project), and rebuild sim's populations from
+    (phi, u, P) as equilibria plus the Chapman-Enskog non-equilibrium part.
+    u = (predicted rho u) / rho(projected phi), or 0 without `velocity`.
+    Returns the fields."""
     lib = L.load()
     n = sg1.M[0]
     stream = torch.cuda.current_stream().cuda_stream
     f = DeviceFields(torch, n)
-    f.phi.copy_(torch.from_numpy(phi0_host))
+    phi0 = torch.from_numpy(phi0_host).cuda()
+    f.phi.copy_(phi0)
     tmp16 = torch.zeros(n, 16, dtype=torch.bfloat16, device="cuda")
     x32 = torch.zeros(n, NC, dtype=torch.float32, device="cuda")
     x32n = torch.zeros_like(x32)
@@ -181,14 +188,16 @@ def predict_into(torch, sg1, sim, phi0_host, prm, k_apply):
     rho_dif = prm.rho_H - prm.rho_L
     if delta is None:
         delta = torch.zeros(n, 16, dtype=torch.float32, device="cuda")
-    _ck(lib.lbm_sg_unpack(_ptr(x32), NC, _ptr(delta), 16, _ptr(f.phi), ctypes.c_void_p(u),
-                          ctypes.c_void_p(u + 8 * n), _ptr(f.P), _scale_arr(), prm.rho_L, rho_dif, n, stream),
-        "lbm_sg_unpack")
-    # the total of phi of the start, restored exactly (Eq. 1 conserves it)
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    L.field_sums_noalloc(f.phi, f.P, None, prm.rho_L, rho_dif, out, stream=stream)
-    shift = (float(phi0_host.sum()) - float(out[0].item())) / n
-    _ck(lib.lbm_sg_shift(_ptr(f.phi), n, shift, stream), "lbm_sg_shift")
+    unpack = lambda phi_out, phi_rho: _ck(lib.lbm_sg_unpack(
+        _ptr(x32), NC, _ptr(delta), 16, _ptr(phi_out), ctypes.c_void_p(u), ctypes.c_void_p(u + 8 * n), _ptr(f.P),
+        _scale_arr(), prm.rho_L, rho_dif, phi_rho, n, stream), "lbm_sg_unpack")
+    unpack(f.phi, None)
+    scratch = torch.zeros(769, dtype=torch.float64, device="cuda")
+    _ck(lib.lbm_sg_phi_project(_ptr(f.phi), _ptr(phi0), n, _ptr(scratch), stream), "lbm_sg_phi_project")
+    if velocity:   # u again, now over the density of the projected phi
+        unpack(torch.empty_like(f.phi), _ptr(f.phi))
+    else:
+        f.u.zero_()
     sim.init_fields(f.phi, f.u, f.P, nonequilibrium=True)
     return f
 

@@ -12,12 +12,12 @@
   nu_water = 0.17, W = 2.5, g = 1e-7, walls normal to y), FP32, started from
   the analytic profile (FP64 quadrature of d/dy(eta u') = -rho g with the tanh
   density, the interpolated viscosity and u = 0 at the halfway walls): the
-  velocity and the interface shear stress stay at the quadrature's, while the
-  uncorrected model (no Eq. 13) moves away from it at the interface.
+  velocity stays at the quadrature's over 40000 steps, as the FP64 oracle's
+  does, while the uncorrected model (no Eq. 13) leaves it or diverges.
 """
 import numpy as np
 import pytest
-from scipy.integrate import cumulative_trapezoid, trapezoid
+from scipy.integrate import cumulative_trapezoid
 
 from oracle import pflbm as O
 from paper_1812_00118_gb300 import inputs as I
@@ -122,7 +122,7 @@ def channel_quadrature(ny, W, ratio, g, nu_H=0.17, mu_ratio=100.0):
 
 
 def run_channel(L, hocorr, steps, ny=256, W=2.5, ratio=1000.0, g=1e-7):
-    y, ua, stress, nu_L = channel_quadrature(ny, W, ratio, g)
+    y, ua, _, nu_L = channel_quadrature(ny, W, ratio, g)
     prm = L.make_params(M=0.1, W=W, sigma=0.01, rho_L=1.0 / ratio, rho_H=1.0, nu_L=nu_L, nu_H=0.17,
                         g=(g, 0.0, 0.0), hocorr=hocorr, store=L.F32)
     nx = nz = 4
@@ -137,33 +137,22 @@ def run_channel(L, hocorr, steps, ny=256, W=2.5, ratio=1000.0, g=1e-7):
     rho = prm.rho_L + f * (prm.rho_H - prm.rho_L)
     ux = (ru[: f.size].reshape(nz, ny, nx) / rho).mean(axis=(0, 2))
     u_nodes = np.interp(np.arange(ny), y, ua)
-    prof_err = np.abs(ux - u_nodes).max() / np.abs(u_nodes).max()
-    # interface shear stress: eta u' is continuous, u' jumps by the viscosity
-    # ratio within the interface, so compare the velocity change across the
-    # interface cell, u(j+1) - u(j), with its quadrature, the integral of
-    # (eta u') / eta over [j, j+1]
-    j = ny // 2 - 1
-    sel = (y >= j) & (y <= j + 1)
-    tL, tH = nu_L / T + 0.5, 0.17 / T + 0.5
-    phif = 0.5 + 0.5 * np.tanh(2 * ((ny / 2 - 0.5) - y[sel]) / W)
-    om = 1 / tL + phif * (1 / tH - 1 / tL)
-    eta = (prm.rho_L + phif * (prm.rho_H - prm.rho_L)) * T * (1 / om - 0.5)
-    du_ana = trapezoid(stress[sel] / eta, y[sel])
-    du_num = ux[j + 1] - ux[j]
-    return prof_err, abs(du_num - du_ana) / abs(du_ana)
+    return np.abs(ux - u_nodes).max() / np.abs(u_nodes).max()
 
 
 def test_layered_channel_256_against_quadrature(lbm):
-    """4 x 256 x 4 channel, density ratio 1000, g = 1e-7, FP32, 40000 steps
-    from the analytic profile: velocity within 2 % of the quadrature's
-    maximum, and the velocity change across the interface cell (the
-    interface shear stress integrated over the cell) within 3 %; without
-    Eq. 13 the profile and the interface stress leave it (the interface peak
-    of Section 3; at density ratio 1000 the uncorrected model diverges)."""
-    prof, tau = run_channel(lbm, 1, 40000)
-    prof0, tau0 = run_channel(lbm, 0, 40000)
-    # the uncorrected model may also diverge at this density ratio (Section 3)
-    prof0, tau0 = (v if np.isfinite(v) else np.inf for v in (prof0, tau0))
-    print("channel 256: with Eq. 13 profile %.3e stress %.3e; without %.3e %.3e" % (prof, tau, prof0, tau0))
-    assert prof < 0.02 and tau < 0.03, (prof, tau)
-    assert prof0 > 2 * prof or tau0 > 2 * tau, (prof0, tau0)
+    """4 x 256 x 4 channel, density ratio 1000, dynamic viscosity ratio 100,
+    g = 1e-7, FP32, 40000 steps from the analytic profile: the velocity stays
+    within 1 % of the quadrature's maximum (the FP64 oracle on the same grid
+    ends 0.52 % from it after 40000 steps; the GPU run measured 0.53 %), and
+    without Eq. 13 the run leaves that profile or diverges (the interface peak
+    of Section 3).  The interface sits next to the velocity maximum, where the
+    shear stress passes through zero, so the velocity change across the
+    interface cell (7e-8, against node errors of 1e-5 in the GPU run and in
+    the oracle alike) does not resolve the stress; the profile does."""
+    prof = run_channel(lbm, 1, 40000)
+    prof0 = run_channel(lbm, 0, 40000)
+    prof0 = prof0 if np.isfinite(prof0) else np.inf   # the uncorrected model may diverge (Section 3)
+    print("channel 256: profile error with Eq. 13 %.3e, without %.3e" % (prof, prof0))
+    assert prof < 0.01, prof
+    assert prof0 > 2 * prof, prof0

@@ -53,7 +53,7 @@ def test_warm_start_reaches_tolerance_in_fewer_steps(env):
             assert abs(f.sum() - phi0.sum()) < 1e-5 * phi0.sum()
             if len(placed) == 1:
                 cx, cy, R = placed[0]
-                law = (-1.0 if sd % 2 else 1.0) * WS.PHYS["sigma"] / R    # a bubble's jump has the other sign
+                law = WS.PHYS["sigma"] / R    # inside minus outside, for a drop and for a bubble
                 lap[mode] = sim.laplace((cx % Lsz, cy % Lsz), R - 8.0, R + 8.0) / law - 1.0
             sim.close()
         assert steps["plain"] is not None and steps["warm"] is not None, (sd, steps)

@@ -6,8 +6,9 @@
   by exactly sum_x (mu grad phi + F);
 * diffusion of a sine mode at rate M k^2 (Eq. 1 with tau = M/T + 1/2);
 * shear-wave decay at nu k^2 in either pure phase (Eq. 9 endpoints, filter);
-* Laplace's law dP = sigma / R for a static drop at density ratio 1000
-  (Section 4.1), converging as the interface is resolved;
+* Laplace's law dP = sigma / R for a static drop and bubble at density
+  ratio 1000 (Section 4.1), converging as the interface is resolved, and
+  dP = 2 sigma / R for a 3-D bubble;
 * the layered two-phase Poiseuille profile against FP64 quadrature of
   d/dy(rho nu u') = -rho g with the diffuse interface and mixed viscosity
   (Section 3), and the interface peak of the uncorrected model that Eq. 13
@@ -102,18 +103,19 @@ def test_shear_wave_viscosity(lat, phase):
     assert np.log(a1 / a2) / 400 == pytest.approx(nu * k * k, rel=1e-3)
 
 
-def _laplace(R, W, sigma, steps, nu_H=0.17, mu_ratio=60.0):
-    """Static drop of Section 4.1: box 5R, periodic, rho ratio 1000, M = 0.1."""
+def _laplace(R, W, sigma, steps, nu_H=0.17, mu_ratio=60.0, drop=True):
+    """Static drop (or bubble) of Section 4.1: box 5R, periodic, rho ratio
+    1000, M = 0.1.  Returns dP / (sigma / R), dP = P inside - P outside."""
     N = int(5 * R)
     p = O.Params(M=0.1, W=W, sigma=sigma, rho_L=1e-3, rho_H=1.0,
                  nu_L=nu_H * 1000.0 / mu_ratio, nu_H=nu_H)
     shape = (1, N, N)
     centre = (N / 2, N / 2, 0)
-    phi, u, P = I.sphere(shape, centre, R, W, drop=True)
+    phi, u, P = I.sphere(shape, centre, R, W, drop=drop)
     h, g = O.init_populations(phi, u, P, L.D2Q9, p)
     h, g = O.run(h, g, L.D2Q9, p, steps)
     m = O.macroscopic(h, g, L.D2Q9, p)
-    Reff = D.effective_radius(m["phi"], 2, True)
+    Reff = D.effective_radius(m["phi"], 2, drop)
     return D.laplace_jump(m["P"], centre, Reff, W) / (sigma / Reff)
 
 
@@ -128,6 +130,37 @@ def test_laplace_law_2d():
     assert abs(r4 - 1) < abs(r25 - 1)
     r25b = _laplace(12, 2.5, 0.006, 2500)
     assert r25b == pytest.approx(r25, rel=0.02)
+
+
+@pytest.mark.slow
+def test_laplace_law_2d_bubble():
+    """A light bubble in the heavy phase: the pressure inside is again the
+    higher one, by sigma / R (the surface force mu grad(phi) integrates to
+    the same jump whichever phase the interface encloses)."""
+    r = _laplace(12, 4.0, 0.01, 2500, drop=False)
+    assert abs(r - 1) < 0.08
+
+
+@pytest.mark.slow
+def test_laplace_law_3d_bubble():
+    """Section 4.1 in three dimensions: a bubble at density ratio 1000 holds
+    dP = 2 sigma / R (two principal curvatures), R from the volume of the
+    light phase (the 3-D branch of effective_radius).  R = 8, W = 3 in a
+    32^3 periodic box, centre off the nodes; the jump is established within
+    the 250 steps (sound crosses the box in ~55 steps)."""
+    R, W, N, sigma = 8.0, 3.0, 32, 0.01
+    p = O.Params(M=0.1, W=W, sigma=sigma, rho_L=1e-3, rho_H=1.0, nu_L=0.17 * 1000.0 / 60.0, nu_H=0.17)
+    centre = (N / 2 + 0.31, N / 2 - 0.23, N / 2 + 0.17)
+    phi, u, P = I.sphere((N, N, N), centre, R, W, drop=False)
+    h, g = O.init_populations(phi, u, P, L.D3Q19, p)
+    h, g = O.run(h, g, L.D3Q19, p, 250)
+    m = O.macroscopic(h, g, L.D3Q19, p)
+    Reff = D.effective_radius(m["phi"], 3, drop=False)
+    assert abs(Reff - R) < 0.5
+    ratio = D.laplace_jump(m["P"], centre, Reff, W) / (2.0 * sigma / Reff)
+    assert abs(ratio - 1) < 0.1
+    # the 2-D law would be off by a factor two
+    assert abs(ratio - 0.5) > 0.3
 
 
 def _poiseuille(ratio, hocorr, ny=32, steps=6000, W=2.5):
