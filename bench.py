@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--ttt-cases", type=int, default=1000,
                     help="ttt: training cases (each gives 20 snapshot pairs 2000 steps apart)")
     ap.add_argument("--ttt-iters", type=int, default=4000, help="ttt: Adam iterations (mini-batch 8)")
-    ap.add_argument("--ttt-apply", type=int, default=20,
+    ap.add_argument("--ttt-apply", type=int, default=4,
                     help="ttt: surrogate applications at inference (each jumps 2000 steps)")
     ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt", "rising"], default="bubble128",
                     help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
@@ -724,11 +724,13 @@ def run_rising(args):
 
 
 # ---------------------------------------------------------------- ttt
-TTT_METRIC = "D2Q9 drop/bubble relaxation time-to-tolerance (ms), 8 held-out 256^2 cases, mean"
-TTT_WORKLOAD = ("1-4 static drops or bubbles in a periodic 256^2 box (radii 12-48 capped at L/4, density ratio 1000, "
-                "sigma 0.01, W 4, M 0.1, nu 1/60), started from u = 0, P = 0; converged when "
-                "||P(t) - P(t-100)|| / ||P(t)|| < 1e-6 on 3 checks in a row; accuracy: phi total, mean-removed P "
-                "against plain FP32, Laplace jump against sigma/R on the single-drop cases")
+TTT_TOLS = (1e-3, 1e-4, 1e-5, 1e-6)
+TTT_METRIC = ("D2Q9 drop/bubble relaxation time-to-tolerance (ms to Laplace-jump residual 1e-6), "
+              "8 held-out 256^2 cases, mean")
+TTT_WORKLOAD = ("1-4 static drops or bubbles in a periodic 256^2 box (radii 12-48, density ratio 1000, sigma 0.01, "
+                "W 4, M 0.1, nu 1/60), started from u = 0, P = 0; converged when the Laplace jump J = mean P of the "
+                "bulk heavy phase - mean P of the bulk light phase changes by less than 1e-6 of itself over 100 steps "
+                "on 3 checks in a row; accuracy: phi total, Laplace jump against sigma/R on the single-drop cases")
 
 
 def run_ttt(args):
@@ -741,14 +743,15 @@ def run_ttt(args):
     torch.cuda.set_device(0)
     build.build()
     lbm.load()
-    Lsz, K, tol = 256, 20, 1e-6
+    Lsz, K, tol = 256, 20, TTT_TOLS[-1]
     n_cases, iters, k_apply = args.ttt_cases, args.ttt_iters, args.ttt_apply
     eval_seeds = list(range(5000, 5008))
+    low_seeds = eval_seeds[:2]            # the 16-bit forms run on these two
     zeros2, zeros1 = np.zeros(2 * Lsz * Lsz), np.zeros(Lsz * Lsz)
     clocks = ClockSampler(0)   # the whole workload: data, training and every timed run
     time.sleep(0.3)
     # surrogate: trajectories from the batched solver, training on the GPU
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record()
     S, dropped = WS.generate_snapshots(torch, Lsz, list(range(1000, 1000 + n_cases)), K)
     e[1].record()
@@ -760,13 +763,9 @@ def run_ttt(args):
     n_pairs = int(S.shape[0]) * K
     del S
     torch.cuda.empty_cache()
+    sg_status = int(lbm.load().lbm_sg_status(None))
     sg1 = Surrogate(1, Lsz, Lsz, params=sg.params())
     forms = {}
-
-    def pdiff(P, ref):
-        # pressure differences (the level of P is free): mean-removed fields
-        a, r = P - P.mean(), ref - ref.mean()
-        return float(np.linalg.norm(a - r) / np.linalg.norm(r))
 
     def laplace_err(sim, placed):
         # single-drop or single-bubble cases: the jump inside minus outside against sigma / R (2-D)
@@ -774,82 +773,92 @@ def run_ttt(args):
             return None
         cx, cy, R = placed[0]
         W = WS.PHYS["W"]
-        dP = sim.laplace((cx % Lsz, cy % Lsz), R - 2 * W, R + 2 * W)
-        return dP / (WS.PHYS["sigma"] / R) - 1.0
+        return sim.laplace((cx % Lsz, cy % Lsz), R - 2 * W, R + 2 * W) / (WS.PHYS["sigma"] / R) - 1.0
 
-    def finish(name, sim, phi0, placed, res_steps, ms, ref=None):
+    def record(name, sim, phi0, placed, h, ms, extra_ms=0.0):
         f, P, ru = sim.macro()
-        rec = forms.setdefault(name, {"steps": [], "ms": [], "phi_drift": [], "P_vs_plain": [], "laplace_err": []})
-        rec["steps"].append(res_steps)
-        rec["ms"].append(ms)
+        rec = forms.setdefault(name, {"steps": {str(t): [] for t in TTT_TOLS}, "ms": [], "phi_drift": [],
+                                      "laplace_err": []})
+        for t in TTT_TOLS:
+            rec["steps"][str(t)].append(WS.steps_at(h, t))
+        rec["ms"].append(ms + extra_ms)
         rec["phi_drift"].append(abs(f.sum() - phi0.sum()) / phi0.sum())
-        rec["P_vs_plain"].append(None if ref is None else pdiff(P, ref))
         rec["laplace_err"].append(laplace_err(sim, placed) if np.isfinite(P).all() else None)
-        return P
+        return rec["steps"][str(tol)][-1]
 
-    plain_P, plain_steps = [], []
+    prm = {st: WS.case_params(st) for st in (lbm.F32, lbm.F16S, lbm.BF16S)}
     for sd in eval_seeds:
         phi0, placed = WS.case_fields(Lsz, sd)
-        for name, store, fix in (("plain_f32", lbm.F32, 0), ("plain_f16s", lbm.F16S, 0),
-                                 ("plain_f16s_phifix", lbm.F16S, 100), ("plain_bf16s", lbm.BF16S, 0),
-                                 ("plain_bf16s_phifix", lbm.BF16S, 100)):
-            sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), WS.case_params(store))
-            sim.set_phi_correction(fix)
-            sim.init_fields(phi0, zeros2, zeros1)
-            cap = 400000 if name == "plain_f32" else 2 * plain_steps[-1]
-            st, ms, r = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=cap)
-            ref = None if name == "plain_f32" else plain_P[-1]
-            P = finish(name, sim, phi0, placed, st, ms, ref)
-            if name == "plain_f32":
-                plain_P.append(P)
-                plain_steps.append(st if st is not None else cap)
-            sim.close()
-        # learned warm start: inference + rebuild timed with the run
-        sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), WS.case_params(lbm.F32))
+        sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), prm[lbm.F32])
+        sim.init_fields(phi0, zeros2, zeros1)
+        h = []
+        st, ms, _ = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=2000000, history=h)
+        plain_steps = record("plain_f32", sim, phi0, placed, h, ms)
+        sim.close()
+        cap = plain_steps if plain_steps is not None else 2000000
+        # learned warm start: inference, projection and rebuild timed with the run
+        sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), prm[lbm.F32])
         w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         w0.record()
-        WS.predict_into(torch, sg1, sim, phi0, WS.case_params(lbm.F32), k_apply)
+        WS.predict_into(torch, sg1, sim, phi0, prm[lbm.F32], k_apply)
         w1.record()
         w1.synchronize()
-        st, ms, r = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=2 * plain_steps[-1])
-        finish("warm_f32", sim, phi0, placed, st, ms + w0.elapsed_time(w1), plain_P[-1])
+        h = []
+        st, ms, _ = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=2 * cap, history=h)
+        record("warm_f32", sim, phi0, placed, h, ms, w0.elapsed_time(w1))
         forms["warm_f32"].setdefault("inference_ms", []).append(w0.elapsed_time(w1))
         sim.close()
-    # the same 8 cases as one batch
-    b = lbm.Batch([(Lsz, Lsz)] * len(eval_seeds), WS.case_params(lbm.F32))
+        if sd in low_seeds:
+            for name, store, fix in (("plain_f16s", lbm.F16S, 0), ("plain_f16s_phifix", lbm.F16S, 100),
+                                     ("plain_bf16s", lbm.BF16S, 0), ("plain_bf16s_phifix", lbm.BF16S, 100)):
+                sim = lbm.Simulation(lbm.D2Q9, (Lsz, Lsz), prm[store])
+                sim.set_phi_correction(fix)
+                sim.init_fields(phi0, zeros2, zeros1)
+                h = []
+                st, ms, _ = WS.steps_to_tolerance(torch, sim, tol=tol, max_steps=cap, history=h)
+                record(name, sim, phi0, placed, h, ms)
+                sim.close()
+    # the same 8 cases as one batch (one persistent launch per step for all grids)
+    b = lbm.Batch([(Lsz, Lsz)] * len(eval_seeds), prm[lbm.F32])
     phis, places = [], []
     for k, sd in enumerate(eval_seeds):
         phi0, placed = WS.case_fields(Lsz, sd)
         phis.append(phi0)
         places.append(placed)
         b.grid(k).init_fields(phi0, zeros2, zeros1)
-    done, ms = WS.batch_steps_to_tolerance(torch, b, tol=tol, max_steps=2 * max(plain_steps))
-    rec = {"steps": done, "ms_all_cases": ms, "ms": [ms / len(eval_seeds)] * len(eval_seeds), "phi_drift": [],
-           "P_vs_plain": [], "laplace_err": []}
+    done, ms = WS.batch_steps_to_tolerance(torch, b, tol=tol, max_steps=2000000)
+    rec = {"steps": {str(tol): done}, "ms_all_cases": ms, "ms": [ms / len(eval_seeds)] * len(eval_seeds),
+           "phi_drift": [], "laplace_err": []}
     for k in range(len(eval_seeds)):
         f, P, ru = b.grid(k).macro()
         rec["phi_drift"].append(abs(f.sum() - phis[k].sum()) / phis[k].sum())
-        rec["P_vs_plain"].append(pdiff(P, plain_P[k]))
         rec["laplace_err"].append(laplace_err(b.grid(k), places[k]))
     forms["batch_f32"] = rec
     b.close()
+
+    def mean_or_none(v):
+        ok = [x for x in v if x is not None]
+        return float(np.mean(ok)) if ok else None
+
     summary = {}
     for name, rec in forms.items():
-        ok = [x for x in rec["steps"] if x is not None]
-        summary[name] = {"converged": f"{len(ok)}/{len(rec['steps'])}",
-                         "mean_steps": float(np.mean(ok)) if ok else None,
-                         "mean_ms": float(np.mean(rec["ms"])),
-                         "max_phi_drift": float(max(rec["phi_drift"])),
-                         "max_P_vs_plain_f32": (None if all(v is None for v in rec["P_vs_plain"])
-                                                else float(max(v for v in rec["P_vs_plain"] if v is not None))),
-                         "laplace_err_single_drop_cases": [v for v in rec["laplace_err"] if v is not None]}
-    summary["batch_f32"]["note"] = "all 8 grids in one persistent launch per step; mean_ms = total / 8"
-    for k in ("plain_f16s_phifix", "plain_bf16s_phifix"):
-        summary[k]["note"] = "total of phi re-imposed every 100 steps (lbm_set_phi_correction)"
+        st = rec["steps"]
+        summary[name] = {
+            "cases": len(rec["ms"]),
+            "converged_1e-6": f"{sum(x is not None for x in st[str(tol)])}/{len(st[str(tol)])}",
+            "mean_steps": {t: mean_or_none(v) for t, v in st.items()},
+            "mean_ms": float(np.mean(rec["ms"])),
+            "max_phi_drift": float(max(rec["phi_drift"])),
+            "laplace_err_single_drop_cases": [v for v in rec["laplace_err"] if v is not None]}
+    for t in map(str, TTT_TOLS):
+        p_, w_ = forms["plain_f32"]["steps"][t], forms["warm_f32"]["steps"][t]
+        summary["warm_f32"].setdefault("plain_over_warm_steps", {})[t] = [
+            a / b_ for a, b_ in zip(p_, w_) if a is not None and b_ is not None]
     summary["warm_f32"]["mean_inference_ms"] = float(np.mean(forms["warm_f32"]["inference_ms"]))
-    ratios = [p / w for p, w in zip(forms["plain_f32"]["steps"], forms["warm_f32"]["steps"])
-              if p is not None and w is not None]
-    summary["warm_f32"]["plain_over_warm_steps"] = ratios
+    summary["batch_f32"]["note"] = "all 8 grids in one persistent launch per step; mean_ms = total / 8"
+    for k in ("plain_f16s", "plain_f16s_phifix", "plain_bf16s", "plain_bf16s_phifix"):
+        summary[k]["note"] = ("first 2 eval cases, capped at the plain FP32 run's steps"
+                              + ("; total of phi re-imposed every 100 steps" if k.endswith("phifix") else ""))
     warm = summary["warm_f32"]["mean_ms"]
     clk = clocks.stop()
     line = {
@@ -863,8 +872,9 @@ def run_ttt(args):
                       "snapshots_per_case": K + 1, "iterations": iters, "batch": 8,
                       "data_ms": e[0].elapsed_time(e[1]), "train_ms": e[1].elapsed_time(e[2]),
                       "loss_first_last": [hist[0][1], hist[-1][1]], "identity_loss": identity,
-                      "flops_per_image_forward": sg1.flops_per_image(backward=False),
-                      "kernels": "lbm_sg_* BF16 mma.sync implicit-GEMM convolutions, FP32 accumulation"},
+                      "sg_status": sg_status, "flops_per_image_forward": sg1.flops_per_image(backward=False),
+                      "kernels": "lbm_sg_* tcgen05 implicit-GEMM convolutions (TMEM accumulator), mma.sync weight "
+                                 "gradient, FP32 accumulation"},
     }
     print(json.dumps(line), flush=True)
 

@@ -123,6 +123,15 @@ int lbm_sg_unpack(const float* x32, int cs32, const float* delta, int csd, doubl
  * warm-start comparison: ||P(t) - P(t - k)|| / ||P(t)||. */
 int lbm_sg_residual(const double* a, const double* b, long long n, double* out, double* scratch, void* stream);
 
+/* out (device, 4 doubles) = (mean P over the bulk heavy phase phi >= 1 - d,
+ * mean P over the bulk light phase phi <= d, and the two node counts), FP64
+ * in a fixed order; scratch: 1024 doubles; 0 <= d < 1/2.  out[0] - out[1] is
+ * the Laplace pressure jump of the whole state (Section 4.1), the quantity
+ * whose relative change between checks is the warm-start comparison's
+ * convergence measure. */
+int lbm_sg_phase_pressure(const double* phi, const double* P, long long n, double d, double* out, double* scratch,
+                          void* stream);
+
 /* iters times two explicit diffusion passes a <- a + k lap(a) (five-point,
  * periodic in each of N images of H x W, 0 <= k <= 1/4, tmp: N H W doubles):
  * removes the block-scale roughness of a prediction before it seeds a run. */

@@ -439,6 +439,7 @@ int lbm_init_fields(lbm_ctx* c, const double* phi, const double* u, const double
 }
 
 int lbm_init_fields_ex(lbm_ctx* c, const double* phi, const double* u, const double* P, int on_device, int flags) {
+    lbm::NvtxRange range("lbm_init_fields");
     if (!c || !phi || !u || !P || (flags & ~LBM_INIT_NONEQ)) return LBM_EINVAL;
     const long long N = c->G.N;
     int rc = ensure_scratch(c);
@@ -474,7 +475,10 @@ int lbm_init_fields_ex(lbm_ctx* c, const double* phi, const double* u, const dou
 
 static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev);
 
-int lbm_step(lbm_ctx* c, int n) { return step_impl(c, n, nullptr); }
+int lbm_step(lbm_ctx* c, int n) {
+    lbm::NvtxRange range("lbm_step");
+    return step_impl(c, n, nullptr);
+}
 
 int lbm_step_profiled(lbm_ctx* c, int n, double* kernel_ms) {
     if (!c || n < 0 || !kernel_ms || c->owner) return LBM_EINVAL;
@@ -545,6 +549,7 @@ static int step_impl(lbm_ctx* c, int n, cudaEvent_t* ev) {
 }
 
 int lbm_macro(lbm_ctx* c, double* phi, double* P, double* rho_u, int on_device) {
+    lbm::NvtxRange range("lbm_macro");
     if (!c) return LBM_EINVAL;
     int rc = compute_fields(c);
     if (rc) return rc;
@@ -632,6 +637,7 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
 }
 
 int lbm_diagnostics(lbm_ctx* c, double out[4]) {
+    lbm::NvtxRange range("lbm_diagnostics");
     if (!c || !out) return LBM_EINVAL;
     int rc = compute_fields(c);
     if (rc) return rc;

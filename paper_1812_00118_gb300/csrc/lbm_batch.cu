@@ -282,6 +282,7 @@ lbm_ctx* lbm_batch_grid(lbm_batch* b, int i) {
 }
 
 int lbm_batch_step(lbm_batch* b, int n) {
+    lbm::NvtxRange range("lbm_batch_step");
     if (!b || n < 0) return LBM_EINVAL;
     int rc = upload_cases(b, false);
     if (rc) return rc;

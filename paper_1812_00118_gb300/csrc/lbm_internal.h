@@ -2,12 +2,23 @@
 // per-lattice translation units that instantiate the kernels.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
+
+// NVTX range over a host call (steps, initialisation, read-back,
+// diagnostics): a profiler's timeline shows the library's calls around its
+// kernels.  Costs nothing without a tool attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TmaMaps;
 

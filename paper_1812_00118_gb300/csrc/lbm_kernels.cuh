@@ -1213,10 +1213,13 @@ batch_step_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D,
 }
 
 // ---------------------------------------------------------------- helper kernels
+// (node counts are below 2^31, checked on the host: 32-bit division)
 __device__ __forceinline__ void node_coords(const Geom& G, long long n, int* x, int* y, int* z) {
-    *x = (int)(n % G.NX);
-    *y = (int)((n / G.NX) % G.NY);
-    *z = (int)(n / ((long long)G.NX * G.NY));
+    const int k = (int)n;
+    const int q = k / G.NX;
+    *x = k - q * G.NX;
+    *z = q / G.NY;
+    *y = q - *z * G.NY;
 }
 
 // h_0 += *delta at every node (the rest population pulls from its own cell,
@@ -1255,26 +1258,29 @@ __global__ void phi_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::
     phi[n] = acc;
 }
 
-// CD stencils of a double phi field (node order) at node (x, y, z).
-template <int LAT>
+// CD stencils of a double field (node order) at node (x, y, z), in the
+// arithmetic type R (the values are rounded to R first): FP64 for the
+// diagnostics and FP64 storage, FP32 for initialising FP32 and 16-bit
+// storage (whose kernels compute in FP32; GB300's FP64 rate is low).
+template <int LAT, typename R = double>
 __device__ __forceinline__ void stencils(const double* __restrict__ phi, const Geom& G, int x, int y, int z,
-                                         double* gx, double* gy, double* gz, double* lap) {
+                                         R* gx, R* gy, R* gz, R* lap) {
     using L = Lattice<LAT>;
-    auto at = [&](int a, int b, int c) { return phi[(long long)a + (long long)G.NX * ((long long)b + (long long)G.NY * c)]; };
-    const double f = at(x, y, z);
-    double ax = 0, ay = 0, az = 0, l = 0;
+    auto at = [&](int a, int b, int c) { return (R)phi[a + G.NX * (b + G.NY * c)]; };
+    const R f = at(x, y, z);
+    R ax = 0, ay = 0, az = 0, l = 0;
     Unroll<1, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         constexpr double W = L::w[i];
-        const double v = at(stencil_coord(x + CX, G.NX, G.wall[0]), stencil_coord(y + CY, G.NY, G.wall[1]),
-                            stencil_coord(z + CZ, G.NZ, G.wall[2]));
-        ax += CX * W * v;
-        ay += CY * W * v;
-        az += CZ * W * v;
-        l += W * (v - f);
+        const R v = at(stencil_coord(x + CX, G.NX, G.wall[0]), stencil_coord(y + CY, G.NY, G.wall[1]),
+                       stencil_coord(z + CZ, G.NZ, G.wall[2]));
+        if (CX) ax += (R)(CX * W) * v;
+        if (CY) ay += (R)(CY * W) * v;
+        if (CZ) az += (R)(CZ * W) * v;
+        l += (R)W * (v - f);
     });
-    *gx = 3 * ax; *gy = 3 * ay; *gz = 3 * az; *lap = 6 * l;
+    *gx = (R)3 * ax; *gy = (R)3 * ay; *gz = (R)3 * az; *lap = (R)6 * l;
 }
 
 // Macroscopic fields (phi given) in double: P and u (internal axes).
@@ -1353,11 +1359,9 @@ __global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
     if (n >= G.N) return;
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
-    double gx, gy, gz, lap;
-    stencils<LAT>(phi, G, x, y, z, &gx, &gy, &gz, &lap);
     NodeState<R> s;
     s.phi = (R)phi[n];
-    s.gx = (R)gx; s.gy = (R)gy; s.gz = (R)gz; s.lap = (R)lap;
+    stencils<LAT, R>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
     const R rho_dif = p.rho_dif;
     s.rho = p.rho_L + s.phi * rho_dif;
     s.mu = p.beta * s.phi * (s.phi - (R)1) * (s.phi - (R)0.5) - p.kappa * s.lap;
@@ -1380,14 +1384,14 @@ __global__ void init_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>:
     // Pi(1) components (zero without neq)
     R nxx = 0, nyy = 0, nzz = 0, nxy = 0, nxz = 0, nyz = 0, ntr3 = 0;
     if (neq) {
-        double d[3][3], l;   // d[a][b] = d_a u_b
-        stencils<LAT>(ux, G, x, y, z, &d[0][0], &d[1][0], &d[2][0], &l);
-        if (L::kHasY) stencils<LAT>(uy, G, x, y, z, &d[0][1], &d[1][1], &d[2][1], &l);
-        else d[0][1] = d[1][1] = d[2][1] = 0.0;
-        stencils<LAT>(uz, G, x, y, z, &d[0][2], &d[1][2], &d[2][2], &l);
-        const double pc = s.phi < (R)0 ? 0.0 : (s.phi > (R)1 ? 1.0 : (double)s.phi);
-        const double tau = 1.0 / ((double)p.om_L + pc * (double)p.om_dif);
-        const double cf = -tau * (1.0 / 3.0) * (double)s.rho;
+        R d[3][3], l;   // d[a][b] = d_a u_b
+        stencils<LAT, R>(ux, G, x, y, z, &d[0][0], &d[1][0], &d[2][0], &l);
+        if (L::kHasY) stencils<LAT, R>(uy, G, x, y, z, &d[0][1], &d[1][1], &d[2][1], &l);
+        else d[0][1] = d[1][1] = d[2][1] = (R)0;
+        stencils<LAT, R>(uz, G, x, y, z, &d[0][2], &d[1][2], &d[2][2], &l);
+        const R pc = s.phi < (R)0 ? (R)0 : (s.phi > (R)1 ? (R)1 : s.phi);
+        const R tau = (R)1 / (p.om_L + pc * p.om_dif);
+        const R cf = -tau * (R)(1.0 / 3.0) * s.rho;
         nxx = (R)(cf * 2 * d[0][0]); nyy = (R)(cf * 2 * d[1][1]); nzz = (R)(cf * 2 * d[2][2]);
         nxy = (R)(cf * (d[0][1] + d[1][0])); nxz = (R)(cf * (d[0][2] + d[2][0])); nyz = (R)(cf * (d[1][2] + d[2][1]));
         ntr3 = (nxx + nyy + nzz) * (R)(1.0 / 3.0);

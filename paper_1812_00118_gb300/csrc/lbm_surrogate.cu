@@ -63,24 +63,26 @@ __device__ __forceinline__ long long shift_pixel(long long p, int H, int W, int 
 //
 // A CTA of 128 threads owns 128 consecutive pixels and every output channel
 // (MMA shape M = 128, N = Co, K = 16).  The K loop runs over stages (tap,
-// block of up to 128 input channels).  Per stage every thread copies its
+// block of up to 64 input channels).  Per stage every thread copies its
 // pixel's shifted channel row (16-byte cp.async; rows past the last pixel
-// are zero-filled) and a share of the tap's weight rows into one of two
+// are zero-filled) and a share of the tap's weight rows into one of four
 // shared-memory buffers, in the no-swizzle canonical layout of the tensor
 // core: 8 x 16-byte core matrices, rows 16 bytes apart, 8-row groups 128
 // bytes apart (stride byte offset), the 8-channel chunks one after another
-// (leading byte offset = rows x 16 bytes).  Thread 0 then issues the stage's
-// MMAs and commits them to the buffer's mbarrier; the copies of the next
-// stage go to the other buffer while they run, and a buffer is refilled only
-// after the mbarrier shows its previous MMAs done.  The epilogue reads the
-// accumulator back with tcgen05.ld (warp w reads lanes 32w..32w+31, one pixel
-// per thread), adds the bias and stores FP32.
+// (leading byte offset = rows x 16 bytes).  The copies run two stages ahead
+// of the MMAs: once a stage's copies have landed, thread 0 issues its MMAs
+// and commits them to the buffer's mbarrier, and a buffer is refilled only
+// after its mbarrier shows the MMAs that read it done.  The epilogue reads
+// the accumulator back with tcgen05.ld (warp w reads lanes 32w..32w+31, one
+// pixel per thread), adds the bias and stores FP32.
 //
 // Every wait is bounded: a wait that gives up sets *err (read by
 // lbm_sg_status) and the CTA skips its epilogue, frees its tensor memory and
 // returns.
 constexpr int kTcM = 128;        // pixels per CTA (MMA M)
-constexpr int kTcK = 128;        // input channels per stage
+constexpr int kTcK = 64;         // input channels per stage
+constexpr int kTcBuf = 4;        // stage buffers in shared memory
+constexpr int kTcAhead = 2;      // stages whose copies are in flight ahead of the MMAs
 constexpr long kTcPolls = 1L << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -144,14 +146,14 @@ __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, const float* __restrict__ bias,
                float* __restrict__ y, int csy, long long M, int H, int W, int Ci, int Co, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[kTcBuf];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long p0 = (long long)blockIdx.x * kTcM;
     const int kcap = Ci < kTcK ? Ci : kTcK;   // channels per stage buffer
-    const uint32_t a_bytes = kTcM * kcap * 2, b_bytes = (uint32_t)Co * kcap * 2;
+    const uint32_t a_bytes = kTcM * kcap * 2, stage_bytes = a_bytes + (uint32_t)Co * kcap * 2;
     const uint32_t sb = smem_u32(smem);
-    // buffer b: A at sb + b a_bytes, B at sb + 2 a_bytes + b b_bytes; its barrier at bar0 + 8 b
+    // buffer b: A at sb + b stage_bytes, B a_bytes after it; its barrier at bar0 + 8 b
     const uint32_t bar0 = smem_u32(&bars[0]);
     const uint32_t ncols = Co <= 32 ? 32u : (Co <= 64 ? 64u : 128u);
     if (warp == 0) {
@@ -161,8 +163,8 @@ conv_tc_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        for (int b = 0; b < kTcBuf; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -174,63 +176,89 @@ conv_tc_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, 
     const int nst = 9 * nkb;
     const long long p = p0 + tid;
     const bool in = p < M;
-    bool ok = true;
-    int issued = 0;   // stages whose MMAs were issued and committed
-    for (int st = 0; st < nst; ++st) {
-        const int b = st & 1;
-        const uint32_t a_s = sb + b * a_bytes, b_s = sb + 2 * a_bytes + b * b_bytes, bar = bar0 + 8 * b;
+    // the copies of stage st into buffer st % kTcBuf, as one commit group
+    auto issue = [&](int st) {
+        const uint32_t a_s = sb + (st % kTcBuf) * stage_bytes, b_s = a_s + a_bytes;
         const int tap = st / nkb, kc0 = (st % nkb) * kTcK;
         const int kw = Ci - kc0 < kTcK ? Ci - kc0 : kTcK;
-        // the MMAs of stage st - 2 read this buffer: the (st - 2) / 2-th phase
-        // of its barrier; every thread waits, and all give up together
-        if (st >= 2) {
-            const bool done = mbar_wait_bounded(bar, (uint32_t)((st - 2) >> 1) & 1u, kTcPolls);
-            if (!__syncthreads_and(done)) {
-                ok = false;
-                break;
-            }
-        }
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const bf16* src = x + (in ? shift_pixel(p, H, W, dy, dx) : 0) * csx + kc0;
+        const bf16* src = x + (in ? shift_pixel(p, H, W, tap / 3 - 1, tap % 3 - 1) : 0) * csx + kc0;
         for (int c = 0; c < kw / 8; ++c) cp_async16(a_s + c * (kTcM * 16) + tid * 16, src + c * 8, in ? 16u : 0u);
         for (int k = tid; k < Co * (kw / 8); k += kTcM) {
             const int co = k % Co, c = k / Co;
             cp_async16(b_s + c * (Co * 16) + co * 16, w + ((long long)co * 9 + tap) * Ci + kc0 + c * 8, 16u);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    };
+    // stage s commits to barrier s % kTcBuf: its (s / kTcBuf)-th phase
+    auto wait_stage = [&](int st) {
+        return mbar_wait_bounded(bar0 + 8 * (st % kTcBuf), (uint32_t)(st / kTcBuf) & 1u, kTcPolls);
+    };
+    bool ok = true;
+    int issued = 0;   // stages whose MMAs were issued and committed
+    for (int st = 0; st < kTcAhead && st < nst; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        // copies run kTcAhead stages ahead; buffer (st + kTcAhead) % kTcBuf was
+        // last read by the MMAs of stage st + kTcAhead - kTcBuf
+        const int nxt = st + kTcAhead;
+        if (nxt < nst) {
+            if (nxt >= kTcBuf && !__syncthreads_and(wait_stage(nxt - kTcBuf))) {
+                ok = false;
+                break;
+            }
+            issue(nxt);
+        }
+        // stage st's group is complete once at most the newer ones are pending
+        const int newer = (nst - 1 < st + kTcAhead ? nst - 1 : st + kTcAhead) - st;
+        if (newer >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else if (newer == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
         // the copies were written through the generic proxy; the MMAs read through the async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_s = sb + (st % kTcBuf) * stage_bytes, b_s = a_s + a_bytes;
+            const int kc0 = (st % nkb) * kTcK;
+            const int kw = Ci - kc0 < kTcK ? Ci - kc0 : kTcK;
             for (int s = 0; s < kw / 16; ++s) {
                 const uint64_t ad = tc_smem_desc(a_s + 2 * s * (kTcM * 16), kTcM * 16, 128);
                 const uint64_t bd = tc_smem_desc(b_s + 2 * s * (Co * 16), Co * 16, 128);
                 tc_mma(tmem, ad, bd, idesc, (st > 0 || s > 0) ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8 * (st % kTcBuf))
                          : "memory");
         }
         issued = st + 1;
     }
+    // copies still in flight on the failure path land before the CTA leaves
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the last committed stage completes after every earlier MMA of the CTA
     // (waited for on the failure path too, before the tensor memory is freed)
     if (issued > 0) {
-        const bool done = mbar_wait_bounded(bar0 + 8 * ((issued - 1) & 1), (uint32_t)((issued - 1) >> 1) & 1u, kTcPolls);
+        const bool done = wait_stage(issued - 1);
         ok = __syncthreads_and(ok && done) != 0;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const long long pr = p0 + 32 * warp + lane;
         const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const bool vec = (csy & 3) == 0 && ((uintptr_t)y & 15) == 0;
         for (int c0 = 0; c0 < Co; c0 += 16) {
             float v[16];
             tc_ld16(trow + (uint32_t)c0, v);
             if (pr < M) {
-                float* out = y + pr * csy + c0;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) out[i] = v[i] + (bias ? bias[c0 + i] : 0.0f);
+                for (int i = 0; i < 16; ++i) v[i] += bias ? bias[c0 + i] : 0.0f;
+                float* out = y + pr * csy + c0;
+                if (vec) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) out[i] = v[i];
+                }
             }
         }
     }
@@ -241,10 +269,10 @@ conv_tc_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, 
     if (!ok && tid == 0) atomicExch(err, 1);
 }
 
-// two stage buffers of A (128 pixels) and B (Co weight rows), min(Ci, 128) channels each
+// kTcBuf stage buffers of A (128 pixels) and B (Co weight rows), min(Ci, kTcK) channels each
 size_t conv_tc_smem_bytes(int Ci, int Co) {
     const size_t k = Ci < kTcK ? (size_t)Ci : (size_t)kTcK;
-    return 2u * (kTcM + (size_t)Co) * k * 2;
+    return (size_t)kTcBuf * (kTcM + (size_t)Co) * k * 2;
 }
 
 __device__ int g_sg_err;   // a bounded wait of a surrogate kernel gave up
@@ -567,6 +595,39 @@ __global__ void residual_finish_kernel(const double* __restrict__ part, int nb, 
     out[1] = a2;
 }
 
+// block partials of (sum P, count) over the bulk heavy phase (phi >= 1 - d)
+// and over the bulk light phase (phi <= d), FP64, fixed order
+__global__ void phase_pressure_partial_kernel(const double* __restrict__ phi, const double* __restrict__ P,
+                                              long long n, double d, double* __restrict__ part) {
+    __shared__ double sh[4][kThreads];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double f = phi[k];
+        if (f >= 1.0 - d) { a[0] += P[k]; a[1] += 1.0; }
+        if (f <= d) { a[2] += P[k]; a[3] += 1.0; }
+    }
+    for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = a[j];
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 4; ++j) part[4 * blockIdx.x + j] = sh[j][0];
+}
+
+__global__ void phase_pressure_finish_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < 4; ++j) a[j] += part[4 * b + j];
+    out[0] = a[1] > 0.0 ? a[0] / a[1] : 0.0;
+    out[1] = a[3] > 0.0 ? a[2] / a[3] : 0.0;
+    out[2] = a[1];
+    out[3] = a[3];
+}
+
 // phi <- clip(phi0 + m (phi - phi0), 0, 1), m = 4 phi0 (1 - phi0): the
 // predicted change of phi kept inside the interface band of the start and
 // none in the bulk phases; block partials of sum phi0, sum phi, sum 4 phi (1 - phi)
@@ -652,13 +713,13 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     // 16-byte copies: channel rows and slices start on 16-byte boundaries
     if (csx % 8 || ((uintptr_t)x & 15) || ((uintptr_t)w & 15)) return LBM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = 192 * 1024;   // TEMPORARY headroom for the first hardware check of the descriptor reading
+    const size_t smem = conv_tc_smem_bytes(Ci, Co);
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         if (cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 192 * 1024) != cudaSuccess)
+                                 (int)conv_tc_smem_bytes(kTcK, 128)) != cudaSuccess)
             return LBM_ECUDA;
         attr_set[dev] = true;
     }
@@ -831,6 +892,16 @@ int lbm_sg_residual(const double* a, const double* b, long long n, double* out, 
     cudaStream_t s = (cudaStream_t)stream;
     residual_partial_kernel<<<nb, kThreads, 0, s>>>(a, b, n, scratch);
     residual_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
+    return check(cudaGetLastError());
+}
+
+int lbm_sg_phase_pressure(const double* phi, const double* P, long long n, double d, double* out, double* scratch,
+                          void* stream) {
+    if (!phi || !P || !out || !scratch || n < 1 || !(d >= 0.0 && d < 0.5)) return LBM_EINVAL;
+    const int nb = 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    phase_pressure_partial_kernel<<<nb, kThreads, 0, s>>>(phi, P, n, d, scratch);
+    phase_pressure_finish_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
     return check(cudaGetLastError());
 }
 

@@ -119,6 +119,7 @@ SIGNATURES = [
     ("lbm_sg_smooth", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      _VP]),
     ("lbm_sg_phi_project", ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP]),
+    ("lbm_sg_phase_pressure", ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_double, _VP, _VP, _VP]),
     ("lbm_sg_shift", ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),

@@ -15,10 +15,13 @@ interfaces, total of phi restored in FP64: lbm_sg_phi_project).  The plain
 solver then continues and decides convergence, so the method stays the
 judge and the fallback.
 
-Convergence (time-to-tolerance): every `check_every` steps the pressure
-field P(t) is compared with P(t - check_every); the run has converged when
-||P(t) - P(t - k)|| / ||P(t)|| < tol for `consecutive` checks in a row
-(FP64 sums on the GPU, lbm_sg_residual).
+Convergence (time-to-tolerance): every `check_every` steps the Laplace
+jump of the state, J = mean P of the bulk heavy phase minus mean P of the
+bulk light phase, is compared with its value `check_every` steps before;
+the run has converged when |J(t) - J(t - k)| / |J(t)| < tol for
+`consecutive` checks in a row (FP64 sums on the GPU,
+lbm_sg_phase_pressure).  The node-wise pressure residual ||P(t) - P(t - k)||
+/ ||P(t)|| is available too; FP32 rounding noise keeps it above ~1e-5.
 
 Everything that computes runs in the library's kernels; PyTorch allocates
 device memory and copies it.
@@ -202,30 +205,65 @@ def predict_into(torch, sg1, sim, phi0_host, prm, k_apply, velocity=True):
     return f
 
 
-def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max_steps=200000):
-    """Steps until ||P(t) - P(t - check_every)|| / ||P(t)|| < tol for
-    `consecutive` checks (None if not within max_steps); returns (steps,
-    device ms of the whole loop including the checks, last residual)."""
-    lib = L.load()
-    n = sim.N
-    stream = torch.cuda.current_stream().cuda_stream
-    P = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(2)]
-    out = torch.zeros(2, dtype=torch.float64, device="cuda")
-    scratch = torch.zeros(512, dtype=torch.float64, device="cuda")
-    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+class _Residual:
+    """The convergence measure of one grid, on the GPU in FP64.
+
+    "laplace" (default): J = mean P of the bulk heavy phase (phi >= 0.99)
+    minus mean P of the bulk light phase (phi <= 0.01), the Laplace jump of
+    the whole state (lbm_sg_phase_pressure); r = |J(t) - J(t - k)| / |J(t)|.
+    "field": r = ||P(t) - P(t - k)|| / ||P(t)|| over every node
+    (lbm_sg_residual), which FP32 rounding noise of the pressure field keeps
+    above ~1e-5."""
+
+    def __init__(self, torch, sim, measure="laplace"):
+        self.lib, self.sim, self.measure = L.load(), sim, measure
+        self.stream = torch.cuda.current_stream().cuda_stream
+        n = sim.N
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+        self.phi, self.P = z(n), [z(n), z(n)]
+        self.out, self.scratch = z(4), z(1024)
+        self.cur, self.J = 0, None
+        self._read()
+
+    def _read(self):
+        self.sim.macro(self.phi, self.P[self.cur], None)
+        if self.measure == "laplace":
+            _ck(self.lib.lbm_sg_phase_pressure(_ptr(self.phi), _ptr(self.P[self.cur]), self.sim.N, 0.01,
+                                               _ptr(self.out), _ptr(self.scratch), self.stream),
+                "lbm_sg_phase_pressure")
+            o = self.out.tolist()
+            self.J = o[0] - o[1]
+
+    def update(self):
+        """Read the fields again; the residual against the previous read."""
+        prev_J = self.J
+        self.cur = 1 - self.cur
+        self._read()
+        if self.measure == "laplace":
+            return abs(self.J - prev_J) / abs(self.J) if self.J != 0 else float("inf")
+        _ck(self.lib.lbm_sg_residual(_ptr(self.P[self.cur]), _ptr(self.P[1 - self.cur]), self.sim.N, _ptr(self.out),
+                                     _ptr(self.scratch), self.stream), "lbm_sg_residual")
+        d2, a2 = self.out.tolist()[:2]
+        return float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
+
+
+def steps_to_tolerance(torch, sim, tol=1e-6, check_every=100, consecutive=3, max_steps=200000, measure="laplace",
+                       history=None):
+    """Steps until the residual (see _Residual) stays below tol for
+    `consecutive` checks `check_every` steps apart (None if not within
+    max_steps or if the run diverges); returns (steps, device ms of the
+    whole loop including the checks, last residual).  `history`, a list,
+    receives every residual."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    sim.macro(phi, P[0], None)
-    steps, ok, r, cur, done = 0, 0, float("inf"), 0, None
+    res = _Residual(torch, sim, measure)
+    steps, ok, r, done = 0, 0, float("inf"), None
     while steps < max_steps:
         sim.step(check_every)
         steps += check_every
-        nxt = 1 - cur
-        sim.macro(phi, P[nxt], None)
-        _ck(lib.lbm_sg_residual(_ptr(P[nxt]), _ptr(P[cur]), n, _ptr(out), _ptr(scratch), stream), "lbm_sg_residual")
-        d2, a2 = out.tolist()
-        r = float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
-        cur = nxt
+        r = res.update()
+        if history is not None:
+            history.append(r)
         if not np.isfinite(r):   # the run diverged: no convergence
             break
         ok = ok + 1 if r < tol else 0
@@ -237,40 +275,38 @@ def steps_to_tolerance(torch, sim, tol=1e-3, check_every=100, consecutive=3, max
     return done, e0.elapsed_time(e1), r
 
 
-def batch_steps_to_tolerance(torch, batch, tol=1e-3, check_every=100, consecutive=3, max_steps=200000):
+def batch_steps_to_tolerance(torch, batch, tol=1e-6, check_every=100, consecutive=3, max_steps=200000,
+                             measure="laplace"):
     """steps_to_tolerance for every grid of a Batch stepped together: the
     batch advances until each grid has met the criterion (or max_steps);
     returns (per-grid steps or None, device ms of the whole loop)."""
-    lib = L.load()
-    stream = torch.cuda.current_stream().cuda_stream
-    views = [batch.grid(k) for k in range(len(batch))]
-    P = [[torch.zeros(v.N, dtype=torch.float64, device="cuda") for _ in range(2)] for v in views]
-    phi = [torch.zeros(v.N, dtype=torch.float64, device="cuda") for v in views]
-    out = torch.zeros(2, dtype=torch.float64, device="cuda")
-    scratch = torch.zeros(512, dtype=torch.float64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for k, v in enumerate(views):
-        v.macro(phi[k], P[k][0], None)
-    done = [None] * len(views)
-    ok = [0] * len(views)
-    cur, steps = 0, 0
+    res = [_Residual(torch, batch.grid(k), measure) for k in range(len(batch))]
+    done = [None] * len(res)
+    ok = [0] * len(res)
+    steps = 0
     while steps < max_steps and any(d is None for d in done):
         batch.step(check_every)
         steps += check_every
-        nxt = 1 - cur
-        for k, v in enumerate(views):
-            v.macro(phi[k], P[k][nxt], None)
+        for k, rk in enumerate(res):
             if done[k] is not None:
                 continue
-            _ck(lib.lbm_sg_residual(_ptr(P[k][nxt]), _ptr(P[k][cur]), v.N, _ptr(out), _ptr(scratch), stream),
-                "lbm_sg_residual")
-            d2, a2 = out.tolist()
-            r = float(np.sqrt(d2 / a2)) if a2 > 0 else float("inf")
+            r = rk.update()
             ok[k] = ok[k] + 1 if r < tol else 0
             if ok[k] >= consecutive:
                 done[k] = steps
-        cur = nxt
     e1.record()
     e1.synchronize()
     return done, e0.elapsed_time(e1)
+
+
+def steps_at(history, tol, check_every=100, consecutive=3):
+    """From a residual history: the steps at which the residual had first
+    stayed below tol for `consecutive` checks (None if never)."""
+    run = 0
+    for i, r in enumerate(history):
+        run = run + 1 if r < tol else 0
+        if run >= consecutive:
+            return (i + 1) * check_every
+    return None

@@ -140,3 +140,41 @@ def test_training_lowers_the_loss(env):
     for _ in range(60):
         last = sg.train_step(xd, td, lr=2e-3)
     assert float(last.item()) < 0.7 * first
+
+
+def test_phi_projection_and_phase_pressure(env):
+    """lbm_sg_phi_project against its definition written out in numpy (the
+    predicted change of phi kept to the start's interface band, clipped to
+    [0, 1], the total of the start restored by moving the interfaces), and
+    lbm_sg_phase_pressure against numpy means over the bulk phases."""
+    torch, L, S = env
+    lib = L.load()
+    from paper_1812_00118_gb300 import inputs as I
+    rng = np.random.default_rng(11)
+    phi0, _, _ = I.sphere((1, 96, 96), (47.3, 48.6, 0), 20.0, 4.0, drop=True)
+    phi0 = phi0.reshape(-1)
+    pred = phi0 + rng.normal(scale=0.01, size=phi0.size)
+    n = phi0.size
+    d0 = torch.from_numpy(phi0).cuda()
+    dp = torch.from_numpy(pred).cuda()
+    scr = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.lbm_sg_phi_project(ptr(dp), ptr(d0), n, ptr(scr), s) == 0
+    got = dp.cpu().numpy()
+    m = 4 * phi0 * (1 - phi0)
+    ref = np.clip(phi0 + m * (pred - phi0), 0.0, 1.0)
+    wref = 4 * ref * (1 - ref)
+    ref = ref + (phi0.sum() - ref.sum()) / wref.sum() * wref
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+    assert abs(got.sum() - phi0.sum()) < 1e-10 * phi0.sum()
+    bulk = (phi0 == 0.0) | (phi0 == 1.0)
+    assert bulk.any() and np.array_equal(got[bulk], phi0[bulk])
+    # bulk pressures
+    P = rng.normal(size=n)
+    dP = torch.from_numpy(P).cuda()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    assert lib.lbm_sg_phase_pressure(ptr(d0), ptr(dP), n, 0.01, ptr(out), ptr(scr), s) == 0
+    o = out.cpu().numpy()
+    hv, lt = phi0 >= 0.99, phi0 <= 0.01
+    np.testing.assert_allclose(o, [P[hv].mean(), P[lt].mean(), hv.sum(), lt.sum()], rtol=1e-12)
+    assert lib.lbm_sg_status(s) == 0
