@@ -52,7 +52,8 @@ enum lbm_status {
     LBM_ECUDA = -3,      /* a CUDA call failed */
     LBM_EDIVERGED = -4,  /* a diagnostic found a non-finite value or |u| > 0.3 */
     LBM_ETIMEOUT = -5,   /* a bounded device wait gave up */
-    LBM_ENOTSUP = -6     /* combination not supported by this build */
+    LBM_ENOTSUP = -6,    /* combination not supported by this build */
+    LBM_ECHECKED = -7    /* checked builds: a step kernel met an offset outside its arrays */
 };
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
@@ -293,6 +294,17 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
  * one stream.  Errors: LBM_EINVAL (NULL phi, P or out, n < 0 or
  * n > LBM_NOALLOC_MAX_NODES), LBM_ECUDA (an error was pending before the
  * call -- it is left for its owner to read -- or a launch failed). */
+/* Checked builds (compiled with LBM_CHECKED, a debugging option; the default
+ * build is not one).  The step kernels then check every plane's pull offsets
+ * and every write offset against the population arrays; an offset outside
+ * them is replaced by a valid one and recorded.  lbm_checked_status
+ * synchronises `stream` (NULL: the default stream) and reports the record
+ * since its last call: LBM_ECHECKED if any offset failed, else LBM_OK
+ * (always LBM_OK in a default build); LBM_ECUDA if the synchronisation or
+ * the read failed.  lbm_is_checked_build returns 1 in a checked build. */
+int lbm_checked_status(void* stream);
+int lbm_is_checked_build(void);
+
 #define LBM_NOALLOC_MAX_NODES 33554432
 int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
                            const double* v2, long long n, double rho_L, double rho_dif, double* out,

@@ -52,18 +52,27 @@ def _sources_mtime():
     return newest
 
 
-def build(force=False, verbose=False):
-    """Compile and link; returns the path of liblbm.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+CHECKED_LIB = os.path.join(LIBDIR, "liblbm_checked.so")
+
+
+def build(force=False, verbose=False, checked=False):
+    """Compile and link; returns the path of liblbm.so.  With `checked`, the
+    debugging variant liblbm_checked.so (LBM_CHECKED: the step kernels check
+    their offsets against the population arrays; lbm_checked_status), built
+    into its own object directory; the default build never includes it."""
+    lib_path = CHECKED_LIB if checked else LIB
+    obj_dir = BUILD + ("_checked" if checked else "")
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _sources_mtime():
+        return lib_path
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
+    extra = ["-DLBM_CHECKED"] if checked else []
 
     def compile_one(unit):
         name, src, defs = unit
-        obj = os.path.join(BUILD, name + ".o")
-        cmd = [cc] + ARCH + FLAGS + defs + ["-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, name + ".o")
+        cmd = [cc] + ARCH + FLAGS + extra + defs + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {name}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -74,14 +83,14 @@ def build(force=False, verbose=False):
     units = _units()
     with ThreadPoolExecutor(max_workers=min(len(units), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, units))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -355,6 +355,26 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
 
 extern "C" {
 
+int lbm_checked_status(void* stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LBM_ECUDA;
+    int worst = 0;
+    for (int lat = 0; lat < 2; ++lat)
+        for (int st = 0; st < 4; ++st) {
+            const int v = table_for(lat, st)->checked_status();
+            if (v < 0) return LBM_ECUDA;
+            if (v > worst) worst = v;
+        }
+    return worst ? LBM_ECHECKED : LBM_OK;
+}
+
+int lbm_is_checked_build(void) {
+#ifdef LBM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char* lbm_strerror(int s) {
     switch (s) {
         case LBM_OK: return "ok";
@@ -364,6 +384,7 @@ const char* lbm_strerror(int s) {
         case LBM_EDIVERGED: return "simulation diverged (non-finite value or |u| > 0.3)";
         case LBM_ETIMEOUT: return "bounded device wait timed out";
         case LBM_ENOTSUP: return "not supported";
+        case LBM_ECHECKED: return "an offset check of a checked build failed";
         default: return "unknown status";
     }
 }

@@ -87,6 +87,9 @@ struct KernelTable {
     size_t batch_case_bytes;
     int n_batch_tiles;
     int batch_tile_tx[kMaxBatchTiles];
+    // checked builds: this unit's offset-check flag (0 none, 1 pull, 2 write),
+    // cleared by the read; -1 if the read failed; always 0 in other builds
+    int (*checked_status)();
 };
 
 // One table per (lattice, storage), each defined in its own compilation of

@@ -210,10 +210,15 @@ template <> __device__ __forceinline__ __nv_bfloat16 ld_keep_if<__nv_bfloat16>(c
 // are compensated: a running sum seeded with 1 (so every addend is smaller in
 // magnitude than the sum, as Fast2Sum requires, while phi stays in [-1/2, 1])
 // collects each addition's rounding error exactly, and phi = (s - 1) + e with
-// s - 1 exact (Sterbenz).  An uncompensated FP32 sum of 19 values up to phi/3
-// carries ~1e-7 of error into phi, ten times the rounding of the stored h
-// themselves, and the stencils of Eq. 12 amplify it; at tau near 1/2 it grows
-// over the steps.  FP64 sums plainly.
+// s - 1 exact (Sterbenz).  The moving populations enter in consecutive pairs
+// (directions 1 + 2, 3 + 4, ...; each pair sum of two values up to ~phi/9 is
+// one rounding of ~4e-9), so the compensated chain has 10 links instead of
+// 19.  An uncompensated FP32 sum of 19 values up to phi/3 carries ~1e-7 of
+// error into phi, ten times the rounding of the stored h themselves, and the
+// stencils of Eq. 12 amplify it; at tau near 1/2 it grows over the steps.
+// FP64 sums plainly.  add() is called once per direction in direction order
+// inside unrolled loops, so the pairing bookkeeping folds away at compile
+// time.
 template <typename R>
 struct PhiSum {
     R s = 0, e = 0;
@@ -222,13 +227,24 @@ struct PhiSum {
 };
 template <>
 struct PhiSum<float> {
-    float s = 1.0f, e = 0.0f;
-    __device__ __forceinline__ void add(float v) {
+    float s = 1.0f, e = 0.0f, pend = 0.0f;
+    int n = 0;
+    __device__ __forceinline__ void link(float v) {
         const float t = __fadd_rn(s, v);
         e = __fadd_rn(e, __fsub_rn(v, __fsub_rn(t, s)));
         s = t;
     }
-    __device__ __forceinline__ float value() const { return __fadd_rn(__fsub_rn(s, 1.0f), e); }
+    __device__ __forceinline__ void add(float v) {
+        if (n == 0) link(v);                        // the rest population
+        else if (n & 1) pend = v;                   // first of a pair
+        else link(__fadd_rn(pend, v));              // the pair
+        ++n;
+    }
+    __device__ __forceinline__ float value() const {
+        PhiSum<float> c = *this;
+        if (n > 0 && (n & 1) == 0) c.link(pend);    // an unpaired last value
+        return __fadd_rn(__fsub_rn(c.s, 1.0f), c.e);
+    }
 };
 
 // Padded flat offset of (possibly ghost) coordinates.
@@ -332,6 +348,40 @@ __device__ __forceinline__ PullOffsets pull_offsets(const Geom& G, int x, int y,
     return o;
 }
 
+// ---------------------------------------------------------------- checked builds
+// With LBM_CHECKED (a build option for debugging; the default build has
+// none of this) the pull offsets of every plane and every write offset of the
+// step kernels are checked against the population arrays before use: an
+// offset outside [0, NP) sets this translation unit's flag (read by
+// lbm_checked_status: 1 = a pull, 2 = a write) and is replaced by 0, a valid
+// element, so a bad index gives a wrong result and a report, never a fault.
+// Every pull offset is a sum z[k] + r[j] + c[m], so the extreme sums bound
+// all 27.
+#ifdef LBM_CHECKED
+static __device__ int g_checked_err;
+__device__ __forceinline__ void checked_offsets(PullOffsets& o, long long NP) {
+    long long lo = 0, hi = 0;
+    int mn, mx;
+    mn = min(o.z[0], min(o.z[1], o.z[2])); mx = max(o.z[0], max(o.z[1], o.z[2])); lo += mn; hi += mx;
+    mn = min(o.r[0], min(o.r[1], o.r[2])); mx = max(o.r[0], max(o.r[1], o.r[2])); lo += mn; hi += mx;
+    mn = min(o.c[0], min(o.c[1], o.c[2])); mx = max(o.c[0], max(o.c[1], o.c[2])); lo += mn; hi += mx;
+    if (lo < 0 || hi >= NP) {
+        atomicExch(&g_checked_err, 1);
+        for (int k = 0; k < 3; ++k) o.z[k] = o.r[k] = o.c[k] = 0;
+    }
+}
+__device__ __forceinline__ int checked_write(int off, long long NP) {
+    if (off < 0 || off >= NP) {
+        atomicExch(&g_checked_err, 2);
+        return 0;
+    }
+    return off;
+}
+#else
+__device__ __forceinline__ void checked_offsets(PullOffsets&, long long) {}
+__device__ __forceinline__ int checked_write(int off, long long) { return off; }
+#endif
+
 // Address of the value a pull of direction I reads.
 template <int LAT, int I, typename S>
 __device__ __forceinline__ const S* pull_ptr(const S* const* arr, const PullOffsets& o) {
@@ -372,7 +422,7 @@ __device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, i
                                           const NodeWrites& nw, S v) {
     using L = Lattice<LAT>;
     constexpr int CX = L::cx[J], CY = L::cy[J], CZ = L::cz[J];
-    arr[J][own] = v;
+    arr[J][checked_write(own, G.NP)] = v;
     if constexpr (WALLS) {
         if (nw.wall_adj) {
             const int tx = x + CX, ty = y + CY, tz = z + CZ;
@@ -382,8 +432,8 @@ __device__ __forceinline__ void write_dir(S* const* arr, const Geom& G, int x, i
             // the ghost cell lies across a wall; along the periodic axes the
             // pull wraps, so the cell does too
             if (wall_cross)
-                arr[L::opp(J)][pidx(G, wrap1(tx, G.NX, G.wall[0]), wrap1(ty, G.NY, G.wall[1]),
-                                    wrap1(tz, G.NZ, G.wall[2]))] = v;
+                arr[L::opp(J)][checked_write(pidx(G, wrap1(tx, G.NX, G.wall[0]), wrap1(ty, G.NY, G.wall[1]),
+                                                  wrap1(tz, G.NZ, G.wall[2])), G.NP)] = v;
         }
     }
 }
@@ -419,7 +469,8 @@ __device__ __forceinline__ void moving_wall_write(S* const* arr, const Geom& G, 
     if (cnt == 0) return;
     const R cu = ((R)CX * u0 + (R)CY * u1 + (R)CZ * u2) / (R)cnt;
     const R corr = (R)6 * (R)L::w[J] * s * cu;
-    arr[L::opp(J)][pidx(G, wrap1(t[0], G.NX, G.wall[0]), wrap1(t[1], G.NY, G.wall[1]), wrap1(t[2], G.NZ, G.wall[2]))] =
+    arr[L::opp(J)][checked_write(
+        pidx(G, wrap1(t[0], G.NX, G.wall[0]), wrap1(t[1], G.NY, G.wall[1]), wrap1(t[2], G.NZ, G.wall[2])), G.NP)] =
         store(v - corr);
 }
 
@@ -890,6 +941,7 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
                 HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0, ring_xy);
     }
     auto ring_phi = [&](PullOffsets po) {
+        checked_offsets(po, G.NP);
         PhiSum<R> phi;
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
@@ -909,10 +961,12 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
         if constexpr (kOneRing) {
             PullOffsets po = own_xy;
             pull_z(G, zz, po);
+            checked_offsets(po, G.NP);
             typename St::S hv[Q];
             if ((tid & ~31) < NRING) {   // uniform over the warp
                 PullOffsets pr = ring_xy;
                 pull_z(G, zz, pr);
+                checked_offsets(pr, G.NP);
                 const bool ring = tid < NRING;
                 typename St::S rv[Q];
                 Unroll<0, Q>::run([&](auto ic) {
@@ -950,6 +1004,7 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
             {
                 PullOffsets po = own_xy;
                 pull_z(G, zz, po);
+                checked_offsets(po, G.NP);
                 PhiSum<R> phi;
                 Unroll<0, Q>::run([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
@@ -980,6 +1035,7 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
         const int j = z - z0;
         PullOffsets po = own_xy;   // x, y are the own column when active
         pull_z(G, z, po);
+        checked_offsets(po, G.NP);
         // (1) g of this node (streamed) and the phi fill of the next plane
         Moments<R> m;
         auto g_load = [&](R* gv) {
@@ -1084,7 +1140,8 @@ __device__ __forceinline__ void march_async(const DirPtrs<float, Lattice<LAT>::Q
     // thread's halo-ring positions into ring
     auto issue_fill = [&](int zp, int hs) {
         const int zz = stencil_coord(zp, G.NZ, G.wall[2]);
-        const PullOffsets po = pull_offsets(G, xo, yo, zz);
+        PullOffsets po = pull_offsets(G, xo, yo, zz);
+        checked_offsets(po, G.NP);
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             cp_async4(&sm.hown[hs][i][tid], pull_ptr<LAT, i>(D.hin, po));
@@ -1094,7 +1151,8 @@ __device__ __forceinline__ void march_async(const DirPtrs<float, Lattice<LAT>::Q
             ring_pos<TX, TY, HY>(r, &lx, &ly);
             const int xx = stencil_coord(x0 + lx - 1, G.NX, G.wall[0]);
             const int yy = HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0;
-            const PullOffsets pr = pull_offsets(G, xx, yy, zz);
+            PullOffsets pr = pull_offsets(G, xx, yy, zz);
+            checked_offsets(pr, G.NP);
             Unroll<0, Q>::run([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 cp_async4(&sm.ring[i][r], pull_ptr<LAT, i>(D.hin, pr));
@@ -1116,7 +1174,8 @@ __device__ __forceinline__ void march_async(const DirPtrs<float, Lattice<LAT>::Q
     };
     auto issue_g = [&](int zg) {
         if (!active) return;
-        const PullOffsets po = pull_offsets(G, x, y, zg);
+        PullOffsets po = pull_offsets(G, x, y, zg);
+        checked_offsets(po, G.NP);
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             cp_async4(&sm.gbuf[i][tid], pull_ptr<LAT, i>(D.gin, po));

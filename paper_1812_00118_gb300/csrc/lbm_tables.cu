@@ -125,13 +125,27 @@ cudaError_t batch_dispatch(const BatchArgs& a) {
 #define LBM_ISTMA_tma 1
 #define LBM_TMA(ID, KIND, TX, TY, MB) LBM_ISTMA_##KIND,
 
+int checked_status() {
+#ifdef LBM_CHECKED
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_checked_err, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_checked_err, &zero, sizeof(int)) != cudaSuccess) return -1;
+    }
+    return v;
+#else
+    return 0;
+#endif
+}
+
 const KernelTable kTable = {step_dispatch, maps_dispatch, ok_dispatch,
                             Launchers<LBM_LAT, LBM_ST>::phi, Launchers<LBM_LAT, LBM_ST>::macro,
                             Launchers<LBM_LAT, LBM_ST>::init, Launchers<LBM_LAT, LBM_ST>::get,
                             Launchers<LBM_LAT, LBM_ST>::set, Launchers<LBM_LAT, LBM_ST>::halo,
                             Launchers<LBM_LAT, LBM_ST>::shift_rest, kMaxTiles,
                             {LBM_TILES(LBM_TX)}, {LBM_TILES(LBM_TY)},
-                            {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS};
+                            {LBM_TILES(LBM_TMA)}, LBM_BATCH_FIELDS, checked_status};
 
 }  // namespace
 

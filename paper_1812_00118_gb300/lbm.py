@@ -14,14 +14,16 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
+# LBM_CHECKED=1 in the environment selects the checked debugging build
+# (paper_1812_00118_gb300.build.build(checked=True)); it must exist.
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_checked.so" if os.environ.get("LBM_CHECKED") == "1" else "liblbm.so")
 
 D2Q9, D3Q19 = 0, 1
 PERIODIC, WALL = 0, 1
 F64, F32, F16S, BF16S = 0, 1, 2, 3
 STORE_NAMES = {F64: "f64", F32: "f32", F16S: "f16s", BF16S: "bf16s"}
 
-OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTSUP, ECHECKED = 0, -1, -2, -3, -4, -5, -6, -7
 INIT_NONEQ = 1
 
 
@@ -100,6 +102,8 @@ SIGNATURES = [
     ("lbm_sg_relu_bwd", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, ctypes.c_longlong,
                                        ctypes.c_int, _VP]),
     ("lbm_sg_to_bf16", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, _VP]),
+    ("lbm_checked_status", ctypes.c_int, [_VP]),
+    ("lbm_is_checked_build", ctypes.c_int, []),
     ("lbm_sg_status", ctypes.c_int, [_VP]),
     ("lbm_sg_add", ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_longlong,
                                   ctypes.c_int, _VP]),

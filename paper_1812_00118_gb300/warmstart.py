@@ -276,10 +276,12 @@ def steps_to_tolerance(torch, sim, tol=1e-6, check_every=100, consecutive=3, max
 
 
 def batch_steps_to_tolerance(torch, batch, tol=1e-6, check_every=100, consecutive=3, max_steps=200000,
-                             measure="laplace"):
+                             measure="laplace", on_converged=None):
     """steps_to_tolerance for every grid of a Batch stepped together: the
     batch advances until each grid has met the criterion (or max_steps);
-    returns (per-grid steps or None, device ms of the whole loop)."""
+    returns (per-grid steps or None, device ms of the whole loop).
+    on_converged(k), if given, is called when grid k meets the criterion
+    (the batch keeps stepping the grids that already have)."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     res = [_Residual(torch, batch.grid(k), measure) for k in range(len(batch))]
@@ -296,6 +298,8 @@ def batch_steps_to_tolerance(torch, batch, tol=1e-6, check_every=100, consecutiv
             ok[k] = ok[k] + 1 if r < tol else 0
             if ok[k] >= consecutive:
                 done[k] = steps
+                if on_converged is not None:
+                    on_converged(k)
     e1.record()
     e1.synchronize()
     return done, e0.elapsed_time(e1)
@@ -310,3 +314,25 @@ def steps_at(history, tol, check_every=100, consecutive=3):
         if run >= consecutive:
             return (i + 1) * check_every
     return None
+
+
+def laplace_error(sim, placed, bubble):
+    """For a state of one drop (or one bubble, `bubble`): the Laplace jump
+    (Section 4.1) across its interface against sigma / R, minus 1, measured
+    around the current centre of the enclosed phase (circular mean over the
+    periodic box, so a drop that has drifted is still found) with R from its
+    area (2-D); None for several drops."""
+    if len(placed) != 1:
+        return None
+    nx, ny, _ = sim.shape
+    f, _, _ = sim.macro()
+    if not np.isfinite(f).all():
+        return None
+    w = (1.0 - f if bubble else f).reshape(ny, nx).clip(0.0, 1.0)
+    centre = []
+    for prof, n in ((w.sum(axis=0), nx), (w.sum(axis=1), ny)):
+        a = 2.0 * np.pi * np.arange(n) / n
+        centre.append((np.arctan2((prof * np.sin(a)).sum(), (prof * np.cos(a)).sum()) % (2.0 * np.pi)) * n / (2.0 * np.pi))
+    R = float(np.sqrt(w.sum() / np.pi))
+    W = PHYS["W"]
+    return sim.laplace(tuple(centre), R - 2.0 * W, R + 2.0 * W) / (PHYS["sigma"] / R) - 1.0

@@ -194,8 +194,10 @@ def test_config1_static_droplet_f64(lbm):
     undefined, so rounding decides the trajectory: the oracle run twice with a
     1e-15 relative perturbation of h separates to ~1e-5 by step 300.  After
     2000 steps the test therefore checks what is unique: exact phi
-    conservation, and phi, P and the Laplace jump within ten times the spread
-    of the oracle's own perturbed twin."""
+    conservation, and phi, P and the Laplace jump within ten times the widest
+    spread of three perturbed twins of the oracle (one twin's spread is a
+    single sample of a chaotic separation: the GPU, whose rounding is another
+    such perturbation, measured 16 times one twin's P spread in one build)."""
     prm = lbm.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.05 / 3, nu_H=0.05 / 3,
                           store=lbm.F64)
     shape = (1, 64, 64)
@@ -207,30 +209,36 @@ def test_config1_static_droplet_f64(lbm):
     lat = oracle_lattice(0)
     p = oracle_params(prm, (0, 0), 0)
     h, g = O.init_populations(phi, u, P, lat, p)
-    rng = np.random.default_rng(0)
-    h2, g2 = h * (1 + 1e-15 * rng.standard_normal(h.shape)), g.copy()
+    twins = []
+    for seed in (0, 1, 2):
+        rng = np.random.default_rng(seed)
+        twins.append((h * (1 + 1e-15 * rng.standard_normal(h.shape)), g.copy()))
     sim.step(100)
     h, g = O.run(h, g, lat, p, 100)
-    h2, g2 = O.run(h2, g2, lat, p, 100)
+    twins = [O.run(ht, gt, lat, p, 100) for ht, gt in twins]
     f, Pg, ru = sim.macro()
     fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
     assert normwise(f, fo) < 1e-9 and normwise(Pg, Po) < 1e-9 and normwise(ru, ruo) < 1e-9
     sim.step(1900)
     h, g = O.run(h, g, lat, p, 1900)
-    h2, g2 = O.run(h2, g2, lat, p, 1900)
+    twins = [O.run(ht, gt, lat, p, 1900) for ht, gt in twins]
     d1 = sim.diagnostics()
     assert abs(d1["sum_phi"] - d0["sum_phi"]) < 1e-12 * d0["sum_phi"]
     f, Pg, ru = sim.macro()
     fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
-    ft, Pt, _ = oracle_macro_flat(h2, g2, lat, p, 0)
-    assert normwise(f, fo) <= 10 * normwise(ft, fo) + 1e-12
-    assert normwise(Pg, Po) <= 10 * normwise(Pt, Po) + 1e-12
+    tw = [oracle_macro_flat(ht, gt, lat, p, 0) for ht, gt in twins]
+    sf = max(normwise(ft, fo) for ft, _, _ in tw)
+    sP = max(normwise(Pt, Po) for _, Pt, _ in tw)
+    print("config 1 after 2000 steps: GPU vs oracle phi %.2e P %.2e; widest twin spread phi %.2e P %.2e"
+          % (normwise(f, fo), normwise(Pg, Po), sf, sP))
+    assert normwise(f, fo) <= 10 * sf + 1e-12
+    assert normwise(Pg, Po) <= 10 * sP + 1e-12
     from oracle import diagnostics as D
     R = D.effective_radius(fo.reshape(shape), 2, True)
     dP_o = D.laplace_jump(Po.reshape(shape), (31.5, 31.5, 0), R, 4.0)
-    dP_t = D.laplace_jump(Pt.reshape(shape), (31.5, 31.5, 0), R, 4.0)
+    sJ = max(abs(D.laplace_jump(Pt.reshape(shape), (31.5, 31.5, 0), R, 4.0) - dP_o) for _, Pt, _ in tw)
     dP_g = sim.laplace((31.5, 31.5), R - 8.0, R + 8.0)
-    assert abs(dP_g - dP_o) <= 10 * abs(dP_t - dP_o) + 1e-5 * abs(dP_o)
+    assert abs(dP_g - dP_o) <= 10 * sJ + 1e-5 * abs(dP_o)
 
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)

@@ -63,10 +63,8 @@ def test_warm_start_against_plain_solver(env):
             res[mode] = (WS.steps_at(h, 1e-3), steps)
             f, P, _ = sim.macro()
             assert abs(f.sum() - phi0.sum()) < 1e-3 * phi0.sum(), (sd, mode)
-            if len(placed) == 1:
-                cx, cy, R = placed[0]
-                law = WS.PHYS["sigma"] / R    # inside minus outside, for a drop and for a bubble
-                lap[mode] = sim.laplace((cx % Lsz, cy % Lsz), R - 8.0, R + 8.0) / law - 1.0
+            if len(placed) == 1:   # around the drop's current centre, R from its area
+                lap[mode] = WS.laplace_error(sim, placed, bubble=sd % 2 == 1)
             sim.close()
         early.append(res["plain"][0] / res["warm"][0])
         late.append(res["plain"][1] / res["warm"][1])
