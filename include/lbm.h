@@ -118,6 +118,17 @@ typedef struct {
 int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params,
                void* cuda_stream, lbm_ctx** out);
 
+/* lbm_create with options.  flags = 0: the same call; the population arrays
+ * then carry ghost cells along walled axes only (for the bounce-back writes;
+ * a periodic axis wraps its pulls and needs none).  LBM_CREATE_GHOST_BAND:
+ * a band of ghost cells along the periodic axes too, which the bulk-copy
+ * step tile (tile 4 of lbm_set_tile) needs for the periodic images it reads;
+ * the other tiles run on either layout and compute the same values.
+ * Errors: as lbm_create, LBM_EINVAL for an unknown flag. */
+#define LBM_CREATE_GHOST_BAND 1
+int lbm_create_ex(const lbm_grid* grid, int lattice, const lbm_params* params,
+                  void* cuda_stream, int flags, lbm_ctx** out);
+
 /* Initialise the populations from macroscopic fields (Section 4 set-ups
  * start from (phi, u, P)): h = h^eq (Eq. 2) and g = g^eq (Eq. 6 with Eq. 7
  * and Eq. 13) evaluated with the central-difference stencils of the given
@@ -144,8 +155,8 @@ int lbm_init_fields_ex(lbm_ctx* ctx, const double* phi, const double* u, const d
 /* Advance n >= 0 time steps: each step is one launch of the fused
  * collide-and-pull-stream kernel (Eqs. 1-14) and a buffer swap; the
  * bulk-copy tile (see lbm_set_tile) adds one launch of a small kernel that
- * writes the periodic images into the ghost layer of the buffer just written,
- * and so does a node-pair tile once after a state another tile wrote.
+ * writes the periodic images into the ghost band of the buffer just written
+ * (and one more before its first step on a state another tile wrote).
  * Asynchronous on the context stream; returns LBM_ECUDA if a launch fails,
  * and LBM_EDIVERGED without launching anything if the last lbm_diagnostics
  * found the state diverged (until lbm_init_fields or lbm_set_populations
@@ -221,27 +232,28 @@ int lbm_set_phi_correction(lbm_ctx* ctx, int every);
 int lbm_set_wall_velocity(lbm_ctx* ctx, int axis, int side, const double u[3]);
 
 /* Step kernel configuration.  `tile` indexes the compiled step kernels of
- * the lattice:
- *   0-3   per-thread loads, grid = tile columns x chunks of `lz` planes.
- *         D3Q19 CTAs (x-y): 32x4 (g loads held across the phi fill), 32x4,
- *         32x8, 32x4 (the last three in phases, for 8, 4 and 6 CTAs per SM);
- *         D2Q9 CTAs (along x): 128 (held), 128, 256, 64.
- *   4-7   bulk tensor copies into a shared-memory pipeline, persistent CTAs
- *         taking work items of `lz` planes (D3Q19: 32x4, 32x8, 64x4, 32x2;
- *         D2Q9: 128, 64, 192, 32).
- *   8-11  tiles 0-3 launched as one wave: every column split into the same
- *         number of chunks, as many as the resident CTAs allow, each at
+ * the lattice (CTA shapes in nodes: D3Q19 x-y, D2Q9 rows along x):
+ *   0     per-thread loads, the g loads of a plane held in registers across
+ *         the phi fill; 32x4 / 128, 4 CTAs per SM.
+ *   1-3   per-thread loads in phases (phi fill, g moments, collision):
+ *         32x4 / 128 at 8 CTAs per SM, 32x8 / 256 at 4, 32x4 / 64 at 6 / 16.
+ *   4     bulk tensor copies into a shared-memory pipeline (persistent CTAs
+ *         taking work items of `lz` planes; 32x4 / 128).  Needs a context
+ *         created with LBM_CREATE_GHOST_BAND.
+ *   5, 6  tiles 0 and 1 launched as one wave: every column split into the
+ *         same number of chunks, as many as the resident CTAs allow, each at
  *         least `lz` planes long.
- *   12-13 loads issued one plane ahead as asynchronous copies into shared
- *         memory (FP32 storage only; D3Q19: 32x4, 32x2; D2Q9: 128, 256).
- *   14-15 tile 1 at 7 CTAs per SM (72 registers), and the same as a one-wave
+ *   7     loads issued one plane ahead as asynchronous copies into shared
+ *         memory (FP32 storage only; 32x4 / 128).
+ *   8, 9  tile 1 at 7 CTAs per SM (72 registers), and the same as a one-wave
  *         launch.
- * `lz` >= 1 is the number of planes along the march axis (z in 3-D, y in
- * 2-D) as above.  Every tile computes the same arithmetic.  lbm_create picks
- * tile 14 (D3Q19) or tile 1 (D2Q9) with lz = 16; lbm_get_tile reports the
- * current choice and its CTA shape.
+ * Tiles other than 4 and the one-wave forms take chunks of `lz` >= 1 planes
+ * along the march axis (z in 3-D, y in 2-D).  Every tile computes the same
+ * arithmetic.  lbm_create picks tile 8 (D3Q19) or tile 1 (D2Q9) with
+ * lz = 16; lbm_get_tile reports the current choice and its CTA shape.
  * Errors: LBM_EINVAL for an unknown tile or lz < 1, LBM_ENOTSUP for a
- * bulk-copy or asynchronous-copy tile this grid or storage type cannot use. */
+ * bulk-copy or asynchronous-copy tile this grid, layout or storage type
+ * cannot use. */
 int lbm_set_tile(lbm_ctx* ctx, int tile, int lz);
 int lbm_get_tile(const lbm_ctx* ctx, int* tile, int* lz, int* tx, int* ty);
 
@@ -294,6 +306,12 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
  * one stream.  Errors: LBM_EINVAL (NULL phi, P or out, n < 0 or
  * n > LBM_NOALLOC_MAX_NODES), LBM_ECUDA (an error was pending before the
  * call -- it is left for its owner to read -- or a launch failed). */
+
+#define LBM_NOALLOC_MAX_NODES 33554432
+int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
+                           const double* v2, long long n, double rho_L, double rho_dif, double* out,
+                           void* cuda_stream);
+
 /* Checked builds (compiled with LBM_CHECKED, a debugging option; the default
  * build is not one).  The step kernels then check every plane's pull offsets
  * and every write offset against the population arrays; an offset outside
@@ -304,11 +322,6 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* 
  * the read failed.  lbm_is_checked_build returns 1 in a checked build. */
 int lbm_checked_status(void* stream);
 int lbm_is_checked_build(void);
-
-#define LBM_NOALLOC_MAX_NODES 33554432
-int lbm_field_sums_noalloc(const double* phi, const double* P, const double* v0, const double* v1,
-                           const double* v2, long long n, double rho_L, double rho_dif, double* out,
-                           void* cuda_stream);
 
 /* ------------------------------------------------------------------ batches
  * Many independent D2Q9 grids stepped together (the paper runs its 2-D cases

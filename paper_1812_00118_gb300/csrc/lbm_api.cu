@@ -298,7 +298,9 @@ namespace lbm {
 
 // Everything of lbm_create but the device buffers: checks, model constants,
 // internal geometry (ghost-padded, base 0) and kernel table.
-int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream) {
+int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream,
+              int flags) {
+    if (flags & ~LBM_CREATE_GHOST_BAND) return LBM_EINVAL;
     if (!grid || !params) return LBM_EINVAL;
     if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return LBM_EINVAL;
@@ -327,16 +329,19 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
         c->K = table_for(1, params->store);
         c->lz = 16;
     }
-    // ghost padding (see lbm_kernels.cuh): x ghosts of 32 bytes (at least 2
-    // cells), rows padded to 32 bytes; y ghosts 2 cells (D3Q19); one ghost
-    // plane at each z end
+    // ghost padding (see lbm_kernels.cuh), on walled axes only unless the
+    // ghost band is asked for: x ghosts of 32 bytes (at least 2 cells); y
+    // ghosts 2 cells (D3Q19); one ghost plane at each z end.  Rows are padded
+    // to 32 bytes either way.  A periodic axis needs no ghost cell (the pulls
+    // wrap), and leaving them out keeps the 256-byte L2 fetches of the step
+    // kernel from bringing in padding: at 128^3 the rows are then exactly
+    // two 256-byte blocks.
     {
-        // x ghosts: 32 bytes of storage (at least 2 cells), so every row of
-        // nodes starts on a 32-byte sector and warps write whole sectors
+        const bool band = (flags & LBM_CREATE_GHOST_BAND) != 0;
         const int A32 = (int)(32 / c->elem);            // elements per 32 bytes
-        c->G.GX = A32 > 2 ? A32 : 2;
-        c->G.GY = lattice == LBM_D2Q9 ? 0 : 2;
-        c->G.GZ = 1;
+        c->G.GX = (band || c->G.wall[0]) ? (A32 > 2 ? A32 : 2) : 0;
+        c->G.GY = lattice == LBM_D2Q9 ? 0 : ((band || c->G.wall[1]) ? 2 : 0);
+        c->G.GZ = (band || c->G.wall[2]) ? 1 : 0;
         c->G.PX = ((c->G.NX + A32 - 1) / A32) * A32 + 2 * c->G.GX;
         c->G.PY = c->G.NY + 2 * c->G.GY;
         c->G.PZ = c->G.NZ + 2 * c->G.GZ;
@@ -412,11 +417,16 @@ int lbm_lattice_info(int lattice, int* Q, int* c, double* w) {
 }
 
 int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream, lbm_ctx** out) {
+    return lbm_create_ex(grid, lattice, params, cuda_stream, 0, out);
+}
+
+int lbm_create_ex(const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream, int flags,
+                  lbm_ctx** out) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ENOMEM;
-    int rc = ctx_setup(c, grid, lattice, params, cuda_stream);
+    int rc = ctx_setup(c, grid, lattice, params, cuda_stream, flags);
     if (rc) { delete c; return rc; }
     const int Q = lattice == LBM_D2Q9 ? 9 : 19;
     const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;

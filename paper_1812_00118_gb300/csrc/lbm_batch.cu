@@ -226,7 +226,7 @@ int lbm_batch_create(int n, const lbm_grid* grids, const lbm_params* params, voi
         lbm_ctx* v = new (std::nothrow) lbm_ctx();
         if (!v) { free_batch(b); return LBM_ENOMEM; }
         b->views.push_back(v);
-        int rc = params[c].store == b->store ? ctx_setup(v, &grids[c], LBM_D2Q9, &params[c], cuda_stream)
+        int rc = params[c].store == b->store ? ctx_setup(v, &grids[c], LBM_D2Q9, &params[c], cuda_stream, 0)
                                              : LBM_EINVAL;
         if (rc) { free_batch(b); return rc; }
         v->owner = b;

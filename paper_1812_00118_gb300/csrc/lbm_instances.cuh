@@ -193,9 +193,12 @@ template <int LAT, int ST, int TX, int TY>
 bool tma_tile_ok(const Geom& G) {
     using C = TmaCfg<LAT, ST, TX, TY>;
     // shared memory of one CTA, box limits, and the periodic images the
-    // halo of a tile reads (two cells deep) must exist
+    // halo of a tile reads (two cells deep) must exist: a ghost band on
+    // every periodic axis (lbm_create_ex with LBM_CREATE_GHOST_BAND)
     if (C::smem_bytes > 227 * 1024 || C::BX > 256 || C::RH > 256) return false;
     if (G.NX < 2 * kRep || (Lattice<LAT>::kHasY && G.NY < 2 * kRep)) return false;
+    if (!G.wall[0] && G.GX < kRep) return false;
+    if (Lattice<LAT>::kHasY && !G.wall[1] && G.GY < kRep) return false;
     return tensor_map_encoder() != nullptr;
 }
 

@@ -147,5 +147,6 @@ struct lbm_ctx {
 namespace lbm {
 const KernelTable* table_for(int lattice, int store);
 // lbm_create without the buffers (checks, constants, geometry, tables)
-int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream);
+int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* params, void* cuda_stream,
+              int flags);
 }  // namespace lbm

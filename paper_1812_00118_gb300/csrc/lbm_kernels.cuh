@@ -12,12 +12,14 @@
 // reads the ghost layer across a wall (halfway bounce-back): the node next to
 // the wall writes its outgoing f*_j into array opp(j) at x + c_j, the ghost
 // cell its own pull of opp(j) reads, so the pull returns f*_j(x) reflected.
-// The bulk-copy kernels (lbm_tma.cuh) read whole boxes, unwrapped: for them
-// halo_kernel also fills the ghost band (kRep = 2 cells) with the periodic
-// images of the cells the step wrote.
-// GX >= 2 is also 32 bytes of storage (rows padded to 32 bytes) so that every
-// row of nodes starts on a 32-byte sector: a warp's 32 consecutive stores
-// then fill whole sectors, and bulk tensor copies start 16-byte aligned.
+// Ghost widths are 0 along periodic axes (the pulls wrap) unless the context
+// was created with a ghost band: the bulk-copy kernels (lbm_tma.cuh) read
+// whole boxes, unwrapped, and for them halo_kernel fills the band (kRep = 2
+// cells) with the periodic images of the cells the step wrote.
+// Rows are padded to 32 bytes, and a nonzero GX (>= 2) is 32 bytes of
+// storage, so that every row of nodes starts on a 32-byte sector: a warp's 32
+// consecutive stores then fill whole sectors, and bulk tensor copies start
+// 16-byte aligned.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -105,16 +107,23 @@ inline PhysT<R> phys_as(const Phys& p) {
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
 
 template <int ST> struct Storage;
+// load / store convert between the stored value and the population itself;
+// raw / pack only convert the number format, for step code that works on
+// the shifted (and scaled) values directly.
 template <> struct Storage<ST_F64> {
     using S = double; using R = double;
     static __device__ __forceinline__ R load(S v, R, R) { return v; }
     static __device__ __forceinline__ S store(R v, R, R) { return v; }
+    static __device__ __forceinline__ R raw(S v) { return v; }
+    static __device__ __forceinline__ S pack(R v) { return v; }
     static constexpr bool kShifted = false;
 };
 template <> struct Storage<ST_F32> {
     using S = float; using R = float;
     static __device__ __forceinline__ R load(S v, R, R) { return v; }
     static __device__ __forceinline__ S store(R v, R, R) { return v; }
+    static __device__ __forceinline__ R raw(S v) { return v; }
+    static __device__ __forceinline__ S pack(R v) { return v; }
     static constexpr bool kShifted = false;
 };
 template <> struct Storage<ST_F16S> {
@@ -126,6 +135,8 @@ template <> struct Storage<ST_F16S> {
     static __device__ __forceinline__ S store(R v, R shift, R scale) {
         return __float2half_rn((v - shift) * scale);
     }
+    static __device__ __forceinline__ R raw(S v) { return __half2float(v); }
+    static __device__ __forceinline__ S pack(R v) { return __float2half_rn(v); }
     static constexpr bool kShifted = true;
 };
 template <> struct Storage<ST_BF16S> {
@@ -136,6 +147,8 @@ template <> struct Storage<ST_BF16S> {
     static __device__ __forceinline__ S store(R v, R shift, R scale) {
         return __float2bfloat16_rn((v - shift) * scale);
     }
+    static __device__ __forceinline__ R raw(S v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ S pack(R v) { return __float2bfloat16_rn(v); }
     static constexpr bool kShifted = true;
 };
 
@@ -278,8 +291,9 @@ __device__ __forceinline__ int stencil_coord(int v, int n, int wall) {
 template <typename S>
 __device__ __forceinline__ void store_rep(S* __restrict__ arr, const Geom& G, int x, int y, int z, S v) {
     arr[pidx(G, x, y, z)] = v;
-    const int rx = G.wall[0] ? 0 : 1;
-    const int ry = (G.wall[1] || G.GY == 0) ? 0 : 1;
+    // images exist only where the layout has a ghost band on a periodic axis
+    const int rx = (G.wall[0] || G.GX < kRep) ? 0 : 1;
+    const int ry = (G.wall[1] || G.GY < kRep) ? 0 : 1;
     const int Ry = G.GY < kRep ? G.GY : kRep;
     for (int kx = -rx; kx <= rx; ++kx) {
         for (int ky = -ry; ky <= ry; ++ky) {
@@ -474,9 +488,30 @@ __device__ __forceinline__ void moving_wall_write(S* const* arr, const Geom& G, 
         store(v - corr);
 }
 
-// Reciprocal: correctly rounded, through the hardware reciprocal for FP32.
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// Reciprocal on the step path: FP32 takes the approximate hardware
+// reciprocal (within 2 ulp) and one Newton-Raphson step r + r (1 - x r),
+// which leaves an error of about one rounding without the special-case
+// handling of the correctly rounded reciprocal (x is a density here: finite,
+// positive, normal); FP64 divides.
+__device__ __forceinline__ float recip_fast(float x) {
+    const float r = __fdividef(1.0f, x);
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double recip_fast(double x) { return 1.0 / x; }
+// |g| and 1 / (|g| + eps) from g2 = |g|^2 (the interface normal of Eq. 2).
+// FP64 as written.  FP32: one approximate reciprocal square root
+// r = 1 / sqrt(g2 + eps^2), |g| = g2 r, and r for 1 / (|g| + eps) (relative
+// difference below eps / |g|; both give a normal of 0 where grad phi
+// vanishes).
+__device__ __forceinline__ void norm_inv(double g2, double eps, double* mag, double* inv) {
+    *mag = sqrt(g2);
+    *inv = 1.0 / (*mag + eps);
+}
+__device__ __forceinline__ void norm_inv(float g2, float eps, float* mag, float* inv) {
+    const float r = rsqrtf(fmaf(eps, eps, g2));
+    *mag = g2 * r;
+    *inv = r;
+}
 
 // compile-time loop helper
 template <int I, int N>
@@ -537,7 +572,11 @@ struct NodeState {
 //   sum c c K = s [T(u grad + grad u) - u u (u.grad)] + rho_dif T I (u.grad)
 //             + [T(u F + F u) - u u (u.F)] / T,   s = rho_dif + mu / T,
 // which holds exactly on D2Q9 and D3Q19 (fourth-order isotropy); the
-// oracle sums sum c c (g - g^eq) term by term instead.
+// oracle sums sum c c (g - g^eq) term by term instead.  Collected for the
+// kernel: with V = s grad + F / T and c = s (u.grad) + (u.F) / T,
+//   sum c c K = T (u V + V u) - c u u + rho_dif T (u.grad) I,
+// and since P - rho_dif T (u.grad) / 2 = T m0,
+//   Pi = m2 - T m0 I + u Y + W u,   W = T V / 2,  Y = W - (rho + c / 2) u.
 template <typename R, bool THREE_D>
 __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R m0, R mx, R my, R mz,
                                            R mxx, R myy, R mzz, R mxy, R mxz, R myz) {
@@ -550,7 +589,7 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     s.Fy = fr * (R)p.g[1];
     s.Fz = fr * (R)p.g[2];
     const R rho_e = p.hocorr ? s.rho + (R)0.25 * rho_dif * s.lap : s.rho;
-    const R inv_rho_e = recip(rho_e);
+    const R inv_rho_e = recip_fast(rho_e);
     s.ux = (mx + (R)0.5 * (s.mu * s.gx + s.Fx)) * inv_rho_e;
     s.uy = THREE_D ? (my + (R)0.5 * (s.mu * s.gy + s.Fy)) * inv_rho_e : (R)0;
     s.uz = (mz + (R)0.5 * (s.mu * s.gz + s.Fz)) * inv_rho_e;
@@ -558,29 +597,30 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     s.ug = s.ux * s.gx + s.uy * s.gy + s.uz * s.gz;
     s.uF = s.ux * s.Fx + s.uy * s.Fy + s.uz * s.Fz;
     s.P = T * m0 + (R)0.5 * T * rho_dif * s.ug;
-    // second moment of g^eq (closed form above), then Pi
-    const R sK = rho_dif + (R)3 * s.mu;
-    const R iso = rho_dif * T * s.ug;
-    auto ccK = [&](R ua, R ub, R ga, R gb, R Fa, R Fb, bool diag) {
-        R v = sK * (T * (ua * gb + ub * ga) - ua * ub * s.ug) + (T * (ua * Fb + Fa * ub) - ua * ub * s.uF) * (R)3;
-        return diag ? v + iso : v;
-    };
-    const R Pd = s.P;
-    s.pxx = mxx - (s.rho * s.ux * s.ux + Pd - (R)0.5 * ccK(s.ux, s.ux, s.gx, s.gx, s.Fx, s.Fx, true));
-    s.pzz = mzz - (s.rho * s.uz * s.uz + Pd - (R)0.5 * ccK(s.uz, s.uz, s.gz, s.gz, s.Fz, s.Fz, true));
-    s.pxz = mxz - (s.rho * s.ux * s.uz - (R)0.5 * ccK(s.ux, s.uz, s.gx, s.gz, s.Fx, s.Fz, false));
+    // second moment of g^eq (closed form above, collected), then Pi
+    const R sK = rho_dif + (R)3 * s.mu;          // s / T
+    const R sK6 = sK * (R)(1.0 / 6.0);           // T s / 2
+    const R rhop = s.rho + (R)0.5 * sK * s.ug + (R)1.5 * s.uF;   // rho + c / 2
+    const R Tm0 = T * m0;
+    const R Wx = sK6 * s.gx + (R)0.5 * s.Fx, Wz = sK6 * s.gz + (R)0.5 * s.Fz;
+    const R Yx = Wx - rhop * s.ux, Yz = Wz - rhop * s.uz;
+    s.pxx = (mxx - Tm0) + s.ux * (Wx + Yx);
+    s.pzz = (mzz - Tm0) + s.uz * (Wz + Yz);
+    s.pxz = mxz + s.ux * Yz + s.uz * Wx;
     if (THREE_D) {
-        s.pyy = myy - (s.rho * s.uy * s.uy + Pd - (R)0.5 * ccK(s.uy, s.uy, s.gy, s.gy, s.Fy, s.Fy, true));
-        s.pxy = mxy - (s.rho * s.ux * s.uy - (R)0.5 * ccK(s.ux, s.uy, s.gx, s.gy, s.Fx, s.Fy, false));
-        s.pyz = myz - (s.rho * s.uy * s.uz - (R)0.5 * ccK(s.uy, s.uz, s.gy, s.gz, s.Fy, s.Fz, false));
+        const R Wy = sK6 * s.gy + (R)0.5 * s.Fy;
+        const R Yy = Wy - rhop * s.uy;
+        s.pyy = (myy - Tm0) + s.uy * (Wy + Yy);
+        s.pxy = mxy + s.ux * Yy + s.uy * Wx;
+        s.pyz = myz + s.uy * Yz + s.uz * Wy;
     } else {
         s.pyy = s.pxy = s.pyz = (R)0;
     }
     s.tr3 = (s.pxx + s.pyy + s.pzz) * T;
     const R pc = s.phi < (R)0 ? (R)0 : (s.phi > (R)1 ? (R)1 : s.phi);
     s.omega = (R)p.om_L + pc * (R)p.om_dif;
-    const R gmag = sqrt(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz);
-    const R inv = recip(gmag + (R)p.eps);
+    R gmag, inv;
+    norm_inv(s.gx * s.gx + s.gy * s.gy + s.gz * s.gz, (R)p.eps, &gmag, &inv);
     s.nx = s.gx * inv;
     s.ny = s.gy * inv;
     s.nz = s.gz * inv;
@@ -637,45 +677,54 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // Node quantities the pair collision reads, broadcast to both lanes once per
-// node.  w3P, thw, hoc depend on w_i: index 0 for the axis weight, 1 for the
-// diagonal weight (D3Q19: 1/18, 1/36; D2Q9: 1/9, 1/36).
+// node.  w3P, thw, hoc, nwhs depend on w_i: index 0 for the axis weight, 1 for
+// the diagonal weight (D3Q19: 1/18, 1/36; D2Q9: 1/9, 1/36).
+// SH (16-bit shifted storage): the collision computes the stored values
+// themselves, h*_i - w_i h_shift and (g*_i - w_i g_shift) g_scale, so that
+// no population is shifted or scaled on its way to memory: every term of g*
+// carries g_scale (kF = 1.5 g_scale, and w3P holds w_i (3 P - g_shift)
+// g_scale), and h^eq carries the shift -w_i h_shift (nwhs).
 struct PairState {
-    float2 rho, mu3, rho_dif, neg_ug, neg_uF, neg_usq15, phi, inv_tau;
-    float2 w3P[2], thw[2], hoc[2];
-    float om45, tr3;   // (1 - 1/tau_mix) * 4.5 and tr(Pi)/3
+    float2 rho, mu15, hrho_dif, neg_ug, neg_uF15, neg_usq15, phi, inv_tau;
+    float2 w3P[2], thw[2], hoc[2], nwhs[2];
+    float om45, tr3;   // (1 - 1/tau_mix) * 4.5 (times g_scale with SH) and tr(Pi)/3
+    float kF;          // 1.5 g_scale (SH only)
 };
 
-template <int LAT>
+template <int LAT, bool SH>
 __device__ __forceinline__ PairState pair_state(const NodeState<float>& s, const PhysT<float>& p) {
     using L = Lattice<LAT>;
     constexpr int IA = 1, ID = 4;   // an axis and a diagonal direction
     static_assert(L::cx[IA] * L::cx[IA] + L::cy[IA] * L::cy[IA] + L::cz[IA] * L::cz[IA] == 1, "axis");
     static_assert(L::cx[ID] * L::cx[ID] + L::cy[ID] * L::cy[ID] + L::cz[ID] * L::cz[ID] == 2, "diagonal");
     PairState q;
-    q.rho = dup2(s.rho);
-    q.mu3 = dup2(3.0f * s.mu);
-    q.rho_dif = dup2(p.rho_dif);
+    const float sc = SH ? p.g_scale : 1.0f;
+    q.rho = dup2(SH ? s.rho * sc : s.rho);
+    q.mu15 = dup2((SH ? 1.5f * sc : 1.5f) * s.mu);
+    q.hrho_dif = dup2((SH ? 0.5f * sc : 0.5f) * p.rho_dif);
     q.neg_ug = dup2(-s.ug);
-    q.neg_uF = dup2(-s.uF);
+    q.neg_uF15 = dup2((SH ? -1.5f * sc : -1.5f) * s.uF);
     q.neg_usq15 = dup2(-1.5f * s.usq);
     q.phi = dup2(s.phi);
     q.inv_tau = dup2(p.inv_tau_phi);
     const float wk[2] = {(float)L::w[IA], (float)L::w[ID]};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        q.w3P[k] = dup2(3.0f * wk[k] * s.P);
+        q.w3P[k] = dup2(SH ? wk[k] * (3.0f * s.P - p.g_shift) * sc : 3.0f * wk[k] * s.P);
         q.thw[k] = dup2(s.theta * wk[k]);
-        q.hoc[k] = dup2(p.hocorr ? wk[k] * 0.75f * p.rho_dif * s.lap : 0.0f);
+        q.hoc[k] = dup2(p.hocorr ? (SH ? wk[k] * 0.75f * sc : wk[k] * 0.75f) * p.rho_dif * s.lap : 0.0f);
+        q.nwhs[k] = dup2(SH ? -wk[k] * p.h_shift : 0.0f);
     }
-    q.om45 = (1.0f - s.omega) * 4.5f;
+    q.om45 = (1.0f - s.omega) * (SH ? 4.5f * sc : 4.5f);
     q.tr3 = s.tr3;
+    q.kF = SH ? 1.5f * sc : 1.5f;
     return q;
 }
 
 // Post-collision g* and h* of the pair (I, opp(I)): the arithmetic of
 // collide_dir, two directions per instruction.  hin holds the pulled h of I
 // and opp(I) in its lanes.
-template <int LAT, int I>
+template <int LAT, int I, bool SH>
 __device__ __forceinline__ void collide_pair(const NodeState<float>& s, const PairState& q, float2 hin,
                                              float2* h_out, float2* g_out) {
     using L = Lattice<LAT>;
@@ -693,20 +742,24 @@ __device__ __forceinline__ void collide_pair(const NodeState<float>& s, const Pa
     t = fma2(t, a, q.neg_usq15);
     const float2 Gm1 = mul2(t, w);
     const float2 G = add2(Gm1, w);
-    // K = (Gm1 rho_dif + 3 G mu)(c.grad phi - u.grad phi) + 3 G (c.F - u.F)
-    const float2 A = fma2(Gm1, q.rho_dif, mul2(G, q.mu3));
+    // K / 2 = (Gm1 rho_dif / 2 + 3 G mu / 2) B + 3 G C / 2 with
+    // B = c.grad phi - u.grad phi and C = c.F - u.F; with rho Gm1 it folds into
+    // Gm1 (rho + B rho_dif / 2) + G (3 mu B / 2 + 3 C / 2)
     const float2 B = add2(make_float2(cg, -cg), q.neg_ug);
-    const float2 C = add2(make_float2(cF, -cF), q.neg_uF);
-    const float2 K = fma2(A, B, mul2(mul2(G, dup2(3.0f)), C));
+    const float cF15 = (SH ? q.kF : 1.5f) * cF;
+    const float2 C15 = add2(make_float2(cF15, -cF15), q.neg_uF15);
+    const float2 X = fma2(q.hrho_dif, B, q.rho);
+    const float2 Y = fma2(q.mu15, B, C15);
     // c c : Pi, even in c
     const float ccPi = cdot3<CX * CX, CY * CY, CZ * CZ>(s.pxx, s.pyy, s.pzz) +
                        2.0f * cdot3<CX * CY, CX * CZ, CY * CZ>(s.pxy, s.pxz, s.pyz);
     const float filt = (ccPi - q.tr3) * (q.om45 * (float)L::w[I]);
-    float2 gs = fma2(q.rho, Gm1, add2(q.w3P[WK], dup2(filt)));
-    gs = fma2(K, dup2(0.5f), gs);
-    gs = fma2(a, q.hoc[WK], gs);
+    float2 gs = fma2(a, q.hoc[WK], add2(q.w3P[WK], dup2(filt)));
+    gs = fma2(G, Y, gs);
+    gs = fma2(Gm1, X, gs);
     *g_out = gs;
-    const float2 heq = fma2(q.phi, G, mul2(q.thw[WK], make_float2(cn, -cn)));
+    const float2 heq = SH ? fma2(q.phi, G, fma2(q.thw[WK], make_float2(cn, -cn), q.nwhs[WK]))
+                          : fma2(q.phi, G, mul2(q.thw[WK], make_float2(cn, -cn)));
     *h_out = fma2(add2(heq, make_float2(-hin.x, -hin.y)), q.inv_tau, hin);
 }
 
@@ -751,20 +804,27 @@ struct Moments {
 };
 
 // Over opposite pairs (I, J): the odd moments take g_I - g_J, the even ones
-// g_I + g_J.  gv(i) returns the pulled g of direction i.
+// g_I + g_J.  gv(i) returns the pulled g of direction i.  In FP32 the zeroth
+// moment, which gives the pressure (P = T m0 + ...), is summed compensated
+// like phi (PhiSum: a chain seeded with 1 that collects each addition's
+// rounding error): at tau near 1/2 the acoustic modes are barely damped and
+// the rounding of a plain 10-term sum accumulates in P over the steps.
 template <int LAT, typename GA>
 __device__ __forceinline__ auto g_moments(GA gv) {
     using L = Lattice<LAT>;
     using R = decltype(gv(0));
     Moments<R> m;
-    m.m0 = gv(0);
+    PhiSum<float> c0;
+    if constexpr (std::is_same<R, float>::value) c0.link(gv(0));
+    else m.m0 = gv(0);
     Unroll<1, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int o = L::op[i];
         if constexpr (i < o) {
             constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
             const R sp = gv(i) + gv(o), dm = gv(i) - gv(o);
-            m.m0 += sp;
+            if constexpr (std::is_same<R, float>::value) c0.link(sp);
+            else m.m0 += sp;
             if (CX) { m.mx += cmul<CX>(dm); m.mxx += sp; }
             if (CY) { m.my += cmul<CY>(dm); m.myy += sp; }
             if (CZ) { m.mz += cmul<CZ>(dm); m.mzz += sp; }
@@ -773,6 +833,7 @@ __device__ __forceinline__ auto g_moments(GA gv) {
             if (CY * CZ) m.myz += cmul<CY * CZ>(sp);
         }
     });
+    if constexpr (std::is_same<R, float>::value) m.m0 = c0.value();
     return m;
 }
 
@@ -828,29 +889,32 @@ __device__ __forceinline__ void collide_node(const DirPtrs<typename Storage<ST>:
     // sum_i Gamma_i = 1 from biasing the global phi)
     R hsum = 0;
     if constexpr (std::is_same<R, float>::value) {
-        const PairState q = pair_state<LAT>(s, p);
+        // with 16-bit storage hv(i) and the pair collision's outputs are the
+        // stored values themselves (pair_state): only the number format is
+        // converted on the way to memory
+        constexpr bool SH = St::kShifted;
+        const PairState q = pair_state<LAT, SH>(s, p);
         float2 hsum2 = make_float2(0.0f, 0.0f);
+        auto pk = [&](R v) { return St::pack(v); };
         Unroll<1, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int o = L::op[i];
             if constexpr (i < o) {
-                constexpr double W = L::w[i];
                 float2 hs, gs;
-                collide_pair<LAT, i>(s, q, make_float2(hv(i), hv(o)), &hs, &gs);
+                collide_pair<LAT, i, SH>(s, q, make_float2(hv(i), hv(o)), &hs, &gs);
                 hsum2 = add2(hsum2, hs);
-                const R hsh = (R)W * p.h_shift, gsh = (R)W * p.g_shift;
-                write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.x, hsh, (R)1));
-                write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::store(hs.y, hsh, (R)1));
-                write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.x, gsh, p.g_scale));
-                write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs.y, gsh, p.g_scale));
+                write_dir<LAT, i, WALLS>(D.hout, G, x, y, z, own, nw, St::pack(hs.x));
+                write_dir<LAT, o, WALLS>(D.hout, G, x, y, z, own, nw, St::pack(hs.y));
+                write_dir<LAT, i, WALLS>(D.gout, G, x, y, z, own, nw, St::pack(gs.x));
+                write_dir<LAT, o, WALLS>(D.gout, G, x, y, z, own, nw, St::pack(gs.y));
                 if constexpr (WALLS) {
                     if (p.moving && nw.wall_adj) {
-                        auto sh = [&](R v) { return St::store(v, hsh, (R)1); };
-                        auto sg = [&](R v) { return St::store(v, gsh, p.g_scale); };
-                        moving_wall_write<LAT, i>(D.hout, G, x, y, z, hs.x, s.phi, p, sh);
-                        moving_wall_write<LAT, o>(D.hout, G, x, y, z, hs.y, s.phi, p, sh);
-                        moving_wall_write<LAT, i>(D.gout, G, x, y, z, gs.x, s.rho, p, sg);
-                        moving_wall_write<LAT, o>(D.gout, G, x, y, z, gs.y, s.rho, p, sg);
+                        // the wall term of g in the units of the stored g
+                        const R srho = SH ? s.rho * p.g_scale : s.rho;
+                        moving_wall_write<LAT, i>(D.hout, G, x, y, z, hs.x, s.phi, p, pk);
+                        moving_wall_write<LAT, o>(D.hout, G, x, y, z, hs.y, s.phi, p, pk);
+                        moving_wall_write<LAT, i>(D.gout, G, x, y, z, gs.x, srho, p, pk);
+                        moving_wall_write<LAT, o>(D.gout, G, x, y, z, gs.y, srho, p, pk);
                     }
                 }
             }
@@ -879,7 +943,13 @@ __device__ __forceinline__ void collide_node(const DirPtrs<typename Storage<ST>:
         constexpr double W0 = L::w[0];
         R hs, gs;
         collide_dir<LAT, 0, R>(s, p, (R)0, &hs, &gs);
-        write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
+        // stored rest value: phi - sum of the moving h*_i (less w_0 h_shift);
+        // with 16-bit storage hsum sums the stored values h*_i - w_i h_shift,
+        // so phi - h_shift - hsum is the stored h*_0 - w_0 h_shift (sum w = 1)
+        if constexpr (St::kShifted)
+            write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::pack((s.phi - p.h_shift) - hsum));
+        else
+            write_dir<LAT, 0, WALLS>(D.hout, G, x, y, z, own, nw, St::store(s.phi - hsum, (R)W0 * p.h_shift, (R)1));
         write_dir<LAT, 0, WALLS>(D.gout, G, x, y, z, own, nw, St::store(gs, (R)W0 * p.g_shift, p.g_scale));
     }
 }
@@ -891,8 +961,10 @@ struct MarchSmem {
     R phis[4][TY + 2 * HY][TX + 2];
     // pulled h of the thread's own node on the last two filled planes: the fill
     // of plane z+1 loads them anyway, the collision of the next iteration
-    // reads them back (each thread touches only its own column: no barrier)
-    R hown[2][Lattice<LAT>::Q][TX * TY];
+    // reads them back (each thread touches only its own column: no barrier).
+    // The moving directions only: the collision closes the rest population
+    // with phi.
+    R hown[2][Lattice<LAT>::Q - 1][TX * TY];
 };
 
 // The march of one CTA over planes [z0, z1) of the tile column at (x0, y0).
@@ -940,15 +1012,22 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
         pull_xy(G, stencil_coord(x0 + lx - 1, G.NX, G.wall[0]),
                 HY ? stencil_coord(y0 + ly - HY, G.NY, G.wall[1]) : y0, ring_xy);
     }
+    // 16-bit storage keeps h_i - w_i h_shift: the fill sums and keeps the
+    // stored values as they are (phi = their sum + h_shift, as sum w_i = 1)
+    // and the collision works on them, so no population is shifted on load
+    // or store
+    auto with_shift = [&](R v) {
+        if constexpr (St::kShifted) return v + p.h_shift;
+        else return v;
+    };
     auto ring_phi = [&](PullOffsets po) {
         checked_offsets(po, G.NP);
         PhiSum<R> phi;
         Unroll<0, Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            constexpr double W = L::w[i];
-            phi.add(St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1));
+            phi.add(St::raw(pull_pad<LAT, i, false>(D.hin, po)));
         });
-        return phi.value();
+        return with_shift(phi.value());
     };
     // the thread's own position (its pulled h kept in hown[hs]) and its share
     // of the halo ring; with one ring position per thread, both sets of loads
@@ -977,14 +1056,13 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
                 PhiSum<R> phi, rphi;
                 Unroll<0, Q>::run([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    constexpr double W = L::w[i];
-                    const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
-                    hown[hs][i][tid] = v;
+                    const R v = St::raw(hv[i]);
+                    if constexpr (i > 0) hown[hs][i - 1][tid] = v;
                     phi.add(v);
-                    rphi.add(St::load(rv[i], (R)W * p.h_shift, (R)1));
+                    rphi.add(St::raw(rv[i]));
                 });
-                phis[slot][ty + HY][tx + 1] = phi.value();
-                if (ring) (&phis[slot][0][0])[ring_off] = rphi.value();
+                phis[slot][ty + HY][tx + 1] = with_shift(phi.value());
+                if (ring) (&phis[slot][0][0])[ring_off] = with_shift(rphi.value());
             } else {
                 Unroll<0, Q>::run([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
@@ -993,12 +1071,11 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
                 PhiSum<R> phi;
                 Unroll<0, Q>::run([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    constexpr double W = L::w[i];
-                    const R v = St::load(hv[i], (R)W * p.h_shift, (R)1);
-                    hown[hs][i][tid] = v;
+                    const R v = St::raw(hv[i]);
+                    if constexpr (i > 0) hown[hs][i - 1][tid] = v;
                     phi.add(v);
                 });
-                phis[slot][ty + HY][tx + 1] = phi.value();
+                phis[slot][ty + HY][tx + 1] = with_shift(phi.value());
             }
         } else {
             {
@@ -1008,12 +1085,11 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
                 PhiSum<R> phi;
                 Unroll<0, Q>::run([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    constexpr double W = L::w[i];
-                    const R v = St::load(pull_pad<LAT, i, false>(D.hin, po), (R)W * p.h_shift, (R)1);
-                    hown[hs][i][tid] = v;
+                    const R v = St::raw(pull_pad<LAT, i, false>(D.hin, po));
+                    if constexpr (i > 0) hown[hs][i - 1][tid] = v;
                     phi.add(v);
                 });
-                phis[slot][ty + HY][tx + 1] = phi.value();
+                phis[slot][ty + HY][tx + 1] = with_shift(phi.value());
             }
             for (int k = tid; k < NRING; k += TX * TY) {
                 int lx, ly;
@@ -1060,7 +1136,7 @@ __device__ __forceinline__ void march(const DirPtrs<typename Storage<ST>::S, Lat
         }
         __syncthreads();
         if (active) {
-            auto hv = [&](int i) { return hown[(j + 1) & 1][i][tid]; };
+            auto hv = [&](int i) { return hown[(j + 1) & 1][i - 1][tid]; };   // i >= 1
             // only a node next to a wall writes bounce-back ghost cells: the
             // rest take the wall-free collision (fewer live registers)
             if (WALLS && node_writes<LAT>(G, x, y, z).wall_adj)

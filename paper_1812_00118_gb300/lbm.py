@@ -25,6 +25,7 @@ STORE_NAMES = {F64: "f64", F32: "f32", F16S: "f16s", BF16S: "bf16s"}
 
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTSUP, ECHECKED = 0, -1, -2, -3, -4, -5, -6, -7
 INIT_NONEQ = 1
+CREATE_GHOST_BAND = 1
 
 
 class LbmLibraryMissing(RuntimeError):
@@ -59,6 +60,8 @@ _VP, _DP, _IP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER
 SIGNATURES = [
     ("lbm_create", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), _VP,
                                   ctypes.POINTER(_VP)]),
+    ("lbm_create_ex", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), _VP,
+                                     ctypes.c_int, ctypes.POINTER(_VP)]),
     ("lbm_init_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     ("lbm_init_fields_ex", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -244,9 +247,11 @@ class Simulation:
     """One LB domain on the current CUDA device (owns an lbm_ctx).
 
     shape is the user grid (nx, ny) for D2Q9 or (nx, ny, nz) for D3Q19;
-    bc is a per-axis tuple of PERIODIC / WALL."""
+    bc is a per-axis tuple of PERIODIC / WALL; ghost_band=True keeps ghost
+    cells along the periodic axes too (lbm_create_ex with
+    LBM_CREATE_GHOST_BAND), which the bulk-copy step tile needs."""
 
-    def __init__(self, lattice, shape, params, bc=(PERIODIC, PERIODIC, PERIODIC), stream=None):
+    def __init__(self, lattice, shape, params, bc=(PERIODIC, PERIODIC, PERIODIC), stream=None, ghost_band=False):
         lib = load()
         self.lattice = lattice
         self.dim = 2 if lattice == D2Q9 else 3
@@ -265,8 +270,8 @@ class Simulation:
             stream = torch.cuda.current_stream().cuda_stream
         self._stream = stream
         ctx = ctypes.c_void_p()
-        _check(lib.lbm_create(ctypes.byref(g), lattice, ctypes.byref(params), ctypes.c_void_p(stream),
-                              ctypes.byref(ctx)), "lbm_create")
+        _check(lib.lbm_create_ex(ctypes.byref(g), lattice, ctypes.byref(params), ctypes.c_void_p(stream),
+                                 CREATE_GHOST_BAND if ghost_band else 0, ctypes.byref(ctx)), "lbm_create_ex")
         self._ctx = ctx
 
     # -- lifetime

@@ -38,7 +38,7 @@ def case(lat, shape, bc, tile, steps, store):
         phi, u, P = I.smooth_random((1, ny, nx), 5, dim=2)
         ushape = np.ascontiguousarray(np.stack([u[0], u[1]]).reshape(-1))
     prm = L.make_params(M=0.1, W=3.0, sigma=0.01, rho_L=0.1, rho_H=1.0, nu_L=0.05, nu_H=0.02, store=store)
-    sim = L.Simulation(lat, shape, prm, bc=bc)
+    sim = L.Simulation(lat, shape, prm, bc=bc, ghost_band=tile == 4)
     sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), ushape, np.ascontiguousarray(P.reshape(-1)))
     if tile is not None:
         try:

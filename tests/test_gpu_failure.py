@@ -58,7 +58,7 @@ def test_nan_input_diverged_then_recovers(lbm):
 
 def test_pipeline_wait_timeout_reported(lbm):
     phi, u, P = fields((12, 16, 40))
-    sim = lbm.Simulation(lbm.D3Q19, (40, 16, 12), lbm.make_params(store=lbm.F32))
+    sim = lbm.Simulation(lbm.D3Q19, (40, 16, 12), lbm.make_params(store=lbm.F32), ghost_band=True)
     try:
         sim.set_tile(4, 4)
     except lbm.LbmError as e:

@@ -52,14 +52,14 @@ def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False, s
     nz, ny, nx = shape
     phi, u, P = I.smooth_random(shape, 41, dim=2 if lat_id == 0 else 3)
     prm = L.make_params(M=0.1, W=3.0, sigma=0.01, rho_L=0.01, rho_H=1.0, nu_L=0.1, nu_H=0.05,
-                        store=L.F64 if store is None else store)
+                        store=L.F64 if store is None else store, g_scale=1e3 if store == L.F16S else 0.0)
     user = (nx, ny) if lat_id == 0 else (nx, ny, nz)
     if batch:
         b = L.Batch([user], prm, bcs=[bc])
         sim = b.grid(0)
     else:
         b = None
-        sim = L.Simulation(lat_id, user, prm, bc=bc)
+        sim = L.Simulation(lat_id, user, prm, bc=bc, ghost_band=tile is not None and tile[0] == 4)
         if tile is not None:
             sim.set_tile(*tile)
     for side in (0, 1):
@@ -79,7 +79,7 @@ def run_case(L, lat_id, shape, bc, axis, walls, steps, tile=None, batch=False, s
     return out, oracle_macro_flat(h, g, lat, p, lat_id), b
 
 
-PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy", "batch", "async")
+PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy", "batch", "async", "f16s")
          if not (path == "batch" and CASES[c][0] == 1)]   # batches hold D2Q9 grids
 
 
@@ -87,11 +87,17 @@ PATHS = [(c, path) for c in range(len(CASES)) for path in ("default", "bulkcopy"
 def test_sliding_walls_against_oracle(lbm, case, path):
     lat_id, shape, bc, axis, walls = CASES[case]
     tile = {"bulkcopy": (4, 3), "async": (7, 5)}.get(path)
-    store = lbm.F32 if path == "async" else lbm.F64
+    store = {"async": lbm.F32, "f16s": lbm.F16S}.get(path, lbm.F64)
     (f, Pg, ru), (fo, Po, ruo), _ = run_case(lbm, lat_id, shape, bc, axis, walls, 40, tile=tile,
                                              batch=path == "batch", store=store)
-    tol = 1e-5 if path == "async" else 1e-10
-    assert normwise(f, fo) < tol and normwise(Pg, Po) < tol and normwise(ru, ruo) < tol
+    # FP16-shifted storage (default tile, the wall term written in the units of
+    # the stored values): its 11-bit rounding bounds the agreement, while the
+    # wall-driven momentum is what rho u mostly is, so a wrong scale or sign of
+    # the wall term would be off by its own size
+    tol = {"async": 1e-5, "f16s": 2e-2}.get(path, 1e-10)
+    errs = (normwise(f, fo), normwise(Pg, Po), normwise(ru, ruo))
+    print(path, "errors phi, P, rho u:", errs)
+    assert max(errs) < tol, errs
 
 
 def test_layered_couette_f32(lbm):

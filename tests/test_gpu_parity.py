@@ -42,8 +42,10 @@ def lbm():
     return L
 
 
-def make_case(L, lat_id, shape_zyx, bc, store, seed=3, drop=False, **kw):
-    """Seeded smooth random (or drop) fields; returns (sim, oracle h, g, lat, p)."""
+def make_case(L, lat_id, shape_zyx, bc, store, seed=3, drop=False, ghost_band=False, **kw):
+    """Seeded smooth random (or drop) fields; returns (sim, oracle h, g, lat, p).
+    ghost_band: the layout with ghost cells along the periodic axes too (the
+    bulk-copy tile needs it)."""
     nz, ny, nx = shape_zyx
     if drop:
         # centre off the nodes: at a node with grad phi = 0 exactly and theta != 0
@@ -58,7 +60,7 @@ def make_case(L, lat_id, shape_zyx, bc, store, seed=3, drop=False, **kw):
     base.update(kw)
     prm = L.make_params(**base)
     user_shape = (nx, ny) if lat_id == 0 else (nx, ny, nz)
-    sim = L.Simulation(lat_id, user_shape, prm, bc=bc)
+    sim = L.Simulation(lat_id, user_shape, prm, bc=bc, ghost_band=ghost_band)
     sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, lat_id),
                     np.ascontiguousarray(P.reshape(-1)))
     lat = oracle_lattice(lat_id)
@@ -194,13 +196,14 @@ def test_config1_static_droplet_f64(lbm):
     undefined, so rounding decides the trajectory: the oracle run twice with a
     1e-15 relative perturbation of h separates to ~1e-5 by step 300.  After
     2000 steps the test therefore checks what is unique: exact phi
-    conservation and Laplace's law, and bounds the separation of phi, P and
+    conservation, and bounds the separation of phi, P and
     the Laplace jump by ten times the widest spread of three perturbed twins
     of the oracle or 1e-3 normwise, whichever is larger.  The GPU's rounding
     is itself such a perturbation, and where it lands is a matter of chance:
     two builds whose FP64 steps differ only by the compiler's contraction of
     a * b + c (1e-16 after one step) ended 2000 steps at P 3.2e-5 and 3.2e-4
-    from the oracle, the twins at 2.1e-5."""
+    from the oracle, the twins at 2.1e-5.  Laplace's law is checked on the
+    relaxed drop, the same run continued to 40000 steps."""
     prm = lbm.make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.05 / 3, nu_H=0.05 / 3,
                           store=lbm.F64)
     shape = (1, 64, 64)
@@ -242,11 +245,21 @@ def test_config1_static_droplet_f64(lbm):
     sJ = max(abs(D.laplace_jump(Pt.reshape(shape), (31.5, 31.5, 0), R, 4.0) - dP_o) for _, Pt, _ in tw)
     dP_g = sim.laplace((31.5, 31.5), R - 8.0, R + 8.0)
     assert abs(dP_g - dP_o) <= max(10 * sJ, 1e-3 * abs(dP_o))
-    # and Laplace's law itself (Section 4.1): at W = 4 the jump of a relaxed
-    # drop sits 6-7 % below sigma / R (the oracle's pin); after 2000 steps at
-    # tau = 0.55 pressure waves still ring, so the bound is 15 %
-    print("config 1 Laplace jump / (sigma / R): GPU %.4f, oracle %.4f" % (dP_g / (0.01 / R), dP_o / (0.01 / R)))
-    assert abs(dP_g / (0.01 / R) - 1.0) < 0.15, dP_g / (0.01 / R)
+    print("config 1 Laplace jump / (sigma / R) after 2000 steps: GPU %.4f, oracle %.4f"
+          % (dP_g / (0.01 / R), dP_o / (0.01 / R)))
+    # Laplace's law itself (Section 4.1) holds for the relaxed drop only.  At
+    # step 2000 the jump is still in a slow pressure oscillation (period about
+    # 4000 steps; in the oracle 1.73 sigma/R at step 2000, 0.48 at 3500, 1.28
+    # at 5500, then 0.95 +- 0.03 from step 13000 to 20000), so the law is
+    # checked on the GPU run continued to 40000 steps: at W = 4 the relaxed
+    # jump sits 5-7 % below sigma / R (the oracle's Laplace pin), bound 10 %.
+    sim.step(38000)
+    R40 = D.effective_radius(sim.macro()[0].reshape(shape), 2, True)
+    ratio = sim.laplace((31.5, 31.5), R40 - 8.0, R40 + 8.0) / (0.01 / R40)
+    print("config 1 Laplace jump / (sigma / R) after 40000 steps: GPU %.4f" % ratio)
+    assert abs(ratio - 1.0) < 0.10, ratio
+    d2 = sim.diagnostics()
+    assert abs(d2["sum_phi"] - d0["sum_phi"]) < 1e-11 * d0["sum_phi"]
 
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
@@ -255,17 +268,17 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
     bulk tensor copy pipeline, tile 4; one-wave launches, tiles 5-6 and 9; 7
     CTAs per SM, tile 8) and z-chunk length computes the same arithmetic: FP64
     results agree to rounding (the compiler may contract a*b+c differently per
-    instantiation).  The cp.async tile (7) computes in FP32 only."""
+    instantiation).  The cp.async tile (7) computes in FP32 only.  Every
+    context has the ghost band the bulk-copy tile reads."""
     ref = None
     for tile, lz in ((0, 16), (1, 3), (2, 7), (3, 1), (0, 100), (4, 1), (4, 7), (5, 5), (6, 1), (6, 100),
                      (7, 4), (8, 16), (8, 1), (9, 3), (9, 100)):
-        sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64)
+        sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F64, ghost_band=True)
         try:
             sim.set_tile(tile, lz)
         except lbm.LbmError as e:
-            # bulk copies (4) may not apply to a grid; cp.async (7) has no
-            # FP64 form
-            assert e.code == lbm.ENOTSUP and tile in (4, 7), tile
+            # cp.async (7) has no FP64 form
+            assert e.code == lbm.ENOTSUP and tile == 7, tile
             continue
         sim.step(7)
         hg, gg = sim.get_populations()
@@ -322,16 +335,34 @@ def test_tile_switching_f32(lbm, lat_id, shape, bc):
     a run on one tile does."""
     ho, go = oracle_pops_after(lbm, lat_id, shape, bc, 7)
     hof, gof = oracle_to_lib_pops(ho, lat_id), oracle_to_lib_pops(go, lat_id)
-    sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32, ghost_band=True)
     for tile, n in ((8, 1), (4, 2), (0, 1), (4, 1), (7, 1), (9, 1)):
-        try:
-            sim.set_tile(tile, 5)
-        except lbm.LbmError as e:
-            assert e.code == lbm.ENOTSUP and tile == 4, tile
-            sim.set_tile(8, 5)
+        sim.set_tile(tile, 5)
         sim.step(n)
     hg, gg = sim.get_populations()
     assert normwise(hg, hof) < 1e-5 and normwise(gg, gof) < 1e-5, (normwise(hg, hof), normwise(gg, gof))
+
+
+@pytest.mark.parametrize("lat_id,shape,bc", CASES, ids=IDS)
+def test_layouts_agree_bit_exact(lbm, lat_id, shape, bc):
+    """The default layout (ghost cells along walled axes only) and the one
+    with a ghost band along the periodic axes too hold the same values at
+    different offsets: the same tile gives the same populations bit for bit,
+    FP64 and FP32, after 7 steps.  Only the banded layout takes the bulk-copy
+    tile; the default one refuses it with LBM_ENOTSUP."""
+    for store in (lbm.F64, lbm.F32):
+        res = []
+        for band in (False, True):
+            sim, *_ = make_case(lbm, lat_id, shape, bc, store, ghost_band=band)
+            sim.step(7)
+            res.append(sim.get_populations())
+        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1]), store
+    sim, *_ = make_case(lbm, lat_id, shape, bc, lbm.F32)
+    periodic_xy = bc[0] == 0 or (lat_id == 1 and bc[1] == 0)
+    if periodic_xy:
+        with pytest.raises(lbm.LbmError) as e:
+            sim.set_tile(4, 4)
+        assert e.value.code == lbm.ENOTSUP
 
 
 @pytest.mark.parametrize("store", ["F64", "F32"])
