@@ -23,6 +23,7 @@ scaling): the single-domain step has no data-parallel split without a halo
 exchange, which this build does not implement.
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--ttt-iters", type=int, default=4000, help="ttt: Adam iterations (mini-batch 8)")
     ap.add_argument("--ttt-apply", type=int, default=4,
                     help="ttt: surrogate applications at inference (each jumps 2000 steps)")
-    ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt", "rising"], default="bubble128",
+    ap.add_argument("--workload", choices=["bubble128", "batch512", "ttt", "rising", "surrogate"], default="bubble128",
                     help="bubble128: the D3Q19 128^3 bubble (default); batch512: 512 uneven D2Q9 grids "
                          "stepped as one batch; ttt: time-to-tolerance of D2Q9 drop relaxation for plain FP32, "
                          "16-bit storage, the batch and the learned warm start; rising: the 256x256x512 rising "
@@ -885,6 +886,104 @@ def run_ttt(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- surrogate training
+SG_METRIC = "learned warm-start surrogate training throughput (TFLOP/s), 4-level U-Net, 8 x 256^2 images"
+SG_WORKLOAD = ("periodic 3x3-convolution U-Net of four levels (32-128 channels, BF16 operands, FP32 accumulation), "
+               "mini-batch of 8 images of 256^2 x 4 channels, one training step = forward, backward, Adam")
+
+
+def run_surrogate(args):
+    """Training throughput of the warm-start surrogate on the library's kernels:
+    convolution multiply-add FLOPs (forward, input and weight gradients, padded
+    channel counts as computed) per second over K timed training steps; the
+    dominant kernel (the tcgen05 forward convolution of the full-resolution
+    decoder layer d1, 64 -> 32 channels) timed alone against the measured
+    BF16 peak; e2e with the batch copied from pinned host memory and the loss
+    read back every step."""
+    import torch
+
+    from paper_1812_00118_gb300 import build, lbm
+    from paper_1812_00118_gb300.surrogate import Surrogate, _ptr
+    torch.cuda.set_device(0)
+    build.build()
+    lbm.load()
+    N, H = 8, 256
+    sg = Surrogate(N, H, H, seed=0)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x_host = torch.randn(N * H * H, 4, generator=g).pin_memory()
+    t_host = (x_host + 0.1 * torch.randn(N * H * H, 4, generator=g)).pin_memory()
+    x = x_host.cuda()
+    t = t_host.cuda()
+    flops = sg.flops_per_image(backward=True) * N
+    # the dominant kernel alone, first (so that a profiler finds it as the 6th
+    # convolution launch): forward convolution of d1 (level 0, 64 -> 32)
+    ly = sg.layers["d1"]
+    hh, ww = sg.HW[0]
+    conv_flops = 2 * N * hh * ww * 9 * ly["cip"] * ly["cop"]
+    # two input / output pairs used in turn: 268 MB, more than the 129 MB L2
+    xin = [torch.randn(N * hh * ww, ly["cip"], generator=g).to(torch.bfloat16).cuda() for _ in range(2)]
+    yout = [torch.zeros(N * hh * ww, ly["cop"], dtype=torch.float32, device="cuda") for _ in range(2)]
+    lib = lbm.load()
+    reps = 50
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream().cuda_stream
+    clocks = ClockSampler(0)
+    time.sleep(0.3)
+    for k in range(reps + 5):
+        if k == 5:
+            c0.record()
+        rc = lib.lbm_sg_conv3x3(_ptr(xin[k & 1]), ly["cip"], _ptr(ly["W16"]), _ptr(ly["b"]), _ptr(yout[k & 1]),
+                                ly["cop"], N, hh, ww, ly["cip"], ly["cop"], ctypes.c_void_p(stream))
+        if rc != 0:
+            raise RuntimeError(f"lbm_sg_conv3x3: {rc}")
+    c1.record()
+    c1.synchronize()
+    conv_ms = c0.elapsed_time(c1) / reps
+    for _ in range(args.warmup):
+        sg.train_step(x, t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sg.train_step(x, t)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # end to end: the batch from pinned host memory, the loss back to the host
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e0.record()
+    for _ in range(args.steps):
+        x.copy_(x_host, non_blocking=True)
+        t.copy_(t_host, non_blocking=True)
+        loss = sg.train_step(x, t)
+        loss_host.copy_(loss.reshape(1), non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    clk = clocks.stop()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    status = int(lib.lbm_sg_status(None))
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    peak = float(peaks["bf16_tflops"])
+    line = {
+        "metric": SG_METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": SG_WORKLOAD, "images": N, "grid": H, "flops_per_step": flops,
+                   "l2": "activations of one step (about 0.5 GB) exceed the 129 MB L2"},
+        "roofline": {"bound": "tensor", "achieved": conv_flops / (conv_ms * 1e-3) / 1e12, "peak": peak,
+                     "unit": "TFLOP/s", "frac": conv_flops / (conv_ms * 1e-3) / 1e12 / peak, "traffic": None,
+                     "peak_kind": "measured (bf16_tflops, burst: the kernel is timed alone)",
+                     "kernel": "lbm_sg_conv3x3 forward, layer d1 (64 -> 32 channels, 8 x 256^2), tcgen05",
+                     "flops_per_launch": conv_flops, "mean_launch_ms": conv_ms},
+        "clocks": clk,
+        "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": 2 * x_host.numel() * 4, "d2h_bytes_per_step": 8},
+        "sg_status": status,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "ttt":
@@ -903,6 +1002,15 @@ def main():
                   flush=True)
         else:
             run_rising(args)
+        return
+    if args.workload == "surrogate":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "metric": SG_METRIC,
+                              "unavailable": "the oracle surrogate is a plain FP64 numpy pass used to check gradients; "
+                                             "the LB oracle is timed on the bubble128 and batch512 workloads"}),
+                  flush=True)
+        else:
+            run_surrogate(args)
         return
     if args.workload == "batch512":
         (run_batch_reference if args.impl == "reference" else run_batch)(args)
