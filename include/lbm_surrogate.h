@@ -33,11 +33,16 @@ extern "C" {
 
 /* y (float) = periodic 3x3 convolution of x (bf16) with w (bf16), plus bias
  * (float[Co], may be NULL): an implicit GEMM on the tcgen05 tensor cores,
- * bf16 products, FP32 sums in tensor memory, 128 pixels per CTA.  x's channel
- * stride csx is a multiple of 8 and x and w start on 16-byte boundaries (the
- * operands are staged in 16-byte copies); LBM_EINVAL otherwise.  A bounded
- * wait inside the kernel that gives up leaves its CTA's part of y unwritten
- * and is reported by lbm_sg_status. */
+ * bf16 products, FP32 sums in tensor memory, 128 pixels per MMA.  When W is a
+ * multiple of 128 and the weights of all nine taps fit in shared memory with
+ * four input rows (9 Co Ci + 4 x 130 Ci bf16 values, at most 200 KB), a CTA
+ * marches a 128-pixel row segment down a chunk of rows, copying every input
+ * row into shared memory once; otherwise a CTA takes 128 consecutive pixels
+ * and copies each tap's shifted rows.  Both accumulate the taps in the same
+ * order.  x's channel stride csx is a multiple of 8 and x and w start
+ * on 16-byte boundaries (the operands are staged in 16-byte copies);
+ * LBM_EINVAL otherwise.  A bounded wait inside the kernel that gives up leaves
+ * its CTA's part of y unwritten and is reported by lbm_sg_status. */
 int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, float* y, int csy, int N, int H, int W,
                    int Ci, int Co, void* stream);
 

@@ -10,7 +10,8 @@
 // 16 (zero-padded by the caller), pixel counts multiples of 16.
 //
 // The forward (and input-gradient) convolution runs on the tcgen05 tensor
-// cores with the accumulator in tensor memory (conv_tc_kernel); the weight
+// cores with the accumulator in tensor memory (conv_row_kernel for images
+// whose width is a multiple of 128, conv_tc_kernel otherwise); the weight
 // gradient, a GEMM over pixels, uses the warp-level mma.sync m16n8k16 BF16
 // instruction with fragments gathered straight from the channels-last
 // tensors.  Both are implicit GEMMs without an im2col buffer.
@@ -36,7 +37,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 __device__ __forceinline__ uint32_t pack_pair(const bf16* lo, const bf16* hi) {
     const uint32_t a = *reinterpret_cast<const unsigned short*>(lo);
     const uint32_t b = *reinterpret_cast<const unsigned short*>(hi);
@@ -276,6 +276,180 @@ size_t conv_tc_smem_bytes(int Ci, int Co) {
 }
 
 __device__ int g_sg_err;   // a bounded wait of a surrogate kernel gave up
+
+// ---------------------------------------------------------------- tcgen05 convolution, row march
+// The same convolution for images whose width is a multiple of 128: a CTA
+// owns a 128-pixel segment of one image row and marches down a chunk of
+// rows.  The shifted activations of a 3x3 tap are then rows of a halo
+// strip: for row r the taps read input rows r - 1, r, r + 1 at pixel
+// offsets -1, 0, +1 around the segment.  The strip holds four input rows
+// (130 pixels each, the periodic neighbours included) in the tensor core's
+// no-swizzle K-major layout, one 16-byte row per (pixel, 8 channels): a tap's
+// A operand is the strip row of its dy started (1 + dx) pixels in, 128 rows
+// of 16 bytes, 8-row core matrices 128 bytes apart, 8-channel planes 130 x 16
+// bytes apart.  Every input row is copied into shared memory once (the tap
+// kernel above copies it nine times), the weights of all nine taps stay
+// resident for the whole march, and one thread issues the 9 x Ci/16 MMAs of
+// a row into one of two tensor-memory accumulators while the CTA writes out
+// the previous row from the other and the copy of the next input row is in
+// flight.  Every wait is bounded, as in the tap kernel.
+constexpr int kRowM = 128;          // pixels of a row segment (MMA M)
+constexpr int kRowHalo = kRowM + 2;
+constexpr int kRowSlots = 4;        // input rows resident in the strip
+
+__host__ __device__ constexpr uint32_t row_plane_bytes() { return kRowHalo * 16; }
+__host__ __device__ inline uint32_t row_slot_bytes(int Ci) { return (uint32_t)(Ci / 8) * row_plane_bytes(); }
+__host__ __device__ inline uint32_t row_w_bytes(int Ci, int Co) { return (uint32_t)9 * Co * Ci * 2; }
+size_t conv_row_smem_bytes(int Ci, int Co) {
+    return (size_t)kRowSlots * row_slot_bytes(Ci) + row_w_bytes(Ci, Co);
+}
+// tensor-memory columns of the two accumulators (a power of two, at least 32)
+__host__ __device__ inline uint32_t row_tmem_cols(int Co) {
+    const int need = 2 * Co;
+    return need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : 256u));
+}
+
+__global__ void __launch_bounds__(128, 1)
+conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w, const float* __restrict__ bias,
+                float* __restrict__ y, int csy, int N, int H, int W, int Ci, int Co, int rows_per_cta, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = W / kRowM;
+    const int chunks = (H + rows_per_cta - 1) / rows_per_cta;
+    int b = blockIdx.x;
+    const int chunk = b % chunks;
+    b /= chunks;
+    const int seg = b % segs, n = b / segs;
+    const int y0 = chunk * rows_per_cta;
+    const int y1 = y0 + rows_per_cta < H ? y0 + rows_per_cta : H;
+    const int x0 = seg * kRowM;
+    const uint32_t sb = smem_u32(smem);
+    const uint32_t slot_bytes = row_slot_bytes(Ci);
+    const uint32_t wb = sb + kRowSlots * slot_bytes;     // weights: [tap][ci chunk][co][16 bytes]
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    const uint32_t ncols = row_tmem_cols(Co);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc_bf16(kRowM, Co);
+    const int nch = Ci / 8;
+    const long long img = (long long)n * H * W;
+    // input row yy (wrapped) into strip slot yy & 3: pixels x0 - 1 .. x0 + 128 (wrapped)
+    auto copy_row = [&](int yy) {
+        const int yr = ((yy % H) + H) % H;
+        const uint32_t dst = sb + (uint32_t)(yy & 3) * slot_bytes;
+        const bf16* row = x + (img + (long long)yr * W) * csx;
+        for (int k = tid; k < nch * kRowHalo; k += kRowM) {
+            const int c = k / kRowHalo, px = k - c * kRowHalo;
+            int xx = x0 - 1 + px;
+            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            cp_async16(dst + c * row_plane_bytes() + px * 16, row + (long long)xx * csx + c * 8, 16u);
+        }
+    };
+    // prologue: the weights of every tap and input rows y0 - 1 .. y0 + 1, one group
+    for (int k = tid; k < 9 * nch * Co; k += kRowM) {
+        const int co = k % Co, rest = k / Co, c = rest % nch, tap = rest / nch;
+        cp_async16(wb + ((uint32_t)(tap * nch + c) * Co + co) * 16, w + ((long long)co * 9 + tap) * Ci + c * 8, 16u);
+    }
+    for (int yy = y0 - 1; yy <= y0 + 1; ++yy) copy_row(yy);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    bool ok = true;
+    // row j of the march (row y0 + j) accumulates in buffer j & 1 and commits
+    // to barrier j & 1: the (j >> 1)-th phase of that barrier
+    auto wait_row = [&](int j) { return mbar_wait_bounded(bar0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1u, kTcPolls); };
+    auto epilogue = [&](int j) {
+        const int r = y0 + j;
+        const uint32_t acc = tmem + (uint32_t)((j & 1) * Co) + ((uint32_t)(32 * warp) << 16);
+        const long long pix = img + (long long)r * W + x0 + 32 * warp + lane;
+        float* out = y + pix * csy;
+        const bool vec = (csy & 3) == 0 && ((uintptr_t)y & 15) == 0;
+        for (int c0 = 0; c0 < Co; c0 += 16) {
+            float v[16];
+            tc_ld16(acc + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += bias ? bias[c0 + i] : 0.0f;
+            if (vec) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) out[c0 + i] = v[i];
+            }
+        }
+    };
+    const int nrows = y1 - y0;
+    int issued = 0;   // rows whose MMAs were issued and committed
+    for (int j = 0; j < nrows && ok; ++j) {
+        const int r = y0 + j;
+        // (1) row j - 1: its MMAs done (they read strip slot (r - 2) & 3 last),
+        // its accumulator out
+        if (j > 0) {
+            if (!__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(j - 1);
+        }
+        // (2) input row r + 2 into the slot row r - 2 held
+        const bool more = r + 2 <= y1;
+        if (more) {
+            copy_row(r + 2);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        // (3) rows r - 1 .. r + 1 landed (only the group just issued may be pending)
+        if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        // (4) the 9 x Ci/16 MMAs of row r into buffer j & 1
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)((j & 1) * Co);
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                const uint32_t a_s = sb + (uint32_t)((r + dy) & 3) * slot_bytes + (uint32_t)(1 + dx) * 16;
+                const uint32_t b_s = wb + (uint32_t)tap * nch * Co * 16;
+                for (int s2 = 0; s2 < Ci / 16; ++s2) {
+                    const uint64_t ad = tc_smem_desc(a_s + 2 * s2 * row_plane_bytes(), row_plane_bytes(), 128);
+                    const uint64_t bd = tc_smem_desc(b_s + 2 * s2 * (Co * 16), Co * 16, 128);
+                    tc_mma(acc, ad, bd, idesc, (tap > 0 || s2 > 0) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8 * (j & 1))
+                         : "memory");
+        }
+        issued = j + 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last issued row: its MMAs complete after every earlier one (waited
+    // for on the failure path too, before the tensor memory is freed)
+    if (issued > 0) {
+        const bool done = wait_row(issued - 1);
+        const bool all = __syncthreads_and(ok && done) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (all && issued == nrows) epilogue(issued - 1);
+        ok = all && ok;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (!ok && tid == 0) atomicExch(err, 1);
+}
 
 // partial[chunk, co, tap, ci] = sum over the chunk's pixels p of gy[p, co] x[shift(p, tap), ci];
 // one warp per (chunk, tap, 16 output channels, 8 input channels).
@@ -698,6 +872,38 @@ __global__ void smooth_kernel(const double* __restrict__ a, double* __restrict__
     b[p] = c + k * lap;
 }
 
+constexpr size_t kRowSmemMax = 200 * 1024;
+
+// Dynamic shared memory of a row-march launch: its need, raised if necessary
+// so that no more CTAs fit on an SM than its 512 tensor-memory columns serve
+// at once (each CTA holds row_tmem_cols(Co) of them for its whole life).
+size_t conv_row_launch_smem(size_t need, int Co) {
+    const int per_sm = 512 / (int)row_tmem_cols(Co);
+    const size_t sm_bytes = 228 * 1024;            // shared memory of an SM
+    const size_t floor_bytes = sm_bytes / (size_t)(per_sm + 1) + 1;
+    return need > floor_bytes ? need : floor_bytes;
+}
+
+// Resident row-march CTAs on the current device (SMs x CTAs per SM), with the
+// attribute for large dynamic shared memory set once per device.
+cudaError_t conv_row_slots(size_t need, int Co, int* out) {
+    static bool attr_set[64] = {};
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(conv_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmemMax);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_row_kernel, kRowM, conv_row_launch_smem(need, Co));
+    if (e != cudaSuccess) return e;
+    *out = sms * (occ > 0 ? occ : 1);
+    return cudaSuccess;
+}
+
 bool conv_dims_ok(long long M, int Ci, int Co) { return M > 0 && M % 16 == 0 && Ci > 0 && Ci % 16 == 0 && Co > 0 && Co % 16 == 0; }
 
 }  // namespace
@@ -725,6 +931,22 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     }
     int* err = nullptr;
     if (cudaGetSymbolAddress((void**)&err, g_sg_err) != cudaSuccess) return LBM_ECUDA;
+    // rows of 128-pixel segments: the row-march kernel, when its strip and
+    // the weights of all taps fit in shared memory
+    const size_t row_smem = conv_row_smem_bytes(Ci, Co);
+    if (W % kRowM == 0 && H >= 2 && row_smem <= kRowSmemMax) {
+        int slots = 0;
+        if (conv_row_slots(row_smem, Co, &slots) != cudaSuccess) return LBM_ECUDA;
+        const long long cols = (long long)N * (W / kRowM);
+        long long chunks = slots / cols;
+        if (chunks < 1) chunks = 1;
+        if (chunks > H) chunks = H;
+        const int rows = (int)((H + chunks - 1) / chunks);
+        const long long nb = cols * ((H + rows - 1) / rows);
+        conv_row_kernel<<<(unsigned)nb, kRowM, conv_row_launch_smem(row_smem, Co), s>>>(
+            (const bf16*)x, csx, (const bf16*)w, bias, y, csy, N, H, W, Ci, Co, rows, err);
+        return check(cudaGetLastError());
+    }
     const unsigned nb = (unsigned)((M + kTcM - 1) / kTcM);
     conv_tc_kernel<<<nb, kTcM, smem, s>>>((const bf16*)x, csx, (const bf16*)w, bias, y, csy, M, H, W, Ci, Co, err);
     return check(cudaGetLastError());

@@ -87,6 +87,42 @@ def test_conv_kernels_exact_on_integers(env):
     assert np.array_equal(gb.cpu().numpy().astype(np.float64), gb_ref)
 
 
+@pytest.mark.parametrize("N,H,W,Ci,Co", [(1, 2, 128, 16, 32), (2, 5, 128, 128, 32), (1, 7, 256, 32, 128),
+                                         (3, 4, 256, 64, 48), (1, 64, 128, 32, 64), (1, 6, 128, 128, 128)],
+                         ids=["h2", "ci128", "co128", "co48", "rows1", "fallback"])
+def test_conv_row_march_exact_on_integers(env, N, H, W, Ci, Co):
+    """Images whose width is a multiple of 128 go through the row-march
+    convolution (its strip of input rows and all nine taps' weights in
+    shared memory; the last case is too large for that and takes the tap
+    kernel), with chunks of one row up to several per CTA.  On small
+    integers every product and partial sum is exact: the result equals the
+    oracle bit for bit, forward and through the flipped weights (the input
+    gradient)."""
+    torch, L, S = env
+    lib = L.load()
+    rng = np.random.default_rng(N * 1000 + H * 10 + Ci + Co)
+    x = rng.integers(-3, 4, size=(N, H, W, Ci)).astype(np.float64)
+    w = rng.integers(-3, 4, size=(Co, Ci, 3, 3)).astype(np.float64)
+    b = rng.integers(-5, 6, size=Co).astype(np.float64)
+    gy = rng.integers(-2, 3, size=(N, H, W, Co)).astype(np.float64)
+    dev = "cuda"
+    x16 = torch.tensor(x.reshape(-1, Ci), dtype=torch.bfloat16, device=dev)
+    w16 = torch.tensor(np.transpose(w.reshape(Co, Ci, 9), (0, 2, 1)).copy(), dtype=torch.bfloat16, device=dev)
+    bias = torch.tensor(b, dtype=torch.float32, device=dev)
+    y = torch.zeros(N * H * W, Co, dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.lbm_sg_conv3x3(ptr(x16), Ci, ptr(w16), ptr(bias), ptr(y), Co, N, H, W, Ci, Co, s) == 0
+    assert np.array_equal(y.cpu().numpy().astype(np.float64), OS.conv3x3(x, w, b).reshape(-1, Co))
+    wt = torch.zeros(Ci, 9, Co, dtype=torch.bfloat16, device=dev)
+    assert lib.lbm_sg_weight_flip(ptr(w16), ptr(wt), Ci, Co, s) == 0
+    g16 = torch.tensor(gy.reshape(-1, Co), dtype=torch.bfloat16, device=dev)
+    gx = torch.zeros(N * H * W, Ci, dtype=torch.float32, device=dev)
+    assert lib.lbm_sg_conv3x3(ptr(g16), Co, ptr(wt), None, ptr(gx), Ci, N, H, W, Co, Ci, s) == 0
+    gx_ref, _, _ = OS.conv3x3_backward(x, w, gy)
+    assert np.array_equal(gx.cpu().numpy().astype(np.float64), gx_ref.reshape(-1, Ci))
+    assert lib.lbm_sg_status(s) == 0
+
+
 def test_conv_rejects_bad_sizes(env):
     torch, L, S = env
     lib = L.load()
