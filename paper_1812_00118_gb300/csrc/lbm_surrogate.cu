@@ -11,10 +11,11 @@
 //
 // The forward (and input-gradient) convolution runs on the tcgen05 tensor
 // cores with the accumulator in tensor memory (conv_row_kernel for images
-// whose width is a multiple of 128, conv_tc_kernel otherwise); the weight
-// gradient, a GEMM over pixels, uses the warp-level mma.sync m16n8k16 BF16
-// instruction with fragments gathered straight from the channels-last
-// tensors.  Both are implicit GEMMs without an im2col buffer.
+// whose width is a multiple of 128, conv_tc_kernel otherwise); so does the
+// weight gradient, a GEMM over pixels, for widths that are multiples of 64
+// (conv_wgrad_row_kernel), with the warp-level mma.sync m16n8k16 BF16 kernel
+// (fragments gathered straight from the channels-last tensors) for the
+// rest.  All are implicit GEMMs without an im2col buffer.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -395,26 +396,14 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
     int issued = 0;   // rows whose MMAs were issued and committed
     for (int j = 0; j < nrows && ok; ++j) {
         const int r = y0 + j;
-        // (1) row j - 1: its MMAs done (they read strip slot (r - 2) & 3 last),
-        // its accumulator out
-        if (j > 0) {
-            if (!__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(j - 1);
-        }
-        // (2) input row r + 2 into the slot row r - 2 held
-        const bool more = r + 2 <= y1;
-        if (more) {
-            copy_row(r + 2);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        }
-        // (3) rows r - 1 .. r + 1 landed (only the group just issued may be pending)
-        if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // (1) input rows r - 1 .. r + 1 landed (the copy of row r + 1, the
+        // newest group, was issued in the previous iteration)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // (4) the 9 x Ci/16 MMAs of row r into buffer j & 1
+        // (2) the 9 x Ci/16 MMAs of row r into buffer j & 1; they run while the
+        // CTA writes out row j - 1 and copies row r + 2
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)((j & 1) * Co);
@@ -433,6 +422,18 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
                          : "memory");
         }
         issued = j + 1;
+        // (3) row j - 1: its MMAs done (they read strip slot (r - 2) & 3 last),
+        // its accumulator out
+        if (j > 0) {
+            if (!__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(j - 1);
+        }
+        // (4) input row r + 2 into the slot row r - 2 held
+        if (r + 2 <= y1) {
+            copy_row(r + 2);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the last issued row: its MMAs complete after every earlier one (waited
@@ -491,6 +492,204 @@ __global__ void conv_wgrad_kernel(const bf16* __restrict__ x, int csx, const bf1
     out[((long long)(co0 + g) * 9 + tap) * Ci + ci + 1] = acc[1];
     out[((long long)(co0 + g + 8) * 9 + tap) * Ci + ci] = acc[2];
     out[((long long)(co0 + g + 8) * 9 + tap) * Ci + ci + 1] = acc[3];
+}
+
+// ---------------------------------------------------------------- tcgen05 weight gradient, row march
+// gw[co, tap, ci] = sum_p gy[p, co] x[p + d(tap), ci] as GEMMs over pixels
+// on the tensor cores, for images whose width is a multiple of 64: for each
+// tap D_tap (M = co, N = ci) += A (co x pixels) B_tap (ci x pixels)^T with K
+// running over pixels.  A CTA owns a 64-pixel segment of one image row, one
+// tap row dy and a chunk of rows; per row (one stage) it copies the gy row
+// segment and the x row r + dy (66 pixels, the periodic neighbours included)
+// into shared memory in their natural channels-last order (16-byte
+// cp.async, one stage ahead), then transposes them with ldmatrix /
+// stmatrix.trans into the K-major core-matrix layout the MMAs read: A as
+// 128 co rows (rows past Co are never written and their D rows never read),
+// B once per dx in {-1, 0, +1}, the window shifted by dx pixels.  The three
+// taps of the CTA's dy accumulate in tensor memory over the whole march
+// (columns dx Ci + ci, lanes co) and are written out once, as the CTA's
+// partial; the partials are summed in a fixed order (deterministic).
+constexpr int kWgP = 64;              // pixels of a segment: one stage, K = 64 in four MMA steps
+constexpr size_t kWgSmemMax = 220 * 1024;   // below the 227 KB per CTA less the kernel's static shared memory
+
+struct WgLayout {
+    uint32_t gys, xs;                 // natural row strides (padded by 16 bytes against bank conflicts)
+    uint32_t nat_gy, nat;             // bytes of the gy part and of one natural buffer
+    uint32_t opA, opB1, op;           // bytes of A, of one B window, of one operand buffer
+    uint32_t total;
+};
+__host__ __device__ inline WgLayout wg_layout(int Ci, int Co) {
+    WgLayout L;
+    L.gys = (uint32_t)Co * 2 + 16;
+    L.xs = (uint32_t)Ci * 2 + 16;
+    L.nat_gy = kWgP * L.gys;
+    L.nat = L.nat_gy + (kWgP + 2) * L.xs;
+    L.opA = (kWgP / 8) * 128 * 16;
+    L.opB1 = (kWgP / 8) * (uint32_t)Ci * 16;
+    L.op = L.opA + 3 * L.opB1;
+    L.total = 2 * L.nat + 2 * L.op;
+    return L;
+}
+__host__ __device__ inline uint32_t wg_tmem_cols(int Ci) {
+    const int need = 3 * Ci;
+    return need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void stsm_x2_trans(uint32_t addr, uint32_t r0, uint32_t r1) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(addr), "r"(r0), "r"(r1)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ gy, int csg,
+                      float* __restrict__ partial, int N, int H, int W, int Ci, int Co, int rows_per_cta, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = W / kWgP;
+    const int chunks = (H + rows_per_cta - 1) / rows_per_cta;
+    int b = blockIdx.x;
+    const int dyi = b % 3;
+    b /= 3;
+    const int chunk = b % chunks;
+    b /= chunks;
+    const int seg = b % segs, n = b / segs;
+    const int dy = dyi - 1;
+    const int y0 = chunk * rows_per_cta;
+    const int y1 = y0 + rows_per_cta < H ? y0 + rows_per_cta : H;
+    const int x0 = seg * kWgP;
+    const long long pchunk = ((long long)n * segs + seg) * chunks + chunk;
+    const WgLayout Lt = wg_layout(Ci, Co);
+    const uint32_t sb = smem_u32(smem);
+    const uint32_t nat0 = sb, op0 = sb + 2 * Lt.nat;
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    const uint32_t ncols = wg_tmem_cols(Ci);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc_bf16(128, Ci);
+    const int nco8 = Co / 8, nci8 = Ci / 8;
+    const long long img = (long long)n * H * W;
+    // natural copies of stage s (row r = y0 + s): the gy row segment and the
+    // x row r + dy, pixels x0 - 1 .. x0 + 64 (wrapped)
+    auto copy_stage = [&](int st) {
+        const int r = y0 + st;
+        const uint32_t nb = nat0 + (uint32_t)(st & 1) * Lt.nat;
+        const bf16* grow = gy + (img + (long long)r * W) * csg;
+        for (int k = tid; k < kWgP * nco8; k += 128) {
+            const int p = k / nco8, c = k - p * nco8;
+            cp_async16(nb + p * Lt.gys + c * 16, grow + (long long)(x0 + p) * csg + c * 8, 16u);
+        }
+        const int yr = (((r + dy) % H) + H) % H;
+        const bf16* xrow = x + (img + (long long)yr * W) * csx;
+        for (int k = tid; k < (kWgP + 2) * nci8; k += 128) {
+            const int q = k / nci8, c = k - q * nci8;
+            int xx = x0 - 1 + q;
+            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            cp_async16(nb + Lt.nat_gy + q * Lt.xs + c * 16, xrow + (long long)xx * csx + c * 8, 16u);
+        }
+    };
+    // natural buffer st & 1 -> operand buffer st & 1 (K-major: [pixel block][row][8 pixels])
+    auto transpose_stage = [&](int st) {
+        const uint32_t nb = nat0 + (uint32_t)(st & 1) * Lt.nat;
+        const uint32_t ob = op0 + (uint32_t)(st & 1) * Lt.op;
+        const int j = (lane >> 3) & 1, i = lane & 7;   // matrix and row a lane addresses (lanes 0-15 count)
+        const int na = (kWgP / 8) * (nco8 / 2);
+        for (int o = warp; o < na; o += 4) {
+            const int pb = o % (kWgP / 8), cp = o / (kWgP / 8), c = 2 * cp + j;
+            uint32_t r0, r1;
+            ldsm_x2(nb + (uint32_t)(8 * pb + i) * Lt.gys + c * 16, r0, r1);
+            stsm_x2_trans(ob + (uint32_t)pb * (128 * 16) + (uint32_t)(8 * c + i) * 16, r0, r1);
+        }
+        const int nbx = 3 * (kWgP / 8) * (nci8 / 2);
+        for (int o = warp; o < nbx; o += 4) {
+            const int w3 = o % 3, rest = o / 3, pb = rest % (kWgP / 8), cp = rest / (kWgP / 8), c = 2 * cp + j;
+            const int q = 8 * pb + i + w3;   // staging pixel of window pixel 8 pb + i shifted by dx = w3 - 1
+            uint32_t r0, r1;
+            ldsm_x2(nb + Lt.nat_gy + (uint32_t)q * Lt.xs + c * 16, r0, r1);
+            stsm_x2_trans(ob + Lt.opA + (uint32_t)w3 * Lt.opB1 + (uint32_t)pb * Ci * 16 + (uint32_t)(8 * c + i) * 16, r0,
+                          r1);
+        }
+    };
+    auto wait_stage = [&](int st) { return mbar_wait_bounded(bar0 + 8 * (st & 1), (uint32_t)(st >> 1) & 1u, kTcPolls); };
+    const int S = y1 - y0;
+    bool ok = true;
+    int issued = 0;
+    copy_stage(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int st = 0; st < S; ++st) {
+        const bool more = st + 1 < S;
+        if (more) {   // natural buffer (st + 1) & 1 was last read by the transposes of stage st - 1
+            copy_stage(st + 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // operand buffer st & 1 was last read by the MMAs of stage st - 2
+        if (st >= 2 && !__syncthreads_and(wait_stage(st - 2))) { ok = false; break; }
+        transpose_stage(st);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ob = op0 + (uint32_t)(st & 1) * Lt.op;
+            for (int w3 = 0; w3 < 3; ++w3) {
+                for (int k = 0; k < kWgP / 16; ++k) {
+                    const uint64_t ad = tc_smem_desc(ob + 2 * k * (128 * 16), 128 * 16, 128);
+                    const uint64_t bd = tc_smem_desc(ob + Lt.opA + w3 * Lt.opB1 + 2 * k * (Ci * 16), Ci * 16, 128);
+                    tc_mma(tmem + (uint32_t)(w3 * Ci), ad, bd, idesc, (st > 0 || k > 0) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8 * (st & 1))
+                         : "memory");
+        }
+        issued = st + 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (issued > 0) {
+        const bool done = wait_stage(issued - 1);
+        ok = __syncthreads_and(ok && done) != 0 && issued == S;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int co = 32 * warp + lane;
+        for (int w3 = 0; w3 < 3; ++w3) {
+            const int tap = (dy + 1) * 3 + w3;
+            float* out = partial + ((pchunk * Co + co) * 9 + tap) * (long long)Ci;
+            for (int c0 = 0; c0 < Ci; c0 += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w3 * Ci + c0), v);
+                if (co < Co) {
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4)
+                        *reinterpret_cast<float4*>(out + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (!ok && tid == 0) atomicExch(err, 1);
 }
 
 // gw[k] = sum over chunks of partial[chunk, k], in chunk order
@@ -893,6 +1092,9 @@ cudaError_t conv_row_slots(size_t need, int Co, int* out) {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         e = cudaFuncSetAttribute(conv_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_row_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
@@ -901,6 +1103,52 @@ cudaError_t conv_row_slots(size_t need, int Co, int* out) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_row_kernel, kRowM, conv_row_launch_smem(need, Co));
     if (e != cudaSuccess) return e;
     *out = sms * (occ > 0 ? occ : 1);
+    return cudaSuccess;
+}
+
+// Dynamic shared memory of a weight-gradient row-march launch, raised like
+// conv_row_launch_smem so that the CTAs an SM holds fit its tensor memory.
+size_t wg_launch_smem(size_t need, int Ci) {
+    const int per_sm = 512 / (int)wg_tmem_cols(Ci);
+    const size_t floor_bytes = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1;
+    return need > floor_bytes ? need : floor_bytes;
+}
+
+// Row chunks of the weight-gradient row march on the current device: rows
+// per CTA and chunks per column (0 rows: the march does not apply to these
+// sizes).  One wave: 3 taps rows x N x W / 64 segments x chunks CTAs at most
+// the resident CTAs.
+cudaError_t wgrad_row_plan(int N, int H, int W, int Ci, int Co, int* rows, int* chunks) {
+    *rows = 0;
+    *chunks = 0;
+    if (W % kWgP != 0 || Ci > 128 || Co > 128 || Ci % 16 || Co % 16 || H < 1) return cudaSuccess;
+    const WgLayout Lt = wg_layout(Ci, Co);
+    if (Lt.total > kWgSmemMax) return cudaSuccess;
+    static bool attr_set[64] = {};
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(conv_wgrad_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_wgrad_row_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_wgrad_row_kernel, 128,
+                                                          wg_launch_smem(Lt.total, Ci));
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)sms * (occ > 0 ? occ : 1);
+    const long long cols = 3LL * N * (W / kWgP);
+    long long c = slots / cols;
+    if (c < 1) c = 1;
+    if (c > H) c = H;
+    const int r = (int)((H + c - 1) / c);
+    *rows = r;
+    *chunks = (H + r - 1) / r;
     return cudaSuccess;
 }
 
@@ -938,7 +1186,7 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
         int slots = 0;
         if (conv_row_slots(row_smem, Co, &slots) != cudaSuccess) return LBM_ECUDA;
         const long long cols = (long long)N * (W / kRowM);
-        long long chunks = slots / cols;
+        long long chunks = slots / cols;   // one wave
         if (chunks < 1) chunks = 1;
         if (chunks > H) chunks = H;
         const int rows = (int)((H + chunks - 1) / chunks);
@@ -970,7 +1218,17 @@ int lbm_sg_status(void* stream) {
 
 long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co) {
     const long long M = (long long)N * H * W;
-    return ((M + kChunk - 1) / kChunk) * (long long)Co * 9 * Ci;
+    long long need = ((M + kChunk - 1) / kChunk) * (long long)Co * 9 * Ci;
+    int rows = 0, chunks = 0;
+    if (wgrad_row_plan(N, H, W, Ci, Co, &rows, &chunks) == cudaSuccess) {
+        if (rows > 0) {
+            const long long row_need = (long long)N * (W / kWgP) * chunks * Co * 9 * Ci;
+            if (row_need > need) need = row_need;
+        }
+    } else {
+        cudaGetLastError();   // the plan's failure is reported by lbm_sg_conv3x3_wgrad, not left pending
+    }
+    return need;
 }
 
 int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float* gw, float* scratch,
@@ -980,6 +1238,23 @@ int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float*
         return LBM_EINVAL;
     const long long need = lbm_sg_wgrad_scratch_floats(N, H, W, Ci, Co);
     if (scratch_floats < need) return LBM_EINVAL;
+    // rows of 64-pixel segments with 16-byte aligned channel rows: the
+    // tcgen05 row march
+    int rows = 0, rchunks = 0;
+    if (wgrad_row_plan(N, H, W, Ci, Co, &rows, &rchunks) != cudaSuccess) return LBM_ECUDA;
+    if (rows > 0 && csx % 8 == 0 && csg % 8 == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)gy & 15) == 0 &&
+        ((uintptr_t)scratch & 15) == 0) {
+        int* err = nullptr;
+        if (cudaGetSymbolAddress((void**)&err, g_sg_err) != cudaSuccess) return LBM_ECUDA;
+        cudaStream_t s = (cudaStream_t)stream;
+        const long long pchunks = (long long)N * (W / kWgP) * rchunks;
+        const WgLayout Lt = wg_layout(Ci, Co);
+        conv_wgrad_row_kernel<<<(unsigned)(3 * pchunks), 128, wg_launch_smem(Lt.total, Ci), s>>>(
+            (const bf16*)x, csx, (const bf16*)gy, csg, scratch, N, H, W, Ci, Co, rows, err);
+        const long long K = (long long)Co * 9 * Ci;
+        sum_chunks_kernel<<<blocks(K), kThreads, 0, s>>>(scratch, pchunks, K, gw);
+        return check(cudaGetLastError());
+    }
     const long long nchunks = (M + kChunk - 1) / kChunk;
     const long long warps = nchunks * 9LL * (Co / 16) * (Ci / 8);
     cudaStream_t s = (cudaStream_t)stream;

@@ -88,16 +88,19 @@ def test_conv_kernels_exact_on_integers(env):
 
 
 @pytest.mark.parametrize("N,H,W,Ci,Co", [(1, 2, 128, 16, 32), (2, 5, 128, 128, 32), (1, 7, 256, 32, 128),
-                                         (3, 4, 256, 64, 48), (1, 64, 128, 32, 64), (1, 6, 128, 128, 128)],
-                         ids=["h2", "ci128", "co128", "co48", "rows1", "fallback"])
+                                         (3, 4, 256, 64, 48), (1, 64, 128, 32, 64), (1, 6, 128, 128, 128),
+                                         (2, 3, 64, 32, 16)],
+                         ids=["h2", "ci128", "co128", "co48", "rows1", "fallback", "w64"])
 def test_conv_row_march_exact_on_integers(env, N, H, W, Ci, Co):
     """Images whose width is a multiple of 128 go through the row-march
     convolution (its strip of input rows and all nine taps' weights in
-    shared memory; the last case is too large for that and takes the tap
-    kernel), with chunks of one row up to several per CTA.  On small
-    integers every product and partial sum is exact: the result equals the
-    oracle bit for bit, forward and through the flipped weights (the input
-    gradient)."""
+    shared memory; the 128 x 128-channel case is too large for that and
+    takes the tap kernel, as does the 64-wide image), with chunks of one row
+    up to several per CTA; widths that are multiples of 64 take the row-march
+    weight gradient (tcgen05 GEMMs over pixels, operands transposed in shared
+    memory).  On small integers every product and partial sum is exact: the
+    results equal the oracle bit for bit, forward, through the flipped
+    weights (the input gradient) and for the weight gradient."""
     torch, L, S = env
     lib = L.load()
     rng = np.random.default_rng(N * 1000 + H * 10 + Ci + Co)
@@ -118,8 +121,14 @@ def test_conv_row_march_exact_on_integers(env, N, H, W, Ci, Co):
     g16 = torch.tensor(gy.reshape(-1, Co), dtype=torch.bfloat16, device=dev)
     gx = torch.zeros(N * H * W, Ci, dtype=torch.float32, device=dev)
     assert lib.lbm_sg_conv3x3(ptr(g16), Co, ptr(wt), None, ptr(gx), Ci, N, H, W, Co, Ci, s) == 0
-    gx_ref, _, _ = OS.conv3x3_backward(x, w, gy)
+    gx_ref, gw_ref, _ = OS.conv3x3_backward(x, w, gy)
     assert np.array_equal(gx.cpu().numpy().astype(np.float64), gx_ref.reshape(-1, Ci))
+    gw = torch.zeros(Co, 9, Ci, dtype=torch.float32, device=dev)
+    nscr = lib.lbm_sg_wgrad_scratch_floats(N, H, W, Ci, Co)
+    scr = torch.full((nscr,), float("nan"), dtype=torch.float32, device=dev)   # every partial must be written
+    assert lib.lbm_sg_conv3x3_wgrad(ptr(x16), Ci, ptr(g16), Co, ptr(gw), ptr(scr), nscr, N, H, W, Ci, Co, s) == 0
+    got = np.transpose(gw.cpu().numpy().astype(np.float64), (0, 2, 1)).reshape(Co, Ci, 3, 3)
+    assert np.array_equal(got, gw_ref)
     assert lib.lbm_sg_status(s) == 0
 
 
