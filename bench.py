@@ -880,8 +880,8 @@ def run_ttt(args):
                       "data_ms": e[0].elapsed_time(e[1]), "train_ms": e[1].elapsed_time(e[2]),
                       "loss_first_last": [hist[0][1], hist[-1][1]], "identity_loss": identity,
                       "sg_status": sg_status, "flops_per_image_forward": sg1.flops_per_image(backward=False),
-                      "kernels": "lbm_sg_* tcgen05 implicit-GEMM convolutions (TMEM accumulator), mma.sync weight "
-                                 "gradient, FP32 accumulation"},
+                      "kernels": "lbm_sg_* tcgen05 implicit-GEMM convolutions and weight gradients (TMEM "
+                                 "accumulators; mma.sync weight gradient on the 32-wide level), FP32 accumulation"},
     }
     print(json.dumps(line), flush=True)
 

@@ -58,13 +58,14 @@ long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co);
 
 /* gw (float [Co][9][Ci]) = gradient of sum_p <gy[p], y[p]> with respect to w
  * for y = lbm_sg_conv3x3(x, w): gw[co, tap, ci] = sum_p gy[p, co] x[p + d(tap), ci].
- * x, gy bf16.  When W is a multiple of 64, Ci and Co are at most 128, the
- * channel strides are multiples of 8 and x, gy and scratch start on 16-byte
- * boundaries, the sums are GEMMs over pixels on the tcgen05 tensor cores
- * (each CTA marches a 64-pixel row segment down a chunk of rows for one tap
- * row, its operands transposed into shared memory, its three taps
- * accumulated in tensor memory); otherwise warp-level mma.sync over chunks
- * of 1024 pixels.  Deterministic either way: per-CTA (or per-chunk) partials
+ * x, gy bf16.  When W is a multiple of 32, Co is at most 128, Ci is at
+ * most 128 or a multiple of 128, the channel strides are multiples of 8 and
+ * x, gy and scratch start on 16-byte boundaries, the sums are GEMMs over
+ * pixels on the tcgen05 tensor cores (each CTA marches a 64- or 32-pixel row
+ * segment down a chunk of rows for one tap row and a block of at most 128
+ * input channels, its operands transposed into shared memory, its three
+ * taps accumulated in tensor memory); otherwise warp-level mma.sync over
+ * chunks of 1024 pixels.  Deterministic either way: per-CTA (or per-chunk) partials
  * summed in a fixed order.  A bounded wait that gives up is reported by
  * lbm_sg_status. */
 int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float* gw, float* scratch,

@@ -15,6 +15,8 @@ Modules
 lattice      D2Q9 / D3Q19 velocity sets and weights, lattice temperature T.
 pflbm        the per-time-step update (Eqs. 1-14) on whole fields, FP64.
 diagnostics  Laplace-law measurement and global sums used by validation.
+surrogate    the learned warm start's convolutional network, forward and
+             backward in FP64 (the reference of the tensor-core kernels).
 
 Every function cites the section / equation it follows.  Readings of
 places where the paper is silent or garbled are stated at the function

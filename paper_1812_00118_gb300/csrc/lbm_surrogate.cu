@@ -403,7 +403,7 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         // (2) the 9 x Ci/16 MMAs of row r into buffer j & 1; they run while the
-        // CTA writes out row j - 1 and copies row r + 2
+        // CTA copies row r + 2 and writes out row j - 1
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)((j & 1) * Co);
@@ -422,17 +422,17 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
                          : "memory");
         }
         issued = j + 1;
-        // (3) row j - 1: its MMAs done (they read strip slot (r - 2) & 3 last),
-        // its accumulator out
-        if (j > 0) {
-            if (!__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(j - 1);
-        }
-        // (4) input row r + 2 into the slot row r - 2 held
+        // (3) row j - 1's MMAs done: they read strip slot (r - 2) & 3 last, so
+        // input row r + 2 can go there, its copy in flight while (4) row j - 1's
+        // accumulator is written out
+        if (j > 0 && !__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
         if (r + 2 <= y1) {
             copy_row(r + 2);
             asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        if (j > 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(j - 1);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -496,11 +496,12 @@ __global__ void conv_wgrad_kernel(const bf16* __restrict__ x, int csx, const bf1
 
 // ---------------------------------------------------------------- tcgen05 weight gradient, row march
 // gw[co, tap, ci] = sum_p gy[p, co] x[p + d(tap), ci] as GEMMs over pixels
-// on the tensor cores, for images whose width is a multiple of 64: for each
+// on the tensor cores, for images whose width is a multiple of 32: for each
 // tap D_tap (M = co, N = ci) += A (co x pixels) B_tap (ci x pixels)^T with K
-// running over pixels.  A CTA owns a 64-pixel segment of one image row, one
-// tap row dy and a chunk of rows; per row (one stage) it copies the gy row
-// segment and the x row r + dy (66 pixels, the periodic neighbours included)
+// running over pixels.  A CTA owns a segment of P = 64 (or 32) pixels of one
+// image row, one tap row dy, a block of at most 128 input channels and a
+// chunk of rows; per row (one stage) it copies the gy row segment and the x
+// row r + dy (P + 2 pixels, the periodic neighbours included)
 // into shared memory in their natural channels-last order (16-byte
 // cp.async, one stage ahead), then transposes them with ldmatrix /
 // stmatrix.trans into the K-major core-matrix layout the MMAs read: A as
@@ -509,7 +510,7 @@ __global__ void conv_wgrad_kernel(const bf16* __restrict__ x, int csx, const bf1
 // taps of the CTA's dy accumulate in tensor memory over the whole march
 // (columns dx Ci + ci, lanes co) and are written out once, as the CTA's
 // partial; the partials are summed in a fixed order (deterministic).
-constexpr int kWgP = 64;              // pixels of a segment: one stage, K = 64 in four MMA steps
+constexpr int kWgCn = 128;            // input channels of one CTA at most (3 Cn tensor-memory columns)
 constexpr size_t kWgSmemMax = 220 * 1024;   // below the 227 KB per CTA less the kernel's static shared memory
 
 struct WgLayout {
@@ -518,14 +519,15 @@ struct WgLayout {
     uint32_t opA, opB1, op;           // bytes of A, of one B window, of one operand buffer
     uint32_t total;
 };
-__host__ __device__ inline WgLayout wg_layout(int Ci, int Co) {
+// P pixels of a segment, Cn input channels and Co output channels of a CTA
+__host__ __device__ inline WgLayout wg_layout(int P, int Cn, int Co) {
     WgLayout L;
     L.gys = (uint32_t)Co * 2 + 16;
-    L.xs = (uint32_t)Ci * 2 + 16;
-    L.nat_gy = kWgP * L.gys;
-    L.nat = L.nat_gy + (kWgP + 2) * L.xs;
-    L.opA = (kWgP / 8) * 128 * 16;
-    L.opB1 = (kWgP / 8) * (uint32_t)Ci * 16;
+    L.xs = (uint32_t)Cn * 2 + 16;
+    L.nat_gy = (uint32_t)P * L.gys;
+    L.nat = L.nat_gy + (uint32_t)(P + 2) * L.xs;
+    L.opA = (uint32_t)(P / 8) * 128 * 16;
+    L.opB1 = (uint32_t)(P / 8) * (uint32_t)Cn * 16;
     L.op = L.opA + 3 * L.opB1;
     L.total = 2 * L.nat + 2 * L.op;
     return L;
@@ -545,29 +547,33 @@ __device__ __forceinline__ void stsm_x2_trans(uint32_t addr, uint32_t r0, uint32
 
 __global__ void __launch_bounds__(128, 1)
 conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ gy, int csg,
-                      float* __restrict__ partial, int N, int H, int W, int Ci, int Co, int rows_per_cta, int* err) {
+                      float* __restrict__ partial, int N, int H, int W, int Ci, int Co, int P, int Cn,
+                      int rows_per_cta, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int segs = W / kWgP;
+    const int segs = W / P;
+    const int nsplit = Ci / Cn;
     const int chunks = (H + rows_per_cta - 1) / rows_per_cta;
     int b = blockIdx.x;
     const int dyi = b % 3;
     b /= 3;
+    const int ci0 = (b % nsplit) * Cn;
+    b /= nsplit;
     const int chunk = b % chunks;
     b /= chunks;
     const int seg = b % segs, n = b / segs;
     const int dy = dyi - 1;
     const int y0 = chunk * rows_per_cta;
     const int y1 = y0 + rows_per_cta < H ? y0 + rows_per_cta : H;
-    const int x0 = seg * kWgP;
+    const int x0 = seg * P;
     const long long pchunk = ((long long)n * segs + seg) * chunks + chunk;
-    const WgLayout Lt = wg_layout(Ci, Co);
+    const WgLayout Lt = wg_layout(P, Cn, Co);
     const uint32_t sb = smem_u32(smem);
     const uint32_t nat0 = sb, op0 = sb + 2 * Lt.nat;
     const uint32_t bar0 = smem_u32(&bars[0]);
-    const uint32_t ncols = wg_tmem_cols(Ci);
+    const uint32_t ncols = wg_tmem_cols(Cn);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(ncols)
@@ -582,22 +588,23 @@ conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restric
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = tc_idesc_bf16(128, Ci);
-    const int nco8 = Co / 8, nci8 = Ci / 8;
+    const uint32_t idesc = tc_idesc_bf16(128, Cn);
+    const int nco8 = Co / 8, nci8 = Cn / 8;
     const long long img = (long long)n * H * W;
-    // natural copies of stage s (row r = y0 + s): the gy row segment and the
-    // x row r + dy, pixels x0 - 1 .. x0 + 64 (wrapped)
+    // natural copies of stage s (row r = y0 + s): the gy row segment and
+    // channels ci0 .. ci0 + Cn - 1 of the x row r + dy, pixels x0 - 1 .. x0 + P
+    // (wrapped)
     auto copy_stage = [&](int st) {
         const int r = y0 + st;
         const uint32_t nb = nat0 + (uint32_t)(st & 1) * Lt.nat;
         const bf16* grow = gy + (img + (long long)r * W) * csg;
-        for (int k = tid; k < kWgP * nco8; k += 128) {
+        for (int k = tid; k < P * nco8; k += 128) {
             const int p = k / nco8, c = k - p * nco8;
             cp_async16(nb + p * Lt.gys + c * 16, grow + (long long)(x0 + p) * csg + c * 8, 16u);
         }
         const int yr = (((r + dy) % H) + H) % H;
-        const bf16* xrow = x + (img + (long long)yr * W) * csx;
-        for (int k = tid; k < (kWgP + 2) * nci8; k += 128) {
+        const bf16* xrow = x + (img + (long long)yr * W) * csx + ci0;
+        for (int k = tid; k < (P + 2) * nci8; k += 128) {
             const int q = k / nci8, c = k - q * nci8;
             int xx = x0 - 1 + q;
             xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
@@ -609,20 +616,21 @@ conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restric
         const uint32_t nb = nat0 + (uint32_t)(st & 1) * Lt.nat;
         const uint32_t ob = op0 + (uint32_t)(st & 1) * Lt.op;
         const int j = (lane >> 3) & 1, i = lane & 7;   // matrix and row a lane addresses (lanes 0-15 count)
-        const int na = (kWgP / 8) * (nco8 / 2);
+        const int npb = P / 8;
+        const int na = npb * (nco8 / 2);
         for (int o = warp; o < na; o += 4) {
-            const int pb = o % (kWgP / 8), cp = o / (kWgP / 8), c = 2 * cp + j;
+            const int pb = o % npb, cp = o / npb, c = 2 * cp + j;
             uint32_t r0, r1;
             ldsm_x2(nb + (uint32_t)(8 * pb + i) * Lt.gys + c * 16, r0, r1);
             stsm_x2_trans(ob + (uint32_t)pb * (128 * 16) + (uint32_t)(8 * c + i) * 16, r0, r1);
         }
-        const int nbx = 3 * (kWgP / 8) * (nci8 / 2);
+        const int nbx = 3 * npb * (nci8 / 2);
         for (int o = warp; o < nbx; o += 4) {
-            const int w3 = o % 3, rest = o / 3, pb = rest % (kWgP / 8), cp = rest / (kWgP / 8), c = 2 * cp + j;
+            const int w3 = o % 3, rest = o / 3, pb = rest % npb, cp = rest / npb, c = 2 * cp + j;
             const int q = 8 * pb + i + w3;   // staging pixel of window pixel 8 pb + i shifted by dx = w3 - 1
             uint32_t r0, r1;
             ldsm_x2(nb + Lt.nat_gy + (uint32_t)q * Lt.xs + c * 16, r0, r1);
-            stsm_x2_trans(ob + Lt.opA + (uint32_t)w3 * Lt.opB1 + (uint32_t)pb * Ci * 16 + (uint32_t)(8 * c + i) * 16, r0,
+            stsm_x2_trans(ob + Lt.opA + (uint32_t)w3 * Lt.opB1 + (uint32_t)pb * Cn * 16 + (uint32_t)(8 * c + i) * 16, r0,
                           r1);
         }
     };
@@ -651,10 +659,10 @@ conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restric
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t ob = op0 + (uint32_t)(st & 1) * Lt.op;
             for (int w3 = 0; w3 < 3; ++w3) {
-                for (int k = 0; k < kWgP / 16; ++k) {
+                for (int k = 0; k < P / 16; ++k) {
                     const uint64_t ad = tc_smem_desc(ob + 2 * k * (128 * 16), 128 * 16, 128);
-                    const uint64_t bd = tc_smem_desc(ob + Lt.opA + w3 * Lt.opB1 + 2 * k * (Ci * 16), Ci * 16, 128);
-                    tc_mma(tmem + (uint32_t)(w3 * Ci), ad, bd, idesc, (st > 0 || k > 0) ? 1u : 0u);
+                    const uint64_t bd = tc_smem_desc(ob + Lt.opA + w3 * Lt.opB1 + 2 * k * (Cn * 16), Cn * 16, 128);
+                    tc_mma(tmem + (uint32_t)(w3 * Cn), ad, bd, idesc, (st > 0 || k > 0) ? 1u : 0u);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -673,10 +681,10 @@ conv_wgrad_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restric
         const int co = 32 * warp + lane;
         for (int w3 = 0; w3 < 3; ++w3) {
             const int tap = (dy + 1) * 3 + w3;
-            float* out = partial + ((pchunk * Co + co) * 9 + tap) * (long long)Ci;
-            for (int c0 = 0; c0 < Ci; c0 += 16) {
+            float* out = partial + ((pchunk * Co + co) * 9 + tap) * (long long)Ci + ci0;
+            for (int c0 = 0; c0 < Cn; c0 += 16) {
                 float v[16];
-                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w3 * Ci + c0), v);
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w3 * Cn + c0), v);
                 if (co < Co) {
 #pragma unroll
                     for (int k = 0; k < 16; k += 4)
@@ -1114,15 +1122,21 @@ size_t wg_launch_smem(size_t need, int Ci) {
     return need > floor_bytes ? need : floor_bytes;
 }
 
+// Segment width of the weight-gradient row march (0: the width allows none)
+// and the input channels of one CTA.
+inline int wg_segment(int W) { return W % 64 == 0 ? 64 : (W % 32 == 0 ? 32 : 0); }
+inline int wg_block(int Ci) { return Ci <= kWgCn ? Ci : kWgCn; }
+
 // Row chunks of the weight-gradient row march on the current device: rows
 // per CTA and chunks per column (0 rows: the march does not apply to these
-// sizes).  One wave: 3 taps rows x N x W / 64 segments x chunks CTAs at most
-// the resident CTAs.
+// sizes).  One wave: 3 tap rows x channel blocks x N x W / P segments x
+// chunks CTAs at most the resident CTAs.
 cudaError_t wgrad_row_plan(int N, int H, int W, int Ci, int Co, int* rows, int* chunks) {
     *rows = 0;
     *chunks = 0;
-    if (W % kWgP != 0 || Ci > 128 || Co > 128 || Ci % 16 || Co % 16 || H < 1) return cudaSuccess;
-    const WgLayout Lt = wg_layout(Ci, Co);
+    const int P = wg_segment(W), Cn = wg_block(Ci);
+    if (P == 0 || Ci % Cn || Co > 128 || Ci % 16 || Co % 16 || H < 1) return cudaSuccess;
+    const WgLayout Lt = wg_layout(P, Cn, Co);
     if (Lt.total > kWgSmemMax) return cudaSuccess;
     static bool attr_set[64] = {};
     int dev = 0, sms = 0, occ = 0;
@@ -1139,10 +1153,10 @@ cudaError_t wgrad_row_plan(int N, int H, int W, int Ci, int Co, int* rows, int* 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_wgrad_row_kernel, 128,
-                                                          wg_launch_smem(Lt.total, Ci));
+                                                          wg_launch_smem(Lt.total, Cn));
     if (e != cudaSuccess) return e;
     const long long slots = (long long)sms * (occ > 0 ? occ : 1);
-    const long long cols = 3LL * N * (W / kWgP);
+    const long long cols = 3LL * (Ci / Cn) * N * (W / P);
     long long c = slots / cols;
     if (c < 1) c = 1;
     if (c > H) c = H;
@@ -1185,8 +1199,15 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     if (W % kRowM == 0 && H >= 2 && row_smem <= kRowSmemMax) {
         int slots = 0;
         if (conv_row_slots(row_smem, Co, &slots) != cudaSuccess) return LBM_ECUDA;
+        int dev = 0, sms = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return LBM_ECUDA;
         const long long cols = (long long)N * (W / kRowM);
-        long long chunks = slots / cols;   // one wave
+        // one CTA per SM: longer marches (the weights and the two halo rows of
+        // a chunk are loaded once per CTA) ran faster than two CTAs per SM on
+        // half the rows (d1 at 8 x 256^2: 0.127 against 0.135 ms)
+        long long chunks = (slots < sms ? slots : sms) / cols;
         if (chunks < 1) chunks = 1;
         if (chunks > H) chunks = H;
         const int rows = (int)((H + chunks - 1) / chunks);
@@ -1222,7 +1243,7 @@ long long lbm_sg_wgrad_scratch_floats(int N, int H, int W, int Ci, int Co) {
     int rows = 0, chunks = 0;
     if (wgrad_row_plan(N, H, W, Ci, Co, &rows, &chunks) == cudaSuccess) {
         if (rows > 0) {
-            const long long row_need = (long long)N * (W / kWgP) * chunks * Co * 9 * Ci;
+            const long long row_need = (long long)N * (W / wg_segment(W)) * chunks * Co * 9 * Ci;
             if (row_need > need) need = row_need;
         }
     } else {
@@ -1247,10 +1268,11 @@ int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float*
         int* err = nullptr;
         if (cudaGetSymbolAddress((void**)&err, g_sg_err) != cudaSuccess) return LBM_ECUDA;
         cudaStream_t s = (cudaStream_t)stream;
-        const long long pchunks = (long long)N * (W / kWgP) * rchunks;
-        const WgLayout Lt = wg_layout(Ci, Co);
-        conv_wgrad_row_kernel<<<(unsigned)(3 * pchunks), 128, wg_launch_smem(Lt.total, Ci), s>>>(
-            (const bf16*)x, csx, (const bf16*)gy, csg, scratch, N, H, W, Ci, Co, rows, err);
+        const int P = wg_segment(W), Cn = wg_block(Ci);
+        const long long pchunks = (long long)N * (W / P) * rchunks;
+        const WgLayout Lt = wg_layout(P, Cn, Co);
+        conv_wgrad_row_kernel<<<(unsigned)(3 * (Ci / Cn) * pchunks), 128, wg_launch_smem(Lt.total, Cn), s>>>(
+            (const bf16*)x, csx, (const bf16*)gy, csg, scratch, N, H, W, Ci, Co, P, Cn, rows, err);
         const long long K = (long long)Co * 9 * Ci;
         sum_chunks_kernel<<<blocks(K), kThreads, 0, s>>>(scratch, pchunks, K, gw);
         return check(cudaGetLastError());

@@ -89,16 +89,17 @@ def test_conv_kernels_exact_on_integers(env):
 
 @pytest.mark.parametrize("N,H,W,Ci,Co", [(1, 2, 128, 16, 32), (2, 5, 128, 128, 32), (1, 7, 256, 32, 128),
                                          (3, 4, 256, 64, 48), (1, 64, 128, 32, 64), (1, 6, 128, 128, 128),
-                                         (2, 3, 64, 32, 16)],
-                         ids=["h2", "ci128", "co128", "co48", "rows1", "fallback", "w64"])
+                                         (2, 3, 64, 32, 16), (2, 3, 64, 256, 64), (1, 4, 32, 128, 128)],
+                         ids=["h2", "ci128", "co128", "co48", "rows1", "fallback", "w64", "ci256", "w32"])
 def test_conv_row_march_exact_on_integers(env, N, H, W, Ci, Co):
     """Images whose width is a multiple of 128 go through the row-march
     convolution (its strip of input rows and all nine taps' weights in
     shared memory; the 128 x 128-channel case is too large for that and
-    takes the tap kernel, as does the 64-wide image), with chunks of one row
-    up to several per CTA; widths that are multiples of 64 take the row-march
-    weight gradient (tcgen05 GEMMs over pixels, operands transposed in shared
-    memory).  On small integers every product and partial sum is exact: the
+    takes the tap kernel, as do the 64- and 32-wide images), with chunks of
+    one row up to several per CTA; widths that are multiples of 32 take the
+    row-march weight gradient (tcgen05 GEMMs over pixels, operands transposed
+    in shared memory; 256 input channels in two blocks of 128).  On small
+    integers every product and partial sum is exact: the
     results equal the oracle bit for bit, forward, through the flipped
     weights (the input gradient) and for the weight gradient."""
     torch, L, S = env
@@ -120,7 +121,11 @@ def test_conv_row_march_exact_on_integers(env, N, H, W, Ci, Co):
     assert lib.lbm_sg_weight_flip(ptr(w16), ptr(wt), Ci, Co, s) == 0
     g16 = torch.tensor(gy.reshape(-1, Co), dtype=torch.bfloat16, device=dev)
     gx = torch.zeros(N * H * W, Ci, dtype=torch.float32, device=dev)
-    assert lib.lbm_sg_conv3x3(ptr(g16), Co, ptr(wt), None, ptr(gx), Ci, N, H, W, Co, Ci, s) == 0
+    for c0 in range(0, Ci, 128):   # at most 128 output channels per call, as the network slices them
+        nco = min(128, Ci - c0)
+        wt_c = ctypes.c_void_p(wt.data_ptr() + c0 * 9 * Co * 2)
+        gx_c = ctypes.c_void_p(gx.data_ptr() + c0 * 4)
+        assert lib.lbm_sg_conv3x3(ptr(g16), Co, wt_c, None, gx_c, Ci, N, H, W, Co, nco, s) == 0
     gx_ref, gw_ref, _ = OS.conv3x3_backward(x, w, gy)
     assert np.array_equal(gx.cpu().numpy().astype(np.float64), gx_ref.reshape(-1, Ci))
     gw = torch.zeros(Co, 9, Ci, dtype=torch.float32, device=dev)
