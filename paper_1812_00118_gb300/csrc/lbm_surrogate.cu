@@ -396,14 +396,26 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
     int issued = 0;   // rows whose MMAs were issued and committed
     for (int j = 0; j < nrows && ok; ++j) {
         const int r = y0 + j;
-        // (1) input rows r - 1 .. r + 1 landed (the copy of row r + 1, the
-        // newest group, was issued in the previous iteration)
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // (1) row j - 1: its MMAs done (they read strip slot (r - 2) & 3 last),
+        // its accumulator out
+        if (j > 0) {
+            if (!__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(j - 1);
+        }
+        // (2) input row r + 2 into the slot row r - 2 held
+        const bool more = r + 2 <= y1;
+        if (more) {
+            copy_row(r + 2);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        // (3) rows r - 1 .. r + 1 landed (only the group just issued may be pending)
+        if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // (2) the 9 x Ci/16 MMAs of row r into buffer j & 1; they run while the
-        // CTA copies row r + 2 and writes out row j - 1
+        // (4) the 9 x Ci/16 MMAs of row r into buffer j & 1
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)((j & 1) * Co);
@@ -422,18 +434,6 @@ conv_row_kernel(const bf16* __restrict__ x, int csx, const bf16* __restrict__ w,
                          : "memory");
         }
         issued = j + 1;
-        // (3) row j - 1's MMAs done: they read strip slot (r - 2) & 3 last, so
-        // input row r + 2 can go there, its copy in flight while (4) row j - 1's
-        // accumulator is written out
-        if (j > 0 && !__syncthreads_and(wait_row(j - 1))) { ok = false; break; }
-        if (r + 2 <= y1) {
-            copy_row(r + 2);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        }
-        if (j > 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(j - 1);
-        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the last issued row: its MMAs complete after every earlier one (waited
@@ -1151,10 +1151,13 @@ cudaError_t wgrad_row_plan(int N, int H, int W, int Ci, int Co, int* rows, int* 
         attr_set[dev] = true;
     }
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_wgrad_row_kernel, 128,
-                                                          wg_launch_smem(Lt.total, Cn));
     if (e != cudaSuccess) return e;
+    // CTAs an SM holds: its 228 KB of shared memory (1 KB reserved per CTA)
+    // and its 512 tensor-memory columns
+    const size_t per_cta = wg_launch_smem(Lt.total, Cn) + 1024;
+    occ = (int)((size_t)(228 * 1024) / per_cta);
+    const int by_tmem = 512 / (int)wg_tmem_cols(Cn);
+    if (occ > by_tmem) occ = by_tmem;
     const long long slots = (long long)sms * (occ > 0 ? occ : 1);
     const long long cols = 3LL * (Ci / Cn) * N * (W / P);
     long long c = slots / cols;
