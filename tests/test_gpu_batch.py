@@ -49,8 +49,8 @@ def fields(shape, seed, drop):
     return I.smooth_random(zyx, seed, dim=2)
 
 
-def make_batch(L, store, grids=GRIDS):
-    base = dict(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1, nu_H=0.02, store=store)
+def make_batch(L, store, grids=GRIDS, g_scale=0.0):
+    base = dict(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1, nu_H=0.02, store=store, g_scale=g_scale)
     params, init = [], []
     for k, (shape, bc, over, drop) in enumerate(grids):
         kw = dict(base)
@@ -95,6 +95,35 @@ def test_batch_equals_grids_alone_f64(lbm):
         sim.step(9)
         h, g = sim.get_populations()
         assert normwise(got[k][0], h) < 1e-14 and normwise(got[k][1], g) < 1e-13, k
+
+
+@pytest.mark.parametrize("store,g_scale,tol", [("F16S", 1e3, 2e-2), ("BF16S", 0.0, 1e-1)], ids=["f16s", "bf16s"])
+def test_batch_16bit_storage(lbm, store, g_scale, tol):
+    """16-bit shifted storage in the batch kernel (the collision computes the
+    stored shifted and scaled values directly): every grid against the same
+    grid stepped alone with the same storage, and against the FP64 oracle,
+    after 5 steps.  Both runs round to 16 bits, so they agree to the storage
+    rounding rather than bit for bit; a wrong shift or scale would be off by
+    the size of the populations themselves."""
+    st = getattr(lbm, store)
+    b, params, init = make_batch(lbm, st, g_scale=g_scale)
+    b.step(5)
+    lat = oracle_lattice(0)
+    for k, (shape, bc, _, _) in enumerate(GRIDS):
+        fb, Pb, rb = b.grid(k).macro()
+        sim = lbm.Simulation(lbm.D2Q9, shape, params[k], bc=bc)
+        phi, u, P = init[k]
+        sim.init_fields(np.ascontiguousarray(phi.reshape(-1)), user_velocity(u, 0), np.ascontiguousarray(P.reshape(-1)))
+        sim.step(5)
+        fs, Ps, rs = sim.macro()
+        sim.close()
+        p = oracle_params(params[k], bc, 0)
+        h, g = O.init_populations(phi, u, P, lat, p)
+        h, g = O.run(h, g, lat, p, 5)
+        fo, Po, ruo = oracle_macro_flat(h, g, lat, p, 0)
+        for name, a, a1, o in (("phi", fb, fs, fo), ("P", Pb, Ps, Po), ("rho_u", rb, rs, ruo)):
+            assert np.isfinite(a).all(), (k, name)
+            assert normwise(a, a1) < tol and normwise(a, o) < tol, (k, name, normwise(a, a1), normwise(a, o))
 
 
 def test_batch_tiles_and_chunks_agree_f64(lbm):
