@@ -469,9 +469,10 @@ def run_batch(args):
         if args.autotune:
             tile, lz, _ = b.autotune(5)
         else:
-            # 32-wide CTAs, 16 planes: the tuner's pick on this workload
-            tile = 2 if args.tile is None else args.tile
-            lz = args.lz
+            # 64-wide CTAs with the g loads held across the phi fill, 32 planes:
+            # the tuner's pick on this workload (lbm_batch_autotune)
+            tile = 0 if args.tile is None else args.tile
+            lz = 32 if args.tile is None else args.lz
             b.set_tile(tile, lz)
         b.set_graph(10)
         b.step(args.warmup)

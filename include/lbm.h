@@ -249,8 +249,10 @@ int lbm_set_wall_velocity(lbm_ctx* ctx, int axis, int side, const double u[3]);
  *         launch.
  * Tiles other than 4 and the one-wave forms take chunks of `lz` >= 1 planes
  * along the march axis (z in 3-D, y in 2-D).  Every tile computes the same
- * arithmetic.  lbm_create picks tile 8 (D3Q19) or tile 1 (D2Q9) with
- * lz = 16; lbm_get_tile reports the current choice and its CTA shape.
+ * arithmetic.  lbm_create picks tile 1 with lz = 16 for D2Q9, and for D3Q19
+ * tile 8 with lz = 16, or tile 3 with lz = 32 for FP32 storage on grids of
+ * 2^24 nodes or more; lbm_get_tile reports the current choice and its CTA
+ * shape.
  * Errors: LBM_EINVAL for an unknown tile or lz < 1, LBM_ENOTSUP for a
  * bulk-copy or asynchronous-copy tile this grid, layout or storage type
  * cannot use. */

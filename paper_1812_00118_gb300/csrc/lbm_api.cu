@@ -351,8 +351,20 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
     c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
     if (!c->K || c->G.NP >= (1LL << 31)) return LBM_EINVAL;
     // default: per-thread loads in phases (the fastest tiles on the measured
-    // grids; lbm_autotune picks per grid): D3Q19 at 7 CTAs per SM, D2Q9 at 8
-    c->tile = lattice == LBM_D2Q9 ? 1 : 8;
+    // grids; lbm_autotune picks per grid): D2Q9 at 8 CTAs per SM; D3Q19 at 7
+    // CTAs per SM (72 registers) and 16 planes, which keeps a grid like 128^3
+    // (1024 CTAs) in one wave, and for FP32 storage from 2^24 nodes on, where
+    // the grid runs in several waves anyway, at 6 CTAs per SM (80 registers,
+    // fewer spills) and 32 planes (256 x 256 x 512: 1.988 against 2.068 ms per
+    // step; the 16-bit forms are faster at 7 CTAs per SM: 1.776 against 1.820)
+    if (lattice == LBM_D2Q9) {
+        c->tile = 1;
+    } else if (params->store == LBM_F32 && c->G.N >= (1LL << 24)) {
+        c->tile = 3;
+        c->lz = 32;
+    } else {
+        c->tile = 8;
+    }
     return LBM_OK;
 }
 
