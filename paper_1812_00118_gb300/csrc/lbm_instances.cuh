@@ -240,7 +240,8 @@ struct Launchers {
     static cudaError_t macro(const void* gin, const Geom& G, const Phys& p, const double* phi, double* P,
                              double* ux, double* uy, double* uz, cudaStream_t s) {
         macro_kernel<LAT, ST><<<blocks_for(G.N, 256), 256, 0, s>>>(
-            dir_ptrs<S, Q>(gin, gin, nullptr, nullptr, G.NP), G, phys_as<double>(p), phi, P, ux, uy, uz);
+            dir_ptrs<S, Q>(gin, gin, nullptr, nullptr, G.NP), G, phys_as<typename Storage<ST>::R>(p), phi, P, ux, uy,
+            uz);
         return cudaGetLastError();
     }
     static cudaError_t init(void* hout, void* gout, const Geom& G, const Phys& p, const double* phi,

@@ -577,9 +577,10 @@ struct NodeState {
 //   sum c c K = T (u V + V u) - c u u + rho_dif T (u.grad) I,
 // and since P - rho_dif T (u.grad) / 2 = T m0,
 //   Pi = m2 - T m0 I + u Y + W u,   W = T V / 2,  Y = W - (rho + c / 2) u.
+// The flow fields: rho, mu, F, u (with the Eq. 13 velocity reading) and P,
+// from phi, its stencils and the zeroth and first moments of g.
 template <typename R, bool THREE_D>
-__device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R m0, R mx, R my, R mz,
-                                           R mxx, R myy, R mzz, R mxy, R mxz, R myz) {
+__device__ __forceinline__ void node_flow(NodeState<R>& s, const PhysT<R>& p, R m0, R mx, R my, R mz) {
     const R T = (R)(1.0 / 3.0);
     const R rho_dif = (R)p.rho_dif;
     s.rho = (R)p.rho_L + s.phi * rho_dif;
@@ -597,6 +598,14 @@ __device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R
     s.ug = s.ux * s.gx + s.uy * s.gy + s.uz * s.gz;
     s.uF = s.ux * s.Fx + s.uy * s.Fy + s.uz * s.Fz;
     s.P = T * m0 + (R)0.5 * T * rho_dif * s.ug;
+}
+
+template <typename R, bool THREE_D>
+__device__ __forceinline__ void node_state(NodeState<R>& s, const PhysT<R>& p, R m0, R mx, R my, R mz,
+                                           R mxx, R myy, R mzz, R mxy, R mxz, R myz) {
+    const R T = (R)(1.0 / 3.0);
+    const R rho_dif = (R)p.rho_dif;
+    node_flow<R, THREE_D>(s, p, m0, mx, my, mz);
     // second moment of g^eq (closed form above, collected), then Pi
     const R sK = rho_dif + (R)3 * s.mu;          // s / T
     const R sK6 = sK * (R)(1.0 / 6.0);           // T s / 2
@@ -1418,10 +1427,15 @@ __device__ __forceinline__ void stencils(const double* __restrict__ phi, const G
     *gx = (R)3 * ax; *gy = (R)3 * ay; *gz = (R)3 * az; *lap = (R)6 * l;
 }
 
-// Macroscopic fields (phi given) in double: P and u (internal axes).
+// Macroscopic fields (phi given): P and u (internal axes), written in
+// double.  Computed in the kernels' arithmetic type R: FP64 for FP64 storage,
+// FP32 for FP32 and 16-bit storage (their values carry FP32 rounding
+// already, and GB300's FP64 rate is low).  Only the flow fields of the step
+// (node_flow), not the collision's second moments.
 template <int LAT, int ST>
-__global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G, PhysT<double> p,
-                             const double* __restrict__ phi, double* P, double* ux, double* uy, double* uz) {
+__global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>::Q> D, Geom G,
+                             PhysT<typename Storage<ST>::R> p, const double* __restrict__ phi, double* P, double* ux,
+                             double* uy, double* uz) {
     using L = Lattice<LAT>;
     using St = Storage<ST>;
     using R = typename St::R;
@@ -1430,24 +1444,25 @@ __global__ void macro_kernel(const DirPtrs<typename Storage<ST>::S, Lattice<LAT>
     int x, y, z;
     node_coords(G, n, &x, &y, &z);
     const PullOffsets po = pull_offsets(G, x, y, z);
-    NodeState<double> s;
-    s.phi = phi[n];
-    stencils<LAT>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
-    double m0 = 0, mx = 0, my = 0, mz = 0;
+    NodeState<R> s;
+    s.phi = (R)phi[n];
+    stencils<LAT, R>(phi, G, x, y, z, &s.gx, &s.gy, &s.gz, &s.lap);
+    R m0 = 0, mx = 0, my = 0, mz = 0;
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int CX = L::cx[i], CY = L::cy[i], CZ = L::cz[i];
         constexpr double W = L::w[i];
-        const double v = (double)St::load(pull_pad<LAT, i, false>(D.gin, po), (R)(W * p.g_shift),
-                                          (R)p.g_inv_scale);
+        const R v = St::load(pull_pad<LAT, i, false>(D.gin, po), (R)W * p.g_shift, p.g_inv_scale);
         m0 += v;
-        mx += CX * v; my += CY * v; mz += CZ * v;
+        if (CX) mx += cmul<CX>(v);
+        if (CY) my += cmul<CY>(v);
+        if (CZ) mz += cmul<CZ>(v);
     });
-    node_state<double, L::kHasY>(s, p, m0, mx, my, mz, 0, 0, 0, 0, 0, 0);
-    P[n] = s.P;
-    ux[n] = s.ux;
-    uy[n] = s.uy;
-    uz[n] = s.uz;
+    node_flow<R, L::kHasY>(s, p, m0, mx, my, mz);
+    P[n] = (double)s.P;
+    ux[n] = (double)s.ux;
+    uy[n] = (double)s.uy;
+    uz[n] = (double)s.uz;
 }
 
 // Where the value pulled by node (x, y, z) for direction I lives: x - c_I

@@ -1081,13 +1081,32 @@ __global__ void smooth_kernel(const double* __restrict__ a, double* __restrict__
 
 constexpr size_t kRowSmemMax = 200 * 1024;
 
+// Shared memory of one SM of the current device (looked up once per device;
+// 228 KB, GB300's, if the query fails).
+size_t sm_shared_bytes() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 228 * 1024;
+    }
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 228 * 1024;
+        }
+        cached[dev] = v;
+    }
+    return (size_t)cached[dev];
+}
+
 // Dynamic shared memory of a row-march launch: its need, raised if necessary
 // so that no more CTAs fit on an SM than its 512 tensor-memory columns serve
 // at once (each CTA holds row_tmem_cols(Co) of them for its whole life).
 size_t conv_row_launch_smem(size_t need, int Co) {
     const int per_sm = 512 / (int)row_tmem_cols(Co);
-    const size_t sm_bytes = 228 * 1024;            // shared memory of an SM
-    const size_t floor_bytes = sm_bytes / (size_t)(per_sm + 1) + 1;
+    const size_t floor_bytes = sm_shared_bytes() / (size_t)(per_sm + 1) + 1;
     return need > floor_bytes ? need : floor_bytes;
 }
 
@@ -1118,7 +1137,7 @@ cudaError_t conv_row_slots(size_t need, int Co, int* out) {
 // conv_row_launch_smem so that the CTAs an SM holds fit its tensor memory.
 size_t wg_launch_smem(size_t need, int Ci) {
     const int per_sm = 512 / (int)wg_tmem_cols(Ci);
-    const size_t floor_bytes = (size_t)(228 * 1024) / (size_t)(per_sm + 1) + 1;
+    const size_t floor_bytes = sm_shared_bytes() / (size_t)(per_sm + 1) + 1;
     return need > floor_bytes ? need : floor_bytes;
 }
 
@@ -1152,10 +1171,10 @@ cudaError_t wgrad_row_plan(int N, int H, int W, int Ci, int Co, int* rows, int* 
     }
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // CTAs an SM holds: its 228 KB of shared memory (1 KB reserved per CTA)
-    // and its 512 tensor-memory columns
+    // CTAs an SM holds: its shared memory (1 KB reserved per CTA) and its 512
+    // tensor-memory columns
     const size_t per_cta = wg_launch_smem(Lt.total, Cn) + 1024;
-    occ = (int)((size_t)(228 * 1024) / per_cta);
+    occ = (int)(sm_shared_bytes() / per_cta);
     const int by_tmem = 512 / (int)wg_tmem_cols(Cn);
     if (occ > by_tmem) occ = by_tmem;
     const long long slots = (long long)sms * (occ > 0 ? occ : 1);
@@ -1201,7 +1220,10 @@ int lbm_sg_conv3x3(const void* x, int csx, const void* w, const float* bias, flo
     const size_t row_smem = conv_row_smem_bytes(Ci, Co);
     if (W % kRowM == 0 && H >= 2 && row_smem <= kRowSmemMax) {
         int slots = 0;
-        if (conv_row_slots(row_smem, Co, &slots) != cudaSuccess) return LBM_ECUDA;
+        if (conv_row_slots(row_smem, Co, &slots) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ECUDA;
+        }
         int dev = 0, sms = 1;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1265,7 +1287,10 @@ int lbm_sg_conv3x3_wgrad(const void* x, int csx, const void* gy, int csg, float*
     // rows of 64-pixel segments with 16-byte aligned channel rows: the
     // tcgen05 row march
     int rows = 0, rchunks = 0;
-    if (wgrad_row_plan(N, H, W, Ci, Co, &rows, &rchunks) != cudaSuccess) return LBM_ECUDA;
+    if (wgrad_row_plan(N, H, W, Ci, Co, &rows, &rchunks) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
     if (rows > 0 && csx % 8 == 0 && csg % 8 == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)gy & 15) == 0 &&
         ((uintptr_t)scratch & 15) == 0) {
         int* err = nullptr;
