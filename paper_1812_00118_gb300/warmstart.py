@@ -12,8 +12,9 @@ are rebuilt from the prediction as equilibria plus the filtered
 non-equilibrium part (lbm_init_fields_ex, LBM_INIT_NONEQ), after the
 predicted phi is projected onto the start (change confined to the
 interfaces, total of phi restored in FP64: lbm_sg_phi_project).  The plain
-solver then continues and decides convergence, so the method stays the
-judge and the fallback.
+solver then continues and decides convergence: the network only chooses
+the state the solver starts from, so a poor prediction costs steps, not
+accuracy.
 
 Convergence (time-to-tolerance): every `check_every` steps the Laplace
 jump of the state, J = mean P of the bulk heavy phase minus mean P of the
