@@ -93,3 +93,33 @@ def test_noalloc_binding_rejects_bad_arguments_before_launch():
     for phi, P, v, o in bad:
         with pytest.raises(ValueError):
             lbm.field_sums_noalloc(phi, P, v, 0.0, 1.0, o, stream=0)
+
+
+def test_create_rejects_bad_arguments_before_any_allocation(lib):
+    """lbm_create_ex validates its grid, parameters and flags before it touches
+    the GPU: an unknown flag, a D2Q9 grid with nz != 1, a bad boundary type or
+    a non-positive mobility return LBM_EINVAL and no context (this machine has
+    no GPU, so reaching an allocation would fail differently)."""
+    import ctypes
+    from paper_1812_00118_gb300 import lbm
+    prm = lbm.make_params()
+    ctx = ctypes.c_void_p()
+
+    def create(grid, lattice=lbm.D3Q19, params=prm, flags=0):
+        ctx.value = None
+        rc = lib.lbm_create_ex(ctypes.byref(grid), lattice, ctypes.byref(params), None, flags, ctypes.byref(ctx))
+        return rc, ctx.value
+
+    g = lbm.lbm_grid()
+    g.nx, g.ny, g.nz = 16, 16, 16
+    assert create(g, flags=2) == (lbm.EINVAL, None)                       # unknown flag
+    assert create(g, flags=lbm.CREATE_GHOST_BAND | 4) == (lbm.EINVAL, None)
+    g2 = lbm.lbm_grid()
+    g2.nx, g2.ny, g2.nz = 16, 16, 2
+    assert create(g2, lattice=lbm.D2Q9) == (lbm.EINVAL, None)            # D2Q9 with nz != 1
+    g3 = lbm.lbm_grid()
+    g3.nx, g3.ny, g3.nz = 16, 16, 16
+    g3.bc[1] = 7
+    assert create(g3) == (lbm.EINVAL, None)                              # unknown boundary type
+    bad = lbm.make_params(M=0.0)
+    assert create(g, params=bad) == (lbm.EINVAL, None)                   # M must be positive
