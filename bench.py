@@ -17,6 +17,12 @@ and no flush is needed between steps.
 --workload batch512 times instead 512 uneven D2Q9 grids (sides 32-512,
 48.3 M nodes) stepped as one batch: one persistent launch per step, replayed
 from a CUDA graph, against one single-grid launch per grid and step.
+--workload rising runs the 256 x 256 x 512 rising bubble in FP32 and FP16 /
+BF16-shifted storage against the GPU's FP64 run (errors, rise velocity).
+--workload ttt measures time to tolerance of drop relaxation, plain against
+the learned warm start (and the batch and 16-bit forms).
+--workload surrogate times the warm-start U-Net's training step on the
+library's tensor-core kernels (TFLOP/s).
 
 N > 1 runs one independent replica per GPU (launched by torchrun; weak
 scaling): the single-domain step has no data-parallel split without a halo
