@@ -288,7 +288,7 @@ def test_tile_shapes_agree(lbm, lat_id, shape, bc):
             assert normwise(hg, ref[0]) < 1e-14 and normwise(gg, ref[1]) < 1e-13, (tile, lz)
 
 
-F32_TILES = ((7, 16), (7, 1), (7, 5), (8, 16), (8, 1), (9, 5))
+F32_TILES = ((7, 16), (7, 1), (7, 5), (8, 16), (8, 1), (9, 5), (3, 32), (3, 4))
 
 
 def oracle_pops_after(lbm, lat_id, shape, bc, steps):
@@ -298,7 +298,8 @@ def oracle_pops_after(lbm, lat_id, shape, bc, steps):
 
 @pytest.mark.parametrize("lat_id,shape,bc", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4]], ids=IDS)
 def test_f32_tiles_agree(lbm, lat_id, shape, bc):
-    """The FP32 tiles -- cp.async (7) and 7 CTAs per SM (8-9) -- against the
+    """The FP32 tiles -- cp.async (7), 7 CTAs per SM (8-9) and 6 CTAs per SM
+    (3, the default of large FP32 grids) -- against the
     per-thread-load tile 1 (same arithmetic: a few FP32 roundings, 1e-6
     normwise after 7 steps) and against the FP64 oracle (populations after 7
     steps, and phi, P, rho u after one step: 1e-5 normwise)."""
@@ -316,7 +317,7 @@ def test_f32_tiles_agree(lbm, lat_id, shape, bc):
         hg, gg = sim.get_populations()
         assert normwise(hg, hr) < 1e-6 and normwise(gg, gr) < 1e-6, (tile, lz, normwise(hg, hr), normwise(gg, gr))
         assert normwise(hg, hof) < 1e-5 and normwise(gg, gof) < 1e-5, (tile, lz)
-    for tile in (7, 8, 9):
+    for tile in (3, 7, 8, 9):
         sim, h, g, lat, p, _ = make_case(lbm, lat_id, shape, bc, lbm.F32)
         sim.set_tile(tile, 16)
         sim.step(1)
