@@ -183,17 +183,28 @@ def make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1 / 6, 
     return p
 
 
-def _ptr(a, writable=False):
+def _ptr(a, writable=False, n=None, device=None, name="field"):
     """(pointer, on_device) for a numpy float64 C-contiguous array or a contiguous
-    torch float64 tensor (CUDA: device pointer; CPU, e.g. pinned: host pointer)."""
+    torch float64 tensor (CUDA: device pointer; CPU, e.g. pinned: host pointer).
+    n: the exact number of elements the library reads or writes; device: the
+    CUDA device a device tensor must live on.  Either mismatch is a ValueError
+    before anything reaches the library, which copies n elements unchecked."""
     if isinstance(a, np.ndarray):
         if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("fields must be C-contiguous float64 arrays")
+            raise ValueError(f"{name}: fields must be C-contiguous float64 arrays")
         if writable and not a.flags["WRITEABLE"]:
-            raise ValueError("output array is read-only")
+            raise ValueError(f"{name}: output array is read-only")
+        if n is not None and a.size != n:
+            raise ValueError(f"{name}: {n} elements required, got {a.size}")
         return ctypes.c_void_p(a.ctypes.data), 0
+    if not hasattr(a, "data_ptr"):
+        raise ValueError(f"{name}: a numpy array or a torch tensor is required, got {type(a).__name__}")
     if not (a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()):
-        raise ValueError("tensor fields must be contiguous float64")
+        raise ValueError(f"{name}: tensor fields must be contiguous float64")
+    if n is not None and a.numel() != n:
+        raise ValueError(f"{name}: {n} elements required, got {a.numel()}")
+    if a.is_cuda and device is not None and a.device.index != device:
+        raise ValueError(f"{name}: on cuda:{a.device.index}, the domain lives on cuda:{device}")
     return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
 
 
@@ -265,8 +276,9 @@ class Simulation:
             g.bc[a] = bc[a] if a < len(bc) else PERIODIC
         self.params = params
         self.Q = 9 if lattice == D2Q9 else 19
+        import torch
+        self._device = torch.cuda.current_device()
         if stream is None:
-            import torch
             stream = torch.cuda.current_stream().cuda_stream
         self._stream = stream
         ctx = ctypes.c_void_p()
@@ -296,7 +308,10 @@ class Simulation:
     def init_fields(self, phi, u, P, nonequilibrium=False):
         """Populations from (phi, u, P); with nonequilibrium, g also carries
         the Chapman-Enskog non-equilibrium part (lbm_init_fields_ex)."""
-        (pp, d0), (pu, d1), (pP, d2) = _ptr(phi), _ptr(u), _ptr(P)
+        N, dev = self.N, self._device
+        (pp, d0), (pu, d1), (pP, d2) = (_ptr(phi, n=N, device=dev, name="phi"),
+                                        _ptr(u, n=self.dim * N, device=dev, name="u"),
+                                        _ptr(P, n=N, device=dev, name="P"))
         if not (d0 == d1 == d2):
             raise ValueError("phi, u and P must all be host or all device")
         if nonequilibrium:
@@ -321,11 +336,11 @@ class Simulation:
             P = np.empty(self.N)
             rho_u = np.empty(self.dim * self.N)
         ptrs, dev = [], None
-        for a in (phi, P, rho_u):
+        for a, n, name in ((phi, self.N, "phi"), (P, self.N, "P"), (rho_u, self.dim * self.N, "rho_u")):
             if a is None:
                 ptrs.append(None)
                 continue
-            p, d = _ptr(a, writable=True)
+            p, d = _ptr(a, writable=True, n=n, device=self._device, name=name)
             dev = d if dev is None else dev
             if d != dev:
                 raise ValueError("outputs must all be host or all device")
@@ -334,15 +349,27 @@ class Simulation:
         return phi, P, rho_u
 
     def get_populations(self, h=None, g=None):
+        """(h, g), Q*N doubles each; both given (host arrays or device tensors)
+        or neither (host arrays are allocated)."""
+        if (h is None) != (g is None):
+            raise ValueError("give both h and g or neither")
         if h is None:
             h = np.empty(self.Q * self.N)
             g = np.empty(self.Q * self.N)
-        (ph, d0), (pg, d1) = _ptr(h, True), _ptr(g, True)
+        n = self.Q * self.N
+        (ph, d0), (pg, d1) = (_ptr(h, True, n=n, device=self._device, name="h"),
+                              _ptr(g, True, n=n, device=self._device, name="g"))
+        if d0 != d1:
+            raise ValueError("h and g must both be host or both device")
         _check(load().lbm_get_populations(self._ctx, ph, pg, d0), "lbm_get_populations")
         return h, g
 
     def set_populations(self, h, g):
-        (ph, d0), (pg, d1) = _ptr(h), _ptr(g)
+        n = self.Q * self.N
+        (ph, d0), (pg, d1) = (_ptr(h, n=n, device=self._device, name="h"),
+                              _ptr(g, n=n, device=self._device, name="g"))
+        if d0 != d1:
+            raise ValueError("h and g must both be host or both device")
         _check(load().lbm_set_populations(self._ctx, ph, pg, d0), "lbm_set_populations")
 
     def diagnostics(self, raise_on_divergence=True):
@@ -408,6 +435,7 @@ class _GridView(Simulation):
         self.Q = 9
         self.params = params
         self._stream = batch._stream
+        self._device = batch._device
         self._ctx = ctx
         self._batch = batch   # keeps the batch (owner of the context) alive
 
@@ -452,8 +480,9 @@ class Batch:
         if len(plist) != n:
             raise ValueError("one parameter block per grid")
         parr = (lbm_params * n)(*plist)
+        import torch
+        self._device = torch.cuda.current_device()
         if stream is None:
-            import torch
             stream = torch.cuda.current_stream().cuda_stream
         self._stream = stream
         self.shapes = [(int(a), int(b)) for a, b in shapes]

@@ -123,3 +123,56 @@ def test_create_rejects_bad_arguments_before_any_allocation(lib):
     assert create(g3) == (lbm.EINVAL, None)                              # unknown boundary type
     bad = lbm.make_params(M=0.0)
     assert create(g, params=bad) == (lbm.EINVAL, None)                   # M must be positive
+
+
+def test_simulation_binding_rejects_wrong_sizes_before_any_call(lib):
+    """Simulation.init_fields / macro / get_populations / set_populations
+    check the element count of every field before the library copies it: phi
+    and P must hold N doubles, u and rho u dim*N, h and g Q*N (a short device
+    tensor would otherwise be read or written past its end on the GPU).  The
+    object is made without a context, so a check that let a bad field through
+    would reach the library with a NULL context and fail differently."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_1812_00118_gb300 import lbm
+    sim = lbm.Simulation.__new__(lbm.Simulation)
+    sim.lattice, sim.dim, sim.Q = lbm.D2Q9, 2, 9
+    sim.shape, sim.N, sim._device, sim._ctx = (6, 5, 1), 30, 0, None
+    N = sim.N
+    z = np.zeros
+    bad_init = [
+        (z(N - 1), z(2 * N), z(N)),          # phi short
+        (z(N), z(3 * N), z(N)),              # u with 3 components on D2Q9
+        (z(N), z(2 * N), z(N + 1)),          # P long
+        (z(N).astype(np.float32), z(2 * N), z(N)),                      # dtype
+        (z((N, 2))[:, 0], z(2 * N), z(N)),                              # not contiguous
+        (torch.zeros(N, dtype=torch.float64), torch.zeros(2 * N - 2, dtype=torch.float64),
+         torch.zeros(N, dtype=torch.float64)),                          # tensor u short
+        ([0.0] * N, z(2 * N), z(N)),                                    # not an array
+    ]
+    for phi, u, P in bad_init:
+        with pytest.raises(ValueError):
+            sim.init_fields(phi, u, P)
+    with pytest.raises(ValueError):
+        sim.macro(z(N), z(N), z(3 * N))
+    with pytest.raises(ValueError):
+        sim.macro(None, z(N - 1), None)
+    ro = z(N)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        sim.macro(ro, None, None)
+    with pytest.raises(ValueError):
+        sim.get_populations(z(9 * N), None)              # one of the two
+    with pytest.raises(ValueError):
+        sim.get_populations(z(9 * N), z(9 * N - 1))
+    with pytest.raises(ValueError):
+        sim.set_populations(z(9 * N + 9), z(9 * N))
+    # correctly sized fields pass the checks and reach the library, which
+    # refuses the missing context
+    for call in (lambda: sim.init_fields(z(N), z(2 * N), z(N)),
+                 lambda: sim.macro(z(N), z(N), z(2 * N)),
+                 lambda: sim.get_populations(z(9 * N), z(9 * N)),
+                 lambda: sim.set_populations(z(9 * N), z(9 * N))):
+        with pytest.raises(lbm.LbmError) as e:
+            call()
+        assert e.value.code == lbm.EINVAL
