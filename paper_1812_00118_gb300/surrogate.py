@@ -227,6 +227,8 @@ class Surrogate:
     def set_input(self, x32):
         """x32: (M, 4) float32 device tensor of normalised inputs; builds the
         padded bf16 copy."""
+        if tuple(x32.shape) != tuple(self.x32.shape):
+            raise ValueError(f"x32: shape {tuple(self.x32.shape)} required, got {tuple(x32.shape)}")
         self.x32.copy_(x32)
         _ck(self.lib.lbm_sg_to_bf16(_ptr(self.x32), NC, _ptr(self.x16), 16, self.M[0], NC, self.stream),
             "lbm_sg_to_bf16")
@@ -263,6 +265,13 @@ class Surrogate:
         lib, s = self.lib, self.stream
         p, a = _ptr, self.a
         M1 = self.M[0]
+        t = self.torch
+        if not (isinstance(target32, t.Tensor) and target32.dtype == t.float32 and target32.is_cuda
+                and target32.is_contiguous() and tuple(target32.shape) == (M1, NC)
+                and target32.device == self.x32.device):
+            # the loss kernel reads M x 4 floats from this pointer unchecked
+            raise ValueError(f"target32: a contiguous float32 CUDA tensor of shape ({M1}, {NC}) on "
+                             f"{self.x32.device} is required")
         _ck(lib.lbm_sg_mse(p(self.x32), NC, p(self.delta), 16, p(target32), NC, p(self.g_delta), p(self.mse_scratch),
                            p(self.loss_dev), M1, NC, s), "lbm_sg_mse")
         _ck(lib.lbm_sg_to_bf16(p(self.g_delta), 16, p(self.g16_1), 16, M1, 16, s), "lbm_sg_to_bf16")

@@ -176,3 +176,22 @@ def test_simulation_binding_rejects_wrong_sizes_before_any_call(lib):
         with pytest.raises(lbm.LbmError) as e:
             call()
         assert e.value.code == lbm.EINVAL
+
+
+def test_surrogate_binding_rejects_bad_targets_before_any_call(lib):
+    """Surrogate.backward hands the target pointer to the loss kernel, which
+    reads M x 4 floats: anything but a contiguous float32 CUDA tensor of that
+    shape on the network's device is a ValueError first (on this CPU-only
+    machine every tensor also fails the device test), and set_input refuses
+    a wrong shape."""
+    torch = pytest.importorskip("torch")
+    from paper_1812_00118_gb300 import surrogate as SG
+    sg = SG.Surrogate.__new__(SG.Surrogate)
+    sg.torch, sg.lib, sg.stream, sg.a, sg.M = torch, lib, 0, {}, [64, 16, 4, 1]
+    sg.x32 = torch.zeros(64, 4)
+    for t in (torch.zeros(64, 4, dtype=torch.float64), torch.zeros(63, 4), torch.zeros(4, 64).t(),
+              torch.zeros(64, 4)):
+        with pytest.raises(ValueError):
+            sg.backward(t)
+    with pytest.raises(ValueError):
+        sg.set_input(torch.zeros(32, 4))
