@@ -342,14 +342,21 @@ int ctx_setup(lbm_ctx* c, const lbm_grid* grid, int lattice, const lbm_params* p
         c->G.GX = (band || c->G.wall[0]) ? (A32 > 2 ? A32 : 2) : 0;
         c->G.GY = lattice == LBM_D2Q9 ? 0 : ((band || c->G.wall[1]) ? 2 : 0);
         c->G.GZ = (band || c->G.wall[2]) ? 1 : 0;
-        c->G.PX = ((c->G.NX + A32 - 1) / A32) * A32 + 2 * c->G.GX;
-        c->G.PY = c->G.NY + 2 * c->G.GY;
-        c->G.PZ = c->G.NZ + 2 * c->G.GZ;
-        c->G.PXY = c->G.PX * c->G.PY;
-        c->G.NP = (long long)c->G.PXY * c->G.PZ;
+        // extents in 64 bits, checked before they are narrowed: the kernels
+        // index one population array with 32-bit offsets (PX * PY * PZ < 2^31)
+        const long long px = ((long long)c->G.NX + A32 - 1) / A32 * A32 + 2LL * c->G.GX;
+        const long long py = (long long)c->G.NY + 2LL * c->G.GY;
+        const long long pz = (long long)c->G.NZ + 2LL * c->G.GZ;
+        const long long pxy = px * py;                 // < 2^63: each factor < 2^32
+        if (pxy >= (1LL << 31) || pxy * pz >= (1LL << 31)) return LBM_EINVAL;
+        c->G.PX = (int)px;
+        c->G.PY = (int)py;
+        c->G.PZ = (int)pz;
+        c->G.PXY = (int)pxy;
+        c->G.NP = pxy * pz;
     }
     c->G.N = (long long)c->G.NX * c->G.NY * c->G.NZ;
-    if (!c->K || c->G.NP >= (1LL << 31)) return LBM_EINVAL;
+    if (!c->K) return LBM_EINVAL;
     // default: per-thread loads in phases (the fastest tiles on the measured
     // grids; lbm_autotune picks per grid): D2Q9 at 8 CTAs per SM; D3Q19 at 7
     // CTAs per SM (72 registers) and 16 planes, which keeps a grid like 128^3

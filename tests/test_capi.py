@@ -195,3 +195,25 @@ def test_surrogate_binding_rejects_bad_targets_before_any_call(lib):
             sg.backward(t)
     with pytest.raises(ValueError):
         sg.set_input(torch.zeros(32, 4))
+
+
+def test_create_rejects_grids_whose_padded_size_overflows(lib):
+    """A grid whose padded size reaches 2^31 cells is refused before any
+    allocation, including sizes whose x-y plane alone overflows 32 bits
+    (65536 x 65536 x 1 would wrap to an empty plane in 32-bit arithmetic)."""
+    import ctypes
+    from paper_1812_00118_gb300 import lbm
+    prm = lbm.make_params()
+    ctx = ctypes.c_void_p()
+    for nx, ny, nz in ((65536, 65536, 1), (65536, 65536, 2), (2048, 1024, 1024), (1 << 30, 4, 1),
+                       (2147483647, 1, 1)):
+        g = lbm.lbm_grid()
+        g.nx, g.ny, g.nz = nx, ny, nz
+        ctx.value = None
+        rc = lib.lbm_create_ex(ctypes.byref(g), lbm.D3Q19, ctypes.byref(prm), None, 0, ctypes.byref(ctx))
+        assert (rc, ctx.value) == (lbm.EINVAL, None), (nx, ny, nz)
+    # a D2Q9 grid of 65536 x 32768 (2^31 cells) too
+    g = lbm.lbm_grid()
+    g.nx, g.ny, g.nz = 65536, 32768, 1
+    rc = lib.lbm_create_ex(ctypes.byref(g), lbm.D2Q9, ctypes.byref(prm), None, 0, ctypes.byref(ctx))
+    assert rc == lbm.EINVAL
