@@ -277,8 +277,10 @@ int lbm_set_wait_limit(lbm_ctx* ctx, long long polls);
  * fastest configuration, and restores the state it started from (the state
  * is saved to, and copied back from, a temporary device copy).  Reports the
  * choice and its time per step (step kernel plus ghost update) in ms; any
- * output pointer may be NULL.  Synchronises.  Errors: LBM_EINVAL (steps < 1),
- * LBM_ENOMEM, LBM_ECUDA. */
+ * output pointer may be NULL.  Synchronises.  If a trial fails, the state is
+ * restored all the same, the context keeps the tile it had and the trial's
+ * status is returned.  Errors: LBM_EINVAL (steps < 1), LBM_EDIVERGED (the
+ * state was found diverged earlier), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_autotune(lbm_ctx* ctx, int steps, int* best_tile, int* best_lz, double* best_ms);
 
 /* Field diagnostics without any allocation.  The paper has no counterpart:
@@ -378,7 +380,9 @@ int lbm_batch_set_graph(lbm_batch* b, int k);
 /* Times every batch tile with lz in {4, 8, 16, 32} for `steps` steps each,
  * keeps the fastest, and restores the state it started from.  Reports the
  * choice and its time per step in ms (any pointer may be NULL).
- * Synchronises.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+ * Synchronises.  If a trial fails, the state is restored all the same, the
+ * batch keeps the tile it had and the trial's status is returned.  Errors:
+ * LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_autotune(lbm_batch* b, int steps, int* best_tile, int* best_lz, double* best_ms);
 
 /* Kernel launches issued by the batch steps (graph replays count their

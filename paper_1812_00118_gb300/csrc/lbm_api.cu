@@ -608,8 +608,10 @@ int lbm_macro(lbm_ctx* c, double* phi, double* P, double* rho_u, int on_device) 
     if (P && copy_field(c, P, f_P(c), N, on_device)) return LBM_ECUDA;
     if (rho_u) {
         double* dst = rho_u;
-        if (!on_device && cudaMallocAsync((void**)&dst, sizeof(double) * c->dim * (size_t)N, c->stream) != cudaSuccess)
+        if (!on_device && cudaMallocAsync((void**)&dst, sizeof(double) * c->dim * (size_t)N, c->stream) != cudaSuccess) {
+            cudaGetLastError();
             return LBM_ENOMEM;
+        }
         const unsigned nb = (unsigned)((N + 255) / 256);
         for (int d = 0; d < c->dim; ++d)
             rho_times_u_kernel<<<nb, 256, 0, c->stream>>>(f_phi(c), f_u(c, internal_axis(c, d)), N, c->P.rho_L,
@@ -632,8 +634,12 @@ int lbm_get_populations(lbm_ctx* c, double* h, double* g, int on_device) {
     const size_t n = (size_t)Q * c->G.N;
     double *dh = h, *dg = g;
     if (!on_device) {
-        if (cudaMallocAsync((void**)&dh, n * sizeof(double), c->stream) != cudaSuccess) return LBM_ENOMEM;
+        if (cudaMallocAsync((void**)&dh, n * sizeof(double), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ENOMEM;
+        }
         if (cudaMallocAsync((void**)&dg, n * sizeof(double), c->stream) != cudaSuccess) {
+            cudaGetLastError();
             cudaFreeAsync(dh, c->stream);
             return LBM_ENOMEM;
         }
@@ -656,8 +662,12 @@ int lbm_set_populations(lbm_ctx* c, const double* h, const double* g, int on_dev
     const double *dh = h, *dg = g;
     double *th = nullptr, *tg = nullptr;
     if (!on_device) {
-        if (cudaMallocAsync((void**)&th, n * sizeof(double), c->stream) != cudaSuccess) return LBM_ENOMEM;
+        if (cudaMallocAsync((void**)&th, n * sizeof(double), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ENOMEM;
+        }
         if (cudaMallocAsync((void**)&tg, n * sizeof(double), c->stream) != cudaSuccess) {
+            cudaGetLastError();
             cudaFreeAsync(th, c->stream);
             return LBM_ENOMEM;
         }
@@ -733,14 +743,21 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
     const size_t bytes = c->elem * (size_t)Q * (size_t)c->G.NP;
     void* save_h = nullptr;
     void* save_g = nullptr;
-    if (cudaMallocAsync(&save_h, bytes, c->stream) != cudaSuccess) return LBM_ENOMEM;
+    if (cudaMallocAsync(&save_h, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ENOMEM;
+    }
     if (cudaMallocAsync(&save_g, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
         cudaFreeAsync(save_h, c->stream);
         return LBM_ENOMEM;
     }
     const bool saved_ghosts = c->ghosts[c->cur];
+    const bool saved_diverged = c->diverged;
+    const int saved_tile = c->tile, saved_lz = c->lz, saved_fix_count = c->phi_fix_count;
     int rc = check_cuda(cudaMemcpyAsync(save_h, c->h[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     if (!rc) rc = check_cuda(cudaMemcpyAsync(save_g, c->g[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const bool saved = rc == LBM_OK;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -766,17 +783,22 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_tile, int* best_lz, double* be
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!rc) {
-        rc = check_cuda(cudaMemcpyAsync(c->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        if (!rc) rc = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    // the state goes back whether or not a trial failed (a failed trial keeps
+    // the tile the context had)
+    if (saved) {
+        int rr = check_cuda(cudaMemcpyAsync(c->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        if (!rr) rr = check_cuda(cudaMemcpyAsync(c->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, c->stream));
         c->cur = 0;
         c->ghosts[0] = saved_ghosts;
         c->ghosts[1] = false;
+        c->diverged = saved_diverged;
+        c->phi_fix_count = saved_fix_count;
+        if (!rc) rc = rr;
     }
     cudaFreeAsync(save_h, c->stream);
     cudaFreeAsync(save_g, c->stream);
-    c->tile = bt;
-    c->lz = bl;
+    c->tile = rc ? saved_tile : bt;
+    c->lz = rc ? saved_lz : bl;
     if (!rc) rc = check_cuda(cudaStreamSynchronize(c->stream));
     if (best_tile) *best_tile = bt;
     if (best_lz) *best_lz = bl;

@@ -363,8 +363,10 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* best_tile, int* best_lz, do
         cudaFreeAsync(save_h, b->stream);
         return LBM_ENOMEM;
     }
+    const int saved_tile = b->tile, saved_lz = b->lz;
     rc = check(cudaMemcpyAsync(save_h, b->h[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
     if (!rc) rc = check(cudaMemcpyAsync(save_g, b->g[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    const bool saved = rc == LBM_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc) rc = check(cudaEventCreate(&e0));
     if (!rc) rc = check(cudaEventCreate(&e1));
@@ -389,15 +391,18 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* best_tile, int* best_lz, do
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (!rc) {
-        rc = check(cudaMemcpyAsync(b->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, b->stream));
-        if (!rc) rc = check(cudaMemcpyAsync(b->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, b->stream));
+    // the state goes back whether or not a trial failed (a failed trial keeps
+    // the tile the batch had)
+    if (saved) {
+        int rr = check(cudaMemcpyAsync(b->h[0], save_h, bytes, cudaMemcpyDeviceToDevice, b->stream));
+        if (!rr) rr = check(cudaMemcpyAsync(b->g[0], save_g, bytes, cudaMemcpyDeviceToDevice, b->stream));
         b->cur = 0;
+        if (!rc) rc = rr;
     }
     cudaFreeAsync(save_h, b->stream);
     cudaFreeAsync(save_g, b->stream);
-    b->tile = bt;
-    b->lz = bl;
+    b->tile = rc ? saved_tile : bt;
+    b->lz = rc ? saved_lz : bl;
     const int ri = set_items(b);
     if (!rc) rc = ri;
     sync_views(b);
