@@ -132,6 +132,8 @@ def generate_snapshots(torch, Lsz, seeds, K, dt=DT, store=L.F32, max_u=0.05, chu
         if idx:
             kept.append(S.index_select(0, torch.tensor(idx, dtype=torch.long, device="cuda")))
         del S
+    if not kept:
+        raise RuntimeError(f"generate_snapshots: all {dropped} cases left the bounds (non-finite or |u| >= {max_u})")
     return torch.cat(kept, 0), dropped
 
 
