@@ -26,7 +26,7 @@ library's tensor-core kernels (TFLOP/s).
 
 N > 1 runs one independent replica per GPU (launched by torchrun; weak
 scaling): the single-domain step has no data-parallel split without a halo
-exchange, which this build does not implement.
+exchange, which the library does not implement.
 """
 import argparse
 import ctypes

@@ -52,7 +52,7 @@ enum lbm_status {
     LBM_ECUDA = -3,      /* a CUDA call failed */
     LBM_EDIVERGED = -4,  /* a diagnostic found a non-finite value or |u| > 0.3 */
     LBM_ETIMEOUT = -5,   /* a bounded device wait gave up */
-    LBM_ENOTSUP = -6,    /* combination not supported by this build */
+    LBM_ENOTSUP = -6,    /* combination the library does not support */
     LBM_ECHECKED = -7    /* checked builds: a step kernel met an offset outside its arrays */
 };
 
