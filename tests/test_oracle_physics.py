@@ -351,3 +351,25 @@ def test_hydrostatic_start_balances_the_body_force():
         h, g = O.run(h, g, L.D2Q9, q, 200)
         umax[name] = np.abs(O.macroscopic(h, g, L.D2Q9, q)["u"]).max()
     assert umax["hydrostatic"] < 0.05 * umax["zero"], umax
+
+
+@pytest.mark.parametrize("lat,shape", [(L.D2Q9, (1, 20, 26)), (L.D3Q19, (9, 8, 10))], ids=["D2Q9", "D3Q19"])
+def test_buoyancy_force_has_no_net_push(lat, shape):
+    """Reading R7, force_mode 1: F = (rho - rho_bar) g with rho_bar the mean
+    density of the domain, so on a periodic domain the body force sums to
+    zero at every step (phi, hence the mean density, is conserved) and the
+    total momentum changes only by the sum of mu grad phi, not by any net
+    weight: buoyancy without a push on the whole fluid."""
+    phi, u, P = I.smooth_random(shape, 13, dim=lat.dim)
+    phi = 0.2 + 0.7 * phi          # mean away from 1/2, so rho_bar differs from the mid-density
+    g_acc = (0.0, -2e-5, 0.0) if lat.dim == 2 else (0.0, 0.0, -2e-5)
+    p = O.Params(M=0.1, W=3.0, sigma=0.01, rho_L=0.01, rho_H=1.0, nu_L=0.1, nu_H=0.05, g=g_acc, force_mode=1)
+    h, g = O.init_populations(phi, u, P, lat, p)
+    rho_mean = float(O.density(phi, p).mean())
+    assert p.rho_bar == pytest.approx(rho_mean, rel=1e-14)
+    for _ in range(2):
+        m = O.macroscopic(h, g, lat, p)
+        scale = np.abs(m["F"]).sum()
+        assert scale > 0
+        assert np.abs(m["F"].reshape(3, -1).sum(axis=1)).max() < 1e-13 * scale
+        h, g = O.run(h, g, lat, p, 10)

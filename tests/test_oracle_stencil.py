@@ -33,11 +33,12 @@ def test_linear_and_quadratic_exactness(lat):
     np.testing.assert_allclose(gq[1][inner], (4 * y - x)[inner], atol=1e-12)
 
 
-@pytest.mark.parametrize("lat", [L.D2Q9, L.D3Q19], ids=lambda l: l.name)
-@pytest.mark.parametrize("axis", [0, 1, 2])
+AXIS_CASES = [(L.D2Q9, 0), (L.D2Q9, 1), (L.D3Q19, 0), (L.D3Q19, 1), (L.D3Q19, 2)]
+AXIS_IDS = ["D2Q9-x", "D2Q9-y", "D3Q19-x", "D3Q19-y", "D3Q19-z"]
+
+
+@pytest.mark.parametrize("lat,axis", AXIS_CASES, ids=AXIS_IDS)
 def test_fourier_symbols(lat, axis):
-    if lat.dim == 2 and axis == 2:
-        pytest.skip("no z axis in 2-D")
     n = 16
     shape = [1, 1, 1]
     shape[2 - axis] = n
@@ -49,3 +50,30 @@ def test_fourier_symbols(lat, axis):
     np.testing.assert_allclose(gr, np.sin(k) * np.cos(k * s), atol=1e-14)
     lap = O.laplacian(phi, lat, bc).reshape(-1)
     np.testing.assert_allclose(lap, -4 * np.sin(k / 2) ** 2 * np.sin(k * s), atol=1e-14)
+
+
+@pytest.mark.parametrize("lat,axis", AXIS_CASES, ids=AXIS_IDS)
+def test_wall_nodes_read_the_adjacent_fluid_value(lat, axis):
+    """Reading R9: behind a wall the stencils read the value of the fluid
+    node next to it (zero normal gradient).  For phi = a s along a walled
+    axis s the central difference at the first node is then (phi(1) -
+    phi(0)) / 2 = a/2 and the Laplacian phi(1) - phi(0) = a (the weights of
+    the directions with c_s = +1 sum to 1/6 on both lattices, so the
+    stencils reduce to the 1-D differences); at the last node a/2 and -a."""
+    shape = (6, 7, 8) if lat.dim == 3 else (1, 7, 8)
+    coords = np.meshgrid(*[np.arange(s, dtype=float) for s in shape], indexing="ij")
+    s = coords[2 - axis]
+    a = 0.37
+    phi = a * s + 0.1
+    gr = O.gradient(phi, lat, WALLS)
+    lap = O.laplacian(phi, lat, WALLS)
+    first = [slice(None)] * 3
+    last = [slice(None)] * 3
+    first[2 - axis], last[2 - axis] = 0, -1
+    np.testing.assert_allclose(gr[axis][tuple(first)], a / 2, atol=1e-14)
+    np.testing.assert_allclose(gr[axis][tuple(last)], a / 2, atol=1e-14)
+    np.testing.assert_allclose(lap[tuple(first)], a, atol=1e-13)
+    np.testing.assert_allclose(lap[tuple(last)], -a, atol=1e-13)
+    for b in range(3):
+        if b != axis:
+            np.testing.assert_allclose(gr[b], 0.0, atol=1e-14)
