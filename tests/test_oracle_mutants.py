@@ -1,7 +1,8 @@
 """The oracle's pins against planted mistakes.
 
 Each case plants one plausible slip -- a dropped term, a wrong sign, factor,
-index or operand -- in a fresh copy of the oracle's step module, built in
+index or operand -- in a fresh copy of an oracle module (the LB step, or the
+surrogate network's forward and backward pass), built in
 this process from its source with one expression replaced (nothing on disk
 changes), points the pin test's module at the copy, and requires the pin to
 fail.  The pins named here check the oracle against what the paper and the
@@ -21,6 +22,7 @@ from oracle import lattice as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = open(os.path.join(ROOT, "oracle", "pflbm.py")).read()
+SRC_SG = open(os.path.join(ROOT, "oracle", "surrogate.py")).read()
 
 D2 = dict(lat=L.D2Q9)
 
@@ -114,15 +116,15 @@ CASES = [
 ]
 
 
-def _planted(old, new):
-    assert SRC.count(old) == 1, f"the expression must occur once: {old!r}"
-    name = "oracle._pflbm_planted"
+def _planted(old, new, src=SRC, fname="pflbm.py"):
+    assert src.count(old) == 1, f"the expression must occur once: {old!r}"
+    name = "oracle._planted_" + fname[:-3]
     mod = types.ModuleType(name)
     mod.__package__ = "oracle"
-    mod.__file__ = os.path.join(ROOT, "oracle", "pflbm.py")
+    mod.__file__ = os.path.join(ROOT, "oracle", fname)
     sys.modules[name] = mod        # dataclasses resolve their module while the class is built
     try:
-        exec(compile(SRC.replace(old, new), mod.__file__, "exec"), mod.__dict__)
+        exec(compile(src.replace(old, new), mod.__file__, "exec"), mod.__dict__)
     finally:
         del sys.modules[name]
     return mod
@@ -134,5 +136,40 @@ def test_pin_fails_on_planted_slip(monkeypatch, slip, old, new, pin_module, pin,
     test = getattr(tm, pin)
     test(**kwargs)                                  # the pin holds on the oracle as it is
     monkeypatch.setattr(tm, "O", _planted(old, new))
+    with pytest.raises(AssertionError):
+        test(**kwargs)
+
+
+# surrogate network oracle: (slip, expression, planted form, pin test of test_oracle_surrogate, arguments)
+SG_CASES = [
+    ("conv reads p - d", "xs = np.roll(x, shift=(1 - dy, 1 - dx), axis=(1, 2))\n            out +=",
+     "xs = np.roll(x, shift=(dy - 1, dx - 1), axis=(1, 2))\n            out +=", "test_conv_matches_loop_definition", {}),
+    ("conv taps transposed", 'out += np.einsum("nhwi,oi->nhwo", xs, W[:, :, dy, dx])',
+     'out += np.einsum("nhwi,oi->nhwo", xs, W[:, :, dx, dy])', "test_conv_matches_loop_definition", {}),
+    ("input gradient shifted the wrong way", "shift=(dy - 1, dx - 1), axis=(1, 2))",
+     "shift=(1 - dy, 1 - dx), axis=(1, 2))", "test_conv_backward_finite_differences", {}),
+    ("weight gradient taps transposed", 'gW[:, :, dy, dx] = np.einsum("nhwo,nhwi->oi", gout, xs)',
+     'gW[:, :, dx, dy] = np.einsum("nhwo,nhwi->oi", gout, xs)', "test_conv_backward_finite_differences", {}),
+    ("pooling gradient not divided by f^2", "return np.repeat(np.repeat(g, f, axis=1), f, axis=2) / (f * f)",
+     "return np.repeat(np.repeat(g, f, axis=1), f, axis=2)", "test_pool_and_upsample_adjoints", dict(f=2)),
+    ("upsampling gradient averaged", "return g.reshape(N, H // f, f, W // f, f, C).sum(axis=(2, 4))",
+     "return g.reshape(N, H // f, f, W // f, f, C).mean(axis=(2, 4))", "test_pool_and_upsample_adjoints", dict(f=2)),
+    ("skip-connection gradient dropped", 'gs3 = gs3 + pool_backward(layer_back("b", ghb))',
+     'gs3 = pool_backward(layer_back("b", ghb))', "test_network_gradient_finite_differences", {}),
+    ("ReLU gradient unmasked", "ga = gy * (cache[name] > 0)", "ga = gy", "test_network_gradient_finite_differences", {}),
+    ("concatenation split swapped", "gs1, gt2 = gc1[..., :n1], upsample_backward(gc1[..., n1:])",
+     "gs1, gt2 = gc1[..., n1:], upsample_backward(gc1[..., :n1])", "test_network_gradient_finite_differences", {}),
+    ("loss gradient factor 2 dropped", "gout = 2.0 * (out - target) / out.size", "gout = (out - target) / out.size",
+     "test_network_gradient_finite_differences", {}),
+    ("residual branch dropped", "return x + delta, c", "return delta, c", "test_identity_when_last_layer_is_zero", {}),
+]
+
+
+@pytest.mark.parametrize("slip,old,new,pin,kwargs", SG_CASES, ids=[c[0] for c in SG_CASES])
+def test_surrogate_pin_fails_on_planted_slip(monkeypatch, slip, old, new, pin, kwargs):
+    tm = importlib.import_module("test_oracle_surrogate")
+    test = getattr(tm, pin)
+    test(**kwargs)
+    monkeypatch.setattr(tm, "S", _planted(old, new, SRC_SG, "surrogate.py"))
     with pytest.raises(AssertionError):
         test(**kwargs)
