@@ -130,6 +130,19 @@ int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params,
 int lbm_create_ex(const lbm_grid* grid, int lattice, const lbm_params* params,
                   void* cuda_stream, int flags, lbm_ctx** out);
 
+/* Device memory plan of a grid, computed on the host without a GPU (nothing
+ * is allocated): the checks of lbm_create_ex, then out[0..2] = padded
+ * extents of the population arrays along the internal axes x, y, z (for
+ * D2Q9 the user's y is the internal z and out[1] = 1; x rows padded to 32
+ * bytes, ghost cells on walled axes, or on every axis with
+ * LBM_CREATE_GHOST_BAND), out[3] = cells per population array (their
+ * product, < 2^31), out[4] = bytes of the population buffers (h and g, two
+ * time levels each: 4 Q out[3] times the storage type's size), out[5] =
+ * bytes a context holds once it has been initialised (out[4], the scratch
+ * fields of 5 N doubles and the reduction partials).  Errors: as
+ * lbm_create_ex (LBM_EINVAL, out untouched). */
+int lbm_layout(const lbm_grid* grid, int lattice, const lbm_params* params, int flags, long long out[6]);
+
 /* Initialise the populations from macroscopic fields (Section 4 set-ups
  * start from (phi, u, P)): h = h^eq (Eq. 2) and g = g^eq (Eq. 6 with Eq. 7
  * and Eq. 13) evaluated with the central-difference stencils of the given

@@ -470,6 +470,25 @@ int lbm_create_ex(const lbm_grid* grid, int lattice, const lbm_params* params, v
     return LBM_OK;
 }
 
+int lbm_layout(const lbm_grid* grid, int lattice, const lbm_params* params, int flags, long long out[6]) {
+    if (!out) return LBM_EINVAL;
+    lbm_ctx c;                       // set-up only: no device call, nothing allocated
+    int rc = ctx_setup(&c, grid, lattice, params, nullptr, flags);
+    if (rc) return rc;
+    const long long Q = lattice == LBM_D2Q9 ? 9 : 19;
+    const long long pops = 4LL * Q * c.G.NP * (long long)c.elem;    // h and g, two buffers each
+    out[0] = c.G.PX;
+    out[1] = c.G.PY;
+    out[2] = c.G.PZ;
+    out[3] = c.G.NP;
+    out[4] = pops;
+    // plus the error flag, and the scratch fields and reduction partials the
+    // first lbm_init_fields / lbm_macro / lbm_diagnostics allocate
+    out[5] = pops + (long long)sizeof(int) + 5LL * (long long)sizeof(double) * c.G.N +
+             8LL * (long long)sizeof(double) * 1024;
+    return LBM_OK;
+}
+
 void lbm_destroy(lbm_ctx* c) {
     if (!c || c->owner) return;
     for (int b = 0; b < 2; ++b) {

@@ -62,6 +62,8 @@ SIGNATURES = [
                                   ctypes.POINTER(_VP)]),
     ("lbm_create_ex", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), _VP,
                                      ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("lbm_layout", ctypes.c_int, [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params), ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_longlong)]),
     ("lbm_init_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     ("lbm_init_fields_ex", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -181,6 +183,21 @@ def make_params(M=0.1, W=4.0, sigma=0.01, rho_L=0.001, rho_H=1.0, nu_L=0.1 / 6, 
     p.P_ref, p.g_scale = P_ref, g_scale
     p.C_dtheta = C_dtheta
     return p
+
+
+def layout(lattice, shape, params, bc=(PERIODIC, PERIODIC, PERIODIC), ghost_band=False):
+    """lbm_layout on the host (no GPU needed): dict of the padded extents px,
+    py, pz of the population arrays (internal axes), cells per array, bytes of
+    the population buffers and bytes of an initialised context."""
+    g = lbm_grid()
+    g.nx, g.ny = int(shape[0]), int(shape[1])
+    g.nz = int(shape[2]) if lattice == D3Q19 else 1
+    for a in range(3):
+        g.bc[a] = bc[a] if a < len(bc) else PERIODIC
+    out = (ctypes.c_longlong * 6)()
+    _check(load().lbm_layout(ctypes.byref(g), lattice, ctypes.byref(params), CREATE_GHOST_BAND if ghost_band else 0,
+                             out), "lbm_layout")
+    return dict(px=out[0], py=out[1], pz=out[2], cells=out[3], population_bytes=out[4], context_bytes=out[5])
 
 
 def _ptr(a, writable=False, n=None, device=None, name="field"):

@@ -217,3 +217,50 @@ def test_create_rejects_grids_whose_padded_size_overflows(lib):
     g.nx, g.ny, g.nz = 65536, 32768, 1
     rc = lib.lbm_create_ex(ctypes.byref(g), lbm.D2Q9, ctypes.byref(prm), None, 0, ctypes.byref(ctx))
     assert rc == lbm.EINVAL
+
+
+@pytest.mark.parametrize("store,elem", [(0, 8), (1, 4), (2, 2), (3, 2)], ids=["f64", "f32", "f16s", "bf16s"])
+def test_layout_plan_on_the_host(lib, store, elem):
+    """lbm_layout reports the padded layout of the population arrays without
+    a GPU: x rows padded to 32 bytes; ghost cells only along walled axes
+    (32 bytes of x, at least 2 cells; 2 in y; one plane in z), or along every
+    axis with the ghost band; population buffers of 4 Q cells x the element
+    size (h and g at two time levels); the context's total adds the 5 N
+    doubles of scratch fields and the reduction partials."""
+    from paper_1812_00118_gb300 import lbm
+    prm = lbm.make_params(store=store)
+    a32 = 32 // elem
+    gx = max(a32, 2)
+    pad = lambda n: (n + a32 - 1) // a32 * a32
+    for shape, bc, band in (((128, 128, 128), (0, 0, 0), False), ((37, 21, 13), (1, 0, 1), False),
+                            ((37, 21, 13), (0, 1, 0), False), ((37, 21, 13), (0, 0, 0), True)):
+        L_ = lbm.layout(lbm.D3Q19, shape, prm, bc=bc, ghost_band=band)
+        nx, ny, nz = shape
+        wx, wy, wz = (band or bc[0] == 1), (band or bc[1] == 1), (band or bc[2] == 1)
+        assert L_["px"] == pad(nx) + (2 * gx if wx else 0)
+        assert L_["py"] == ny + (4 if wy else 0)
+        assert L_["pz"] == nz + (2 if wz else 0)
+        assert L_["px"] * elem % 32 == 0
+        assert L_["cells"] == L_["px"] * L_["py"] * L_["pz"]
+        assert L_["population_bytes"] == 4 * 19 * L_["cells"] * elem
+        assert L_["context_bytes"] == L_["population_bytes"] + 4 + 40 * nx * ny * nz + 8 * 8 * 1024
+    # D2Q9: the user's y is the internal z; no y ghosts
+    L2 = lbm.layout(lbm.D2Q9, (100, 60), prm, bc=(1, 1))
+    assert (L2["px"], L2["py"], L2["pz"]) == (pad(100) + 2 * gx, 1, 62)
+    assert L2["population_bytes"] == 4 * 9 * L2["cells"] * elem
+
+
+def test_layout_refuses_what_create_refuses(lib):
+    from paper_1812_00118_gb300 import lbm
+    prm = lbm.make_params()
+    for lattice, shape in ((lbm.D3Q19, (65536, 65536, 1)), (lbm.D3Q19, (0, 8, 8)), (lbm.D2Q9, (65536, 32768))):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.layout(lattice, shape, prm)
+        assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.layout(lbm.D3Q19, (8, 8, 8), lbm.make_params(M=0.0))
+    # the largest FP32 cube within the 2^31-cell limit of one population array
+    ok = lbm.layout(lbm.D3Q19, (1288, 1288, 1288), prm)
+    assert ok["cells"] < 2 ** 31
+    with pytest.raises(lbm.LbmError):
+        lbm.layout(lbm.D3Q19, (1296, 1296, 1296), prm)
