@@ -162,6 +162,44 @@ def test_laplace_slope_is_sigma():
 
 
 @pytest.mark.slow
+def test_laplace_law_at_the_papers_low_viscosity():
+    """Section 4.1's own parameter set: R = 8, 12, 16 in a periodic box of
+    5 R, nu_water = 3.3e-4 (tau = 0.501), viscosity ratio 60, M = 0.1, W =
+    2.5, density ratio 1000, sigma = 1e-2 in the paper's units (1e-5 with the
+    heavy density 1, reading 16).  So little viscosity leaves the acoustic
+    waves of the start almost undamped and the instantaneous jump swings by
+    tens of percent, so dP is averaged over steps 1000-4000 (every 10th).
+    The averaged jumps follow sigma / R within 20 % (the W = 2.5 surface
+    tension error of the 2-D pins; measured 0.88, 0.87, 0.85) and their line
+    against 1/R has slope sigma within 15 % (0.90) through the origin
+    within 8 % of the jumps (-4 %)."""
+    sigma, W, nu_H = 1e-5, 2.5, 3.3e-4
+    res = []
+    for R in (8, 12, 16):
+        N = 5 * R
+        p = O.Params(M=0.1, W=W, sigma=sigma, rho_L=1e-3, rho_H=1.0, nu_L=nu_H * 1000.0 / 60.0, nu_H=nu_H)
+        shape = (1, N, N)
+        centre = (N / 2, N / 2, 0)
+        phi, u, P = I.sphere(shape, centre, R, W)
+        h, g = O.init_populations(phi, u, P, L.D2Q9, p)
+        h, g = O.run(h, g, L.D2Q9, p, 1000)
+        jumps = []
+        for _ in range(300):
+            m = O.macroscopic(h, g, L.D2Q9, p)
+            Reff = D.effective_radius(m["phi"], 2, True)
+            jumps.append(D.laplace_jump(m["P"], centre, Reff, W))
+            h, g = O.run(h, g, L.D2Q9, p, 10)
+        dP = float(np.mean(jumps))
+        assert abs(dP / (sigma / Reff) - 1.0) < 0.2, (R, dP / (sigma / Reff))
+        res.append((Reff, dP))
+    x = np.array([1.0 / r for r, _ in res])
+    y = np.array([d for _, d in res])
+    slope, icpt = np.linalg.lstsq(np.vstack([x, np.ones_like(x)]).T, y, rcond=None)[0]
+    assert slope == pytest.approx(sigma, rel=0.15)
+    assert abs(icpt) < 0.08 * y.mean()
+
+
+@pytest.mark.slow
 def test_laplace_law_2d_bubble():
     """A light bubble in the heavy phase: the pressure inside is again the
     higher one, by sigma / R (the surface force mu grad(phi) integrates to
