@@ -23,6 +23,7 @@ from oracle import lattice as L
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = open(os.path.join(ROOT, "oracle", "pflbm.py")).read()
 SRC_SG = open(os.path.join(ROOT, "oracle", "surrogate.py")).read()
+SRC_DG = open(os.path.join(ROOT, "oracle", "diagnostics.py")).read()
 
 D2 = dict(lat=L.D2Q9)
 
@@ -171,5 +172,29 @@ def test_surrogate_pin_fails_on_planted_slip(monkeypatch, slip, old, new, pin, k
     test = getattr(tm, pin)
     test(**kwargs)
     monkeypatch.setattr(tm, "S", _planted(old, new, SRC_SG, "surrogate.py"))
+    with pytest.raises(AssertionError):
+        test(**kwargs)
+
+
+# validation diagnostics: (slip, expression, planted form, pin test of test_oracle_diagnostics, arguments)
+DG_CASES = [
+    ("3-D radius with the 2-D formula", "return (3.0 * V / (4.0 * np.pi)) ** (1.0 / 3.0)",
+     "return (V / np.pi) ** (1.0 / 3.0)", "test_effective_radius_of_a_tanh_sphere",
+     dict(dim=3, R=9.6, drop=True)),
+    ("bubble volume from phi", "V = float(phi.sum()) if drop else float((1.0 - phi).sum())",
+     "V = float(phi.sum())", "test_effective_radius_of_a_tanh_sphere", dict(dim=2, R=11.7, drop=False)),
+    ("jump outside minus inside", "return float(inside - outside)", "return float(outside - inside)",
+     "test_laplace_jump_of_a_step_field", {}),
+    ("distance without minimum image", "dd = (dd + n / 2.0) % n - n / 2.0", "dd = dd % n",
+     "test_radial_distance_minimum_image", {}),
+]
+
+
+@pytest.mark.parametrize("slip,old,new,pin,kwargs", DG_CASES, ids=[c[0] for c in DG_CASES])
+def test_diagnostics_pin_fails_on_planted_slip(monkeypatch, slip, old, new, pin, kwargs):
+    tm = importlib.import_module("test_oracle_diagnostics")
+    test = getattr(tm, pin)
+    test(**kwargs)
+    monkeypatch.setattr(tm, "D", _planted(old, new, SRC_DG, "diagnostics.py"))
     with pytest.raises(AssertionError):
         test(**kwargs)
