@@ -113,8 +113,8 @@ typedef struct {
  * stream) of the current device.  Populations are zero until
  * lbm_init_fields or lbm_set_populations.  `lattice` is an lbm_lattice.
  * Errors: LBM_EINVAL (sizes < 1, nz != 1 for D2Q9, a periodic axis shorter
- * than 1, tau <= 1/2, M <= 0, W <= 0, rho <= 0, unknown store, a padded grid
- * of 2^31 cells or more),
+ * than 1, tau <= 1/2, M <= 0, W <= 0, rho <= 0, a parameter that is not
+ * finite, g_scale < 0, unknown store, a padded grid of 2^31 cells or more),
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_create(const lbm_grid* grid, int lattice, const lbm_params* params,
                void* cuda_stream, lbm_ctx** out);

@@ -57,7 +57,13 @@ int derive(const lbm_params& u, int lattice, Phys* out) {
         !(u.nu_L > 0) || !(u.nu_H > 0) || !(u.eps > 0))
         return LBM_EINVAL;
     if (u.force_mode != 0 && u.force_mode != 1) return LBM_EINVAL;
-    if (!std::isfinite(u.C_dtheta)) return LBM_EINVAL;
+    // every real parameter finite (an infinite viscosity or density, or a
+    // NaN shift of the 16-bit storage, would only show as a diverged state)
+    const double reals[] = {u.M, u.W, u.sigma, u.rho_L, u.rho_H, u.nu_L, u.nu_H, u.g[0], u.g[1], u.g[2],
+                            u.eps, u.P_ref, u.g_scale, u.C_dtheta};
+    for (double v : reals)
+        if (!std::isfinite(v)) return LBM_EINVAL;
+    if (u.g_scale < 0) return LBM_EINVAL;
     if (elem_size(u.store) == 0) return LBM_EINVAL;
     Phys p{};
     p.inv_tau_phi = 1.0 / (u.M / kT + 0.5);

@@ -123,6 +123,10 @@ def test_create_rejects_bad_arguments_before_any_allocation(lib):
     assert create(g3) == (lbm.EINVAL, None)                              # unknown boundary type
     bad = lbm.make_params(M=0.0)
     assert create(g, params=bad) == (lbm.EINVAL, None)                   # M must be positive
+    inf, nan = float("inf"), float("nan")
+    for kw in (dict(nu_L=inf), dict(rho_H=inf), dict(sigma=nan), dict(g=(nan, 0.0, 0.0)), dict(eps=inf),
+               dict(store=lbm.F16S, P_ref=nan), dict(store=lbm.F16S, g_scale=-1.0), dict(C_dtheta=inf)):
+        assert create(g, params=lbm.make_params(**kw)) == (lbm.EINVAL, None), kw   # not finite / negative scale
 
 
 def test_simulation_binding_rejects_wrong_sizes_before_any_call(lib):
