@@ -268,3 +268,31 @@ def test_layout_refuses_what_create_refuses(lib):
     assert ok["cells"] < 2 ** 31
     with pytest.raises(lbm.LbmError):
         lbm.layout(lbm.D3Q19, (1296, 1296, 1296), prm)
+
+
+def test_surrogate_calls_validate_arguments_on_the_host(lib):
+    """The surrogate kernels' C-ABI refuses bad arguments before any device
+    call: NULL operands, channel counts that are not multiples of 16 or above
+    128 outputs, operands off their 16-byte boundary, strides below the
+    channel count, pooling factors that do not divide the grid, negative
+    pixel counts, an Adam step below 1, an unstable diffusion coefficient and
+    a bulk-phase threshold of 1/2 or more all return LBM_EINVAL.  The
+    addresses passed are never dereferenced (this machine has no GPU)."""
+    import ctypes
+    from paper_1812_00118_gb300 import lbm
+    V = ctypes.c_void_p
+    p = V(1 << 14)                      # 16-byte aligned, not NULL
+    cases = [
+        lambda: lib.lbm_sg_conv3x3(None, 16, p, None, p, 16, 1, 8, 128, 16, 16, None),
+        lambda: lib.lbm_sg_conv3x3(p, 16, p, None, p, 16, 1, 8, 128, 8, 16, None),
+        lambda: lib.lbm_sg_conv3x3(p, 144, p, None, p, 144, 1, 8, 128, 16, 144, None),
+        lambda: lib.lbm_sg_conv3x3(V((1 << 14) + 2), 16, p, None, p, 16, 1, 8, 128, 16, 16, None),
+        lambda: lib.lbm_sg_conv3x3(p, 8, p, None, p, 16, 1, 8, 128, 16, 16, None),
+        lambda: lib.lbm_sg_pool(p, 16, p, 16, 1, 8, 8, 16, 3, None),
+        lambda: lib.lbm_sg_relu(p, 16, p, 16, -1, 16, None),
+        lambda: lib.lbm_sg_adam(p, p, p, p, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None, None),
+        lambda: lib.lbm_sg_smooth(p, p, 1, 8, 8, 1, 0.3, None),
+        lambda: lib.lbm_sg_phase_pressure(p, p, 10, 0.6, p, p, None),
+    ]
+    for k, call in enumerate(cases):
+        assert call() == lbm.EINVAL, k
