@@ -296,3 +296,27 @@ def test_surrogate_calls_validate_arguments_on_the_host(lib):
     ]
     for k, call in enumerate(cases):
         assert call() == lbm.EINVAL, k
+
+
+def test_every_entry_point_is_documented():
+    """Every function include/*.h declares is preceded by its comment block
+    (what it computes, the arguments' meaning and layout, ownership, errors)
+    or belongs to the group a block describes."""
+    decl = re.compile(r"^(?:int|void|long long|const char\*|lbm_ctx\*|void\*)\s+\*?(lbm\w+)\s*\(")
+    undocumented = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", f)).read().split("\n")
+        for i, line in enumerate(lines):
+            m = decl.match(line)
+            if not m:
+                continue
+            j = i - 1
+            while j >= 0 and (not lines[j].strip() or decl.match(lines[j])
+                              or (lines[j].startswith(" ") and not lines[j].strip().startswith("*"))):
+                j -= 1
+            prev = lines[j].strip() if j >= 0 else ""
+            if not (prev.endswith("*/") or prev.startswith("#define")):
+                undocumented.append(f"{f}: {m.group(1)}")
+    assert not undocumented, undocumented
