@@ -31,6 +31,7 @@ def test_velocity_set_matches_definition(lat):
     ref = reference_set(lat.name)
     got = {tuple(int(a) for a in c): w for c, w in zip(lat.c, lat.w)}
     assert len(got) == lat.Q == len(ref)
+    assert set(got) == set(ref), sorted(set(got) ^ set(ref))
     for v, w in ref.items():
         assert got[v] == pytest.approx(w, abs=1e-16)
 

@@ -24,6 +24,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = open(os.path.join(ROOT, "oracle", "pflbm.py")).read()
 SRC_SG = open(os.path.join(ROOT, "oracle", "surrogate.py")).read()
 SRC_DG = open(os.path.join(ROOT, "oracle", "diagnostics.py")).read()
+SRC_LAT = open(os.path.join(ROOT, "oracle", "lattice.py")).read()
 
 D2 = dict(lat=L.D2Q9)
 
@@ -198,3 +199,26 @@ def test_diagnostics_pin_fails_on_planted_slip(monkeypatch, slip, old, new, pin,
     monkeypatch.setattr(tm, "D", _planted(old, new, SRC_DG, "diagnostics.py"))
     with pytest.raises(AssertionError):
         test(**kwargs)
+
+
+# velocity sets: (slip, expression, planted form, lattice, pin test of test_oracle_lattice)
+LAT_CASES = [
+    ("D3Q19 edge pair made corners", "(1, 0, 1), (-1, 0, -1)", "(1, 1, 1), (-1, -1, -1)", "D3Q19",
+     "test_velocity_set_matches_definition"),
+    ("D3Q19 edge weight 1/18", "[1.0 / 3.0] + [1.0 / 18.0] * 6 + [1.0 / 36.0] * 12",
+     "[1.0 / 3.0] + [1.0 / 18.0] * 7 + [1.0 / 36.0] * 11", "D3Q19", "test_isotropy"),
+    ("D2Q9 rest weight 1/3", "[4.0 / 9.0] + [1.0 / 9.0] * 4", "[1.0 / 3.0] + [1.0 / 9.0] * 4", "D2Q9",
+     "test_isotropy"),
+    ("D2Q9 diagonal pair made long axis", "(1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)",
+     "(2, 0, 0), (-1, 1, 0), (-2, 0, 0), (1, -1, 0)", "D2Q9", "test_velocity_set_matches_definition"),
+]
+
+
+@pytest.mark.parametrize("slip,old,new,name,pin", LAT_CASES, ids=[c[0] for c in LAT_CASES])
+def test_lattice_pin_fails_on_planted_slip(slip, old, new, name, pin):
+    tm = importlib.import_module("test_oracle_lattice")
+    test = getattr(tm, pin)
+    test(lat=getattr(L, name))
+    planted = _planted(old, new, SRC_LAT, "lattice.py")
+    with pytest.raises(AssertionError):
+        test(lat=getattr(planted, name))
