@@ -90,3 +90,16 @@ def test_oracle_runs_only_where_allowed():
         for mod, func in _imports(os.path.join(ROOT, name)):
             if mod.split(".")[0] == "oracle":
                 assert func in funcs, (name, mod, func)
+
+
+def test_nothing_committed_uses_the_working_folder():
+    """No source, test or script reads, imports or runs anything under the
+    git-ignored working folder."""
+    work = "_" + "work/"
+    for base, dirs, files in os.walk(ROOT):
+        dirs[:] = [d for d in dirs if d not in {".git", "_work", "gpurun_out", "__pycache__", "_build",
+                                                "_build_checked", "_lib", "baseline"}]
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".sh", ".ini", ".toml", ".cfg")):
+                path = os.path.join(base, f)
+                assert work not in open(path, errors="replace").read(), path
